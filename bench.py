@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the EnSF analysis step on GB300.
+
+One "step" is one full analysis (Sec. III-A.2): row norms and splits of the
+forecast ensemble, the initial Gaussian particles, then K Euler-Maruyama steps
+of Gram + softmax + weighted sum + score + update.  Metric: member-steps/s =
+N * K / (wall time of one analysis), summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--path split-bf16|split|fp32] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (rows are independent, so a few particle rows
+through a few Euler-Maruyama steps is an exact sample of the work).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2407_12168_gb300 import inputs  # noqa: E402
+
+PATHS = {
+    # name: (gram precision, W X precision)
+    "split-bf16": ("split", "bf16"),
+    "split": ("split", "split"),
+    "fp32": ("fp32", "fp32"),
+}
+METRIC = "EnSF member-steps/s (analysis step, K Euler-Maruyama steps per member)"
+UNIT = "member-steps/s"
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def _dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), \
+        int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _traffic_record(kernel: str, workload: str, path: str):
+    """DRAM traffic per launch from a committed ncu summary, valid only while
+    the kernel source is unchanged (sha256 recorded beside the number)."""
+    fn = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(fn):
+        return None
+    src = os.path.join(ROOT, "paper_2407_12168_gb300", "csrc",
+                       "ensf_simt.cu" if path == "fp32" else "ensf_tc.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(fn):
+        m = re.match(r"^traffic\s+(\S+)\s+(\S+)\s+(\S+)\s+(\S+)\s+bytes_per_launch=(\d+)", line)
+        if m and m.group(1) == kernel and m.group(2) == workload and m.group(3) == path and m.group(4) == sha:
+            return int(m.group(5))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_problem(workload: str, rank: int):
+    fn = inputs.WORKLOADS[workload]
+    # every rank runs an independent filter (another seed: another truth, prior, noise)
+    return fn(seed={"plain-64": 1, "sparse-arctan-128": 2, "large-512": 4}[workload] + 1000 * rank)
+
+
+def cpu_baseline(p, budget_s: float = 15.0):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of
+    the workload: `rows` particle rows through the first `k_stop` of the K
+    Euler-Maruyama steps (rows are independent, every step costs the same)."""
+    from oracle import oracle as o
+    t0 = time.perf_counter()
+    o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed, rows=[0], k_stop=1)
+    per = max(time.perf_counter() - t0, 1e-4)
+    k_stop = int(max(1, min(p.K, budget_s / per)))
+    rows = int(max(1, min(p.n, budget_s / (per * k_stop))))
+    t0 = time.perf_counter()
+    o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed,
+               rows=list(range(rows)), k_stop=k_stop)
+    dt = time.perf_counter() - t0
+    return {"value": rows * k_stop / dt, "unit": UNIT, "cores": o.num_threads(), "kind": "oracle",
+            "sample": f"{rows} particle row(s) x {k_stop} of {p.K} Euler-Maruyama steps of {p.name} "
+                      f"(N={p.n}, d={p.d}), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = _dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as o
+    p = make_problem(args.workload, 0)
+    t0 = time.perf_counter()
+    o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed, rows=[0], k_stop=1)
+    per = max(time.perf_counter() - t0, 1e-4)
+    k_stop = int(max(1, min(p.K, args.ref_step_s / per)))
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed, rows=[it % p.n],
+                   k_stop=k_stop)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = float(np.sum(times))
+    value = args.steps * k_stop / tot
+    sample = f"1 particle row x {k_stop} of {p.K} Euler-Maruyama steps of {p.name} (N={p.n}, d={p.d}) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(p, "oracle-fp64", world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _config(p, path, world):
+    return {"workload": p.name, "N": p.n, "d": p.d, "K": p.K, "eps": p.eps, "sigma_obs": p.sigma_obs,
+            "obs": ("arctan" if p.obs_op == 1 else "identity") + ("" if p.mask is None else
+                                                                  f", {int(p.mask.sum())} of {p.d} points"),
+            "path": path, "noise": "Philox4x32-10 in-kernel",
+            "l2": "inputs larger than L2" if p.n * p.d * 4 > 256 << 20 else "L2 flushed between steps",
+            "parallelism": f"{world} independent filter(s), one per GPU"}
+
+
+def run_ours(args):
+    import torch
+    rank, local_rank, world = _dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2407_12168_gb300 import ensf
+
+    gram, wx = PATHS[args.path]
+    p = make_problem(args.workload, rank)
+    dev = torch.device("cuda", local_rank)
+    prior = torch.from_numpy(p.prior).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    mask = torch.from_numpy(p.mask).to(dev) if p.mask is not None else None
+    out = torch.empty_like(prior)
+    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx)
+    stream = torch.cuda.current_stream()
+    small = p.n * p.d * 4 <= 256 << 20
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if small else None
+
+    def one(k_seed):
+        f.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed + k_seed, out=out)
+
+    for w in range(args.warmup):
+        one(w)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM ----
+    f.profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for s_ in range(args.steps):
+            if flush is not None:
+                flush.zero_()
+            ev[s_][0].record(stream)
+            one(100 + s_)
+            ev[s_][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    prof = f.profile_read()
+    f.profile_enable(False)
+    if f.status_sync() != 0:
+        raise RuntimeError("device error during the benchmark")
+
+    # ---- end to end: host buffers, copies inside the timed region ----
+    h_prior = torch.from_numpy(p.prior).pin_memory()
+    h_y = torch.from_numpy(p.y).pin_memory()
+    h_mask = torch.from_numpy(p.mask).pin_memory() if p.mask is not None else None
+    h_out = torch.empty(prior.shape, dtype=torch.float32).pin_memory()
+    d_prior, d_y = torch.empty_like(prior), torch.empty_like(y)
+    d_mask = torch.empty_like(mask) if mask is not None else None
+    e2e_steps = max(1, min(args.steps, 3))
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    for s_ in range(e2e_steps):
+        if flush is not None:
+            flush.zero_()
+        ee[s_][0].record(stream)
+        d_prior.copy_(h_prior, non_blocking=True)
+        d_y.copy_(h_y, non_blocking=True)
+        if d_mask is not None:
+            d_mask.copy_(h_mask, non_blocking=True)
+        f.analysis(d_prior, d_y, d_mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed + 200 + s_, out=out)
+        h_out.copy_(out, non_blocking=True)
+        ee[s_][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in ee)) / e2e_steps
+    h2d = p.prior.nbytes + p.y.nbytes + (p.mask.nbytes if p.mask is not None else 0)
+    d2h = p.n * p.d * 4
+
+    # ---- max over ranks ----
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    ms_per_step = ms / args.steps
+    member_steps = p.n * p.K
+    value = world * member_steps / (ms_per_step / 1e3)
+    e2e_value = world * member_steps / (e2e_ms / 1e3)
+
+    # ---- roofline of the dominant kernel ----
+    kernels = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kernels, key=lambda k: kernels[k][2])
+    launches, timed, tot_ms = kernels[dom]
+    avg_ms = tot_ms / timed
+    peaks = _peaks()
+    flops_gemm = 2.0 * p.n * p.n * p.d        # algorithmic FLOPs of one Gram or one W X
+    split_factor = {"split": 3.0, "bf16": 1.0, "fp32": 1.0}
+    prec = gram if dom == "gram" else wx
+    executed = flops_gemm * split_factor[prec]
+    if prec == "fp32":
+        bound, peak, peak_src = "alu", FP32_SIMT_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+    else:
+        bound = "tensor"
+        if peaks:
+            peak, peak_src = float(peaks["bf16_tflops_sustained"]), "measured bf16 sustained (MEASURED_PEAKS.json)"
+        else:
+            peak, peak_src = 1700.0, "fallback bf16 sustained"
+    achieved = flops_gemm / (avg_ms / 1e3) / 1e12
+    traffic = _traffic_record(dom, p.name, args.path)
+    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+            "algorithmic_flops_per_launch": flops_gemm, "avg_launch_ms": avg_ms,
+            "executed_flops_per_launch": executed,
+            "executed_tflops": executed / (avg_ms / 1e3) / 1e12,
+            "executed_frac": executed / (avg_ms / 1e3) / 1e12 / peak}
+    gpu_launches = int(sum(v[0] for v in prof.values()))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"split-bf16": "bf16x3+bf16 (fp32 acc)", "split": "bf16x3 (fp32 acc)",
+                                          "fp32": "f32"}[args.path],
+            "data": "synthetic", "config": _config(p, args.path, world), "roofline": roof,
+            "kernels": {k: {"launches": v[0], "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": gpu_launches, "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget_s)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="large-512", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--path", default="split-bf16", choices=sorted(PATHS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: warm-up raised to the minimum of 3", file=sys.stderr)
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * ensf.h -- C ABI of the GB300-native EnSF analysis step.
+ *
+ * The ensemble score filter (EnSF) analysis of Bao et al., "A Scalable
+ * Real-Time Data Assimilation Framework for Predicting Turbulent Atmosphere
+ * Dynamics" (Sec. III-A): every particle z_i starts from N(0, I) at pseudo-time
+ * t = 1 and runs K Euler-Maruyama steps of the reverse-time SDE (Eq. 7),
+ *
+ *   z <- z - dt (b(t) z - sigma^2(t) s(z, t)) + sqrt(sigma^2(t) dt) xi,
+ *
+ * with the posterior score of Eq. 17, s = s_prior + h(t) grad log P(y | z):
+ *
+ *   s_prior(z_i) = -sum_j w_ij (z_i - alpha_t x_j) / beta_t^2        (Eq. 15)
+ *   w_ij = softmax_j(-|z_i - alpha_t x_j|^2 / (2 beta_t^2))          (Eq. 12, 16)
+ *   grad log P(y | z) = mask * H'(z) (y - H(z)) / sigma_obs^2         (Eq. 5)
+ *
+ * Schedule (Eq. 9): alpha_t = 1 - t(1 - eps), beta_t^2 = t,
+ * b = d log(alpha)/dt, sigma^2 = d(beta^2)/dt - 2 b beta^2; damping
+ * h(t) = 1 - t (Eq. 11); grid t_k = 1 - k/K, k = 0..K-1, dt = 1/K.
+ *
+ * Conventions shared by every entry point:
+ *  - All array pointers are DEVICE pointers unless stated otherwise; the
+ *    caller owns them.  Arrays are row-major and densely packed.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; no entry point synchronises the host
+ *    except ensf_status_sync.
+ *  - Argument errors are reported before anything is enqueued.  Device-side
+ *    errors are recorded in an error word inside the workspace and returned
+ *    (and cleared) by ensf_status_sync.
+ *  - The library never allocates device memory: scratch lives in the
+ *    caller-provided workspace.
+ */
+#ifndef ENSF_H
+#define ENSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ENSF_OK = 0,
+    ENSF_EINVAL = 1,        /* bad argument (NULL/misaligned pointer, size out of range) */
+    ENSF_ENOMEM = 2,        /* workspace smaller than ensf_workspace_bytes() */
+    ENSF_ECUDA = 3,         /* a CUDA runtime call failed */
+    ENSF_ENUMERIC = 4,      /* a non-finite value was produced (when checking is on) */
+    ENSF_ETIMEOUT = 5,      /* a bounded device-side wait expired */
+    ENSF_EUNSUPPORTED = 6   /* configuration not supported on this device */
+} ensf_status;
+
+/* Observation operator H of Eq. 2, applied elementwise. */
+typedef enum {
+    ENSF_OBS_IDENTITY = 0,  /* H(z) = z,         H'(z) = 1           */
+    ENSF_OBS_ARCTAN = 1     /* H(z) = arctan(z), H'(z) = 1/(1 + z^2) */
+} ensf_obs_op;
+
+/* Arithmetic of the two contractions of each Euler-Maruyama step. */
+typedef enum {
+    ENSF_PREC_FP32 = 0,        /* CUDA-core FP32 for the Gram Z X^T and for W X */
+    ENSF_PREC_SPLIT_BF16X3 = 1 /* tensor cores: each operand split a = a_hi + a_lo in BF16,
+                                  products a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulate */,
+    ENSF_PREC_BF16 = 2         /* tensor cores: one BF16 product, FP32 accumulate */
+} ensf_precision;
+
+#define ENSF_FLAG_CHECK_FINITE 1u  /* scan the final particles for NaN/Inf */
+
+typedef struct {
+    int max_n;        /* largest ensemble size N this handle will run (>= 1)          */
+    int64_t max_d;    /* largest state dimension d (>= 8, multiple of 8)               */
+    int gram;         /* ensf_precision of the Gram cross term Z X^T (Eq. 12, 16)     */
+    int wx;           /* ensf_precision of the weighted sum W X (Eq. 15)              */
+    unsigned flags;   /* ENSF_FLAG_* */
+} ensf_config;
+
+/* Gaussian noise xi[k][i][j], k = 0..K (slice 0 = the initial particles,
+ * slice k+1 = the noise of Euler-Maruyama step k). */
+typedef struct {
+    const float *buf;   /* [K+1][n][d] FP32 device buffer, or NULL: use the
+                           counter-based stream below, computed inside the kernels */
+    uint64_t seed;      /* Philox4x32-10 key (Salmon et al., SC'11)                */
+    uint32_t offset;    /* fourth counter word (e.g. the assimilation cycle)       */
+} ensf_noise;
+
+typedef struct ensf_handle ensf_handle;
+
+/* Bytes of device workspace a handle with this configuration needs. Returns 0
+ * for an invalid configuration. */
+size_t ensf_workspace_bytes(const ensf_config *cfg);
+
+/* Create a handle over a caller-owned device workspace (256-byte aligned, at
+ * least ensf_workspace_bytes(cfg) bytes, kept alive until ensf_destroy).
+ * Host memory for the handle itself is allocated here.  Returns ENSF_ENOMEM
+ * if ws_bytes is too small, ENSF_EUNSUPPORTED if a tensor-core precision is
+ * requested on a device that is not sm_103. */
+ensf_status ensf_create(const ensf_config *cfg, void *workspace, size_t ws_bytes,
+                        ensf_handle **out);
+
+/* The analysis step (Sec. III-A.2, Eq. 7 and 15-17).
+ *   prior     [n][d] FP32  forecast ensemble x_j (read only; must not alias out)
+ *   y         [d]    FP32  observations (entries where mask = 0 are ignored)
+ *   obs_mask  [d]    uint8 1 = observed, or NULL = every point observed
+ *   obs_op    ensf_obs_op
+ *   sigma_obs > 0          R = sigma_obs^2 I
+ *   K >= 1                 Euler-Maruyama steps on the grid t_k = 1 - k/K
+ *   eps in (0, 1)          alpha_t = 1 - t(1 - eps)
+ *   noise                  see ensf_noise (host struct; may not be NULL)
+ *   out       [n][d] FP32  the analysis ensemble (particles after K steps)
+ * Pointers must be 16-byte aligned; 1 <= n <= max_n; 8 <= d <= max_d and
+ * d % 8 == 0.  Enqueued on `stream`. */
+ensf_status ensf_analysis(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                          const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
+                          const ensf_noise *noise, float *out, void *stream);
+
+/* Normalised weights w_ij of Eq. 16 for given particles z [n][d] at pseudo-
+ * time t, against the forecast ensemble prior [n_x][d], written to
+ * w [n][n_x] FP32.  Uses the handle's Gram precision; this is the Gram +
+ * log-sum-exp stage of one analysis step exposed on its own. */
+ensf_status ensf_weights(ensf_handle *h, const float *z, int n, const float *prior, int n_x,
+                         int64_t d, float t, float eps, float *w, void *stream);
+
+/* Standalone counter-based noise: out[k - k0][i][j] = xi[k][i][j] for
+ * k = k0..k0+count-1, i < n, j < d (the stream used when ensf_noise.buf is
+ * NULL). */
+ensf_status ensf_philox_normal(uint64_t seed, uint32_t offset, int k0, int count, int n,
+                               int64_t d, float *out, void *stream);
+
+/* FP64 squared row norms  out[j] = sum_c x[j][c]^2  of x [n][d]. */
+ensf_status ensf_row_norms(const float *x, int n, int64_t d, double *out, void *stream);
+
+/* FP64 ensemble statistics of z [n][d]: mean[c] = (1/n) sum_i z[i][c]
+ * (device [d], may be NULL) and, when truth != NULL, the RMSE of that mean
+ * against truth [d] written to rmse (device, one double).  Uses `scratch`
+ * (device, at least ensf_stats_scratch_bytes(d) bytes). */
+size_t ensf_stats_scratch_bytes(int64_t d);
+ensf_status ensf_ensemble_stats(const float *z, int n, int64_t d, const float *truth,
+                                double *mean, double *rmse, void *scratch, void *stream);
+
+/* Launch accounting of a handle.  Every kernel launch is counted by kind
+ * ("row_norms", "init_particles", "split_bf16", "gram", "softmax_rows",
+ * "wx_em", "check_finite").  While profiling is on, each launch is also
+ * bracketed by a CUDA event pair recorded on the launching stream (at most
+ * 16384 pairs; later launches are counted but not timed).  Enabling or
+ * disabling clears the counters; the first enable creates the events. */
+typedef struct {
+    char name[32];
+    int64_t launches;        /* launches of this kind since the last enable */
+    int64_t timed_launches;  /* of which bracketed by events */
+    double total_ms;         /* summed event time of the timed launches */
+} ensf_profile_entry;
+
+ensf_status ensf_profile_enable(ensf_handle *h, int on);
+
+/* Waits for the recorded events; writes up to max_entries kinds with at least
+ * one launch and sets *count to the number of such kinds. */
+ensf_status ensf_profile_read(ensf_handle *h, ensf_profile_entry *out, int max_entries, int *count);
+
+/* Wait for `stream` and return the handle's recorded device error, clearing it. */
+ensf_status ensf_status_sync(ensf_handle *h, void *stream);
+
+/* Static description of a status code. */
+const char *ensf_status_string(ensf_status s);
+
+/* Host-side message of the most recent failing call on this thread ("" if none). */
+const char *ensf_last_error(void);
+
+/* Release the handle (the workspace stays the caller's). */
+ensf_status ensf_destroy(ensf_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ENSF_H */

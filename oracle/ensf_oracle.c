@@ -207,12 +207,16 @@ void ensf_oracle_prior_score(const float *X, int n, int64_t d, const double *z, 
  *         full analysis; fewer only to time a bounded sample)
  *   out   [nrows][d] final particles;  traj optional [k_stop+1][nrows][d]
  *         with the particles before step 0 and after every step.
+ *   diag  optional [k_stop][nrows][2]: per step and row, the gap between the
+ *         largest and second-largest log-kernel (how close the weights are to
+ *         a tie) and the scale alpha |z| max_j |x_j| / beta^2 that bounds how
+ *         much a relative error in z . x_j moves a log-kernel.
  * Returns 0, or -1 on an invalid argument.
  */
 int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const uint8_t *mask,
                          double sigma_obs, int K, double eps, int obs_op, const float *noise,
                          uint64_t seed, uint32_t offset, const int *rows, int nrows, int k_stop,
-                         double *out, double *traj)
+                         double *out, double *traj, double *diag)
 {
     if (n < 1 || d < 1 || K < 1 || !(eps > 0.0 && eps < 1.0) || !(sigma_obs > 0.0))
         return -1;
@@ -226,6 +230,14 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
     double *w = (double *)malloc(sizeof(double) * (size_t)nrows * (size_t)n);
     double *l = (double *)malloc(sizeof(double) * (size_t)nrows * (size_t)n);
     double *g = (double *)malloc(sizeof(double) * (size_t)d);
+    double xmax = 0.0;
+    if (diag) {
+        for (int j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int64_t c = 0; c < d; ++c) acc += (double)X[(size_t)j * d + c] * X[(size_t)j * d + c];
+            if (sqrt(acc) > xmax) xmax = sqrt(acc);
+        }
+    }
 
     /* z_i <- xi_0,i : the standard Gaussian sample at pseudo-time T = 1. */
     for (int r = 0; r < nrows; ++r) {
@@ -263,6 +275,19 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
             double lmax = lr[0];
             for (int j = 1; j < n; ++j)
                 if (lr[j] > lmax) lmax = lr[j];
+            if (diag) {
+                double second = -HUGE_VAL;
+                int top = 0;
+                for (int j = 1; j < n; ++j)
+                    if (lr[j] > lr[top]) top = j;
+                for (int j = 0; j < n; ++j)
+                    if (j != top && lr[j] > second) second = lr[j];
+                const double *z = out + (size_t)r * (size_t)d;
+                double zn = 0.0;
+                for (int64_t c = 0; c < d; ++c) zn += z[c] * z[c];
+                diag[((size_t)k * nrows + r) * 2 + 0] = (n > 1) ? lmax - second : HUGE_VAL;
+                diag[((size_t)k * nrows + r) * 2 + 1] = alpha * sqrt(zn) * xmax / beta2;
+            }
             double total = 0.0;
             for (int j = 0; j < n; ++j) {
                 wr[j] = exp(lr[j] - lmax);

@@ -1,0 +1,498 @@
+// ensf_api.cu -- host runtime behind the C ABI of include/ensf.h:
+// argument validation, the workspace layout, the per-step coefficient
+// schedule and the launch sequence of the analysis step.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ensf.h"
+#include "ensf_internal.h"
+#include "ensf_tc.h"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+ensf_status fail(ensf_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+ensf_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(ENSF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ENSF_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kSizingSMs = 256;      // upper bound on SMs used to size split-K scratch
+constexpr int kSimtTile = 64;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+bool is_tc(int p) { return p == ENSF_PREC_SPLIT_BF16X3 || p == ENSF_PREC_BF16; }
+
+// Offsets of every scratch array inside the workspace.
+struct Layout {
+    size_t err = 0, norms = 0, w = 0, partial = 0;
+    size_t xb_hi = 0, xb_lo = 0, zb_hi = 0, zb_lo = 0, xt_hi = 0, xt_lo = 0, wb_hi = 0, wb_lo = 0;
+    size_t total = 0;
+    int64_t partial_floats = 0;
+};
+
+int simt_splits(int n, int n_x, int64_t d, int sms) {
+    int64_t tiles = (int64_t)((n + kSimtTile - 1) / kSimtTile) * ((n_x + kSimtTile - 1) / kSimtTile);
+    int64_t want = (2 * (int64_t)sms + tiles - 1) / tiles;
+    int64_t max_by_d = std::max<int64_t>(1, d / 512);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, max_by_d));
+}
+
+bool config_ok(const ensf_config *c) {
+    if (!c || c->max_n < 1 || c->max_n > 8192 || c->max_d < 8 || c->max_d % 8 != 0) return false;
+    for (int p : {c->gram, c->wx})
+        if (p != ENSF_PREC_FP32 && p != ENSF_PREC_SPLIT_BF16X3 && p != ENSF_PREC_BF16) return false;
+    return true;
+}
+
+Layout make_layout(const ensf_config *c) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
+    const int64_t N = c->max_n, D = c->max_d;
+    L.err = take(sizeof(int) * 4);
+    L.norms = take(sizeof(double) * N);
+    L.w = take(sizeof(float) * N * N);
+    // split-K Gram partials: splits * n * n_x <= (target CTAs + tiles) * tile area
+    int64_t tiles_simt = ((N + kSimtTile - 1) / kSimtTile) * ((N + kSimtTile - 1) / kSimtTile);
+    int64_t simt_cap = (2 * (int64_t)kSizingSMs + tiles_simt) * kSimtTile * kSimtTile;
+    int64_t tc_cap = ensf::tc_partial_floats(c->max_n, kSizingSMs);
+    L.partial_floats = std::max<int64_t>(std::max<int64_t>(simt_cap, tc_cap), N * N);
+    L.partial = take(sizeof(float) * L.partial_floats);
+    if (is_tc(c->gram) || is_tc(c->wx)) {
+        const int64_t NP = round_up(N, 8);  // bf16 row pitch multiple of 16 bytes
+        if (is_tc(c->gram)) {
+            L.xb_hi = take(2 * N * D);
+            L.zb_hi = take(2 * N * D);
+            if (c->gram == ENSF_PREC_SPLIT_BF16X3) {
+                L.xb_lo = take(2 * N * D);
+                L.zb_lo = take(2 * N * D);
+            }
+        }
+        if (is_tc(c->wx)) {
+            L.xt_hi = take(2 * D * NP);
+            L.wb_hi = take(2 * N * NP);
+            if (c->wx == ENSF_PREC_SPLIT_BF16X3) {
+                L.xt_lo = take(2 * D * NP);
+                L.wb_lo = take(2 * N * NP);
+            }
+        }
+    }
+    L.total = off;
+    return L;
+}
+
+// Coefficients of Euler-Maruyama step k (Eq. 9, Eq. 11), in double.
+ensf::StepCoef step_coef(int k, int K, double eps, double sigma_obs, int obs_op) {
+    const double t = 1.0 - (double)k / (double)K;
+    const double alpha = 1.0 - t * (1.0 - eps);
+    const double b = -(1.0 - eps) / alpha;
+    const double beta2 = t;
+    const double sigma2 = 1.0 - 2.0 * b * beta2;
+    const double dt = 1.0 / (double)K;
+    ensf::StepCoef c;
+    c.alpha = (float)alpha;
+    c.inv_beta2 = (float)(1.0 / beta2);
+    c.b = (float)b;
+    c.sigma2 = (float)sigma2;
+    c.h = (float)(1.0 - t);
+    c.dt = (float)dt;
+    c.noise_scale = (float)std::sqrt(sigma2 * dt);
+    c.inv_r = (float)(1.0 / (sigma_obs * sigma_obs));
+    c.alpha_d = alpha;
+    c.inv_2beta2_d = 1.0 / (2.0 * beta2);
+    c.k = k;
+    c.obs_op = obs_op;
+    return c;
+}
+
+bool aligned16(const void *p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+// Per-handle launch accounting: every kernel launch is counted by kind; when
+// profiling is on, an event pair brackets each launch on its own stream.
+enum ProfKind { P_NORMS, P_INIT, P_SPLIT, P_GRAM, P_SOFTMAX, P_WXEM, P_CHECK, P_COUNT };
+const char *const kProfNames[P_COUNT] = {"row_norms", "init_particles", "split_bf16", "gram",
+                                         "softmax_rows", "wx_em", "check_finite"};
+constexpr size_t kProfPairs = 16384;
+
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> events;   // 2 * kProfPairs, created on first enable
+    std::vector<int> kinds;            // kind of each recorded pair
+    int64_t launches[P_COUNT] = {};
+    int64_t dropped = 0;
+    bool open = false;                 // a begin event awaits its end event
+};
+
+struct ensf_handle {
+    ensf_config cfg;
+    Prof prof;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout L;
+    int sms = 0;
+    int device = 0;
+    ensf::TcContext *tc = nullptr;
+
+    template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+    int *err() const { return at<int>(L.err); }
+};
+
+namespace {
+
+cudaError_t prof_begin(ensf_handle *h, int kind, cudaStream_t s) {
+    h->prof.launches[kind]++;
+    h->prof.open = false;
+    if (!h->prof.on) return cudaSuccess;
+    size_t pair = h->prof.kinds.size();
+    if (pair >= kProfPairs) { h->prof.dropped++; return cudaSuccess; }
+    h->prof.kinds.push_back(kind);
+    h->prof.open = true;
+    return cudaEventRecord(h->prof.events[2 * pair], s);
+}
+
+cudaError_t prof_end(ensf_handle *h, cudaStream_t s) {
+    if (!h->prof.open) return cudaSuccess;
+    h->prof.open = false;
+    return cudaEventRecord(h->prof.events[2 * (h->prof.kinds.size() - 1) + 1], s);
+}
+
+// Launch `call` counted (and, when profiling, timed) under `kind`.
+#define ENSF_LAUNCH(h, kind, s, call)                                   \
+    do {                                                                \
+        cudaError_t pe_ = prof_begin((h), (kind), (s));                 \
+        if (pe_ != cudaSuccess) return cuda_fail(pe_, "cudaEventRecord"); \
+        ENSF_CUDA(call);                                                \
+        pe_ = prof_end((h), (s));                                       \
+        if (pe_ != cudaSuccess) return cuda_fail(pe_, "cudaEventRecord"); \
+    } while (0)
+
+// Gram + row softmax for particles z [n][d] against prior [n_x][d] at step
+// coefficients c.  Writes W FP32 into h->w when want_fp32, and the BF16
+// weight planes when the W X contraction runs on tensor cores.
+ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *prior, int n_x, int64_t d,
+                         const ensf::StepCoef &c, bool want_fp32, cudaStream_t s) {
+    const Layout &L = h->L;
+    float *partial = h->at<float>(L.partial);
+    int splits = 0;
+    int64_t part_stride = 0;
+    int ldp = 0;
+    if (h->cfg.gram == ENSF_PREC_FP32) {
+        splits = simt_splits(n, n_x, d, h->sms);
+        ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_fp32(z, n, prior, n_x, d, splits, partial, s));
+        part_stride = (int64_t)n * n_x;
+        ldp = n_x;
+    } else {
+        ensf::TcGramArgs a;
+        a.zb_hi = h->at<__nv_bfloat16>(L.zb_hi);
+        a.zb_lo = L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
+        a.xb_hi = h->at<__nv_bfloat16>(L.xb_hi);
+        a.xb_lo = L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr;
+        a.n = n;
+        a.n_x = n_x;
+        a.d = d;
+        a.split3 = (h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
+        a.partial = partial;
+        a.partial_cap = L.partial_floats;
+        a.err = h->err();
+        ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_tc(h->tc, a, h->sms, &splits, &part_stride, &ldp, s));
+    }
+    __nv_bfloat16 *wb_hi = nullptr, *wb_lo = nullptr;
+    int ldwb = 0;
+    if (is_tc(h->cfg.wx)) {
+        wb_hi = h->at<__nv_bfloat16>(L.wb_hi);
+        wb_lo = L.wb_lo ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
+        ldwb = (int)round_up(n_x, 8);
+    }
+    ENSF_LAUNCH(h, P_SOFTMAX, s,
+                ensf::launch_softmax_rows(partial, splits, part_stride, ldp, n, n_x, h->at<double>(L.norms),
+                                          c.alpha_d, c.inv_2beta2_d, want_fp32 ? h->at<float>(L.w) : nullptr,
+                                          n_x, wb_hi, wb_lo, ldwb, s));
+    return ENSF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ensf_last_error(void) { return g_last_error; }
+
+const char *ensf_status_string(ensf_status s) {
+    switch (s) {
+        case ENSF_OK: return "ENSF_OK";
+        case ENSF_EINVAL: return "ENSF_EINVAL: invalid argument";
+        case ENSF_ENOMEM: return "ENSF_ENOMEM: workspace too small";
+        case ENSF_ECUDA: return "ENSF_ECUDA: CUDA runtime error";
+        case ENSF_ENUMERIC: return "ENSF_ENUMERIC: non-finite value produced";
+        case ENSF_ETIMEOUT: return "ENSF_ETIMEOUT: bounded device wait expired";
+        case ENSF_EUNSUPPORTED: return "ENSF_EUNSUPPORTED: configuration not supported on this device";
+    }
+    return "unknown ensf_status";
+}
+
+size_t ensf_workspace_bytes(const ensf_config *cfg) {
+    if (!config_ok(cfg)) return 0;
+    return make_layout(cfg).total;
+}
+
+ensf_status ensf_create(const ensf_config *cfg, void *workspace, size_t ws_bytes, ensf_handle **out) {
+    if (!out) return fail(ENSF_EINVAL, "ensf_create: out is NULL");
+    *out = nullptr;
+    if (!config_ok(cfg)) return fail(ENSF_EINVAL, "ensf_create: invalid configuration");
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+        return fail(ENSF_EINVAL, "ensf_create: workspace must be non-NULL and 256-byte aligned");
+    Layout L = make_layout(cfg);
+    if (ws_bytes < L.total)
+        return fail(ENSF_ENOMEM, "ensf_create: workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    int dev = 0;
+    ENSF_CUDA(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    ENSF_CUDA(cudaGetDeviceProperties(&prop, dev));
+    ensf_handle *h = new (std::nothrow) ensf_handle;
+    if (!h) return fail(ENSF_ENOMEM, "ensf_create: host allocation failed");
+    h->cfg = *cfg;
+    h->ws = static_cast<char *>(workspace);
+    h->ws_bytes = ws_bytes;
+    h->L = L;
+    h->sms = prop.multiProcessorCount;
+    h->device = dev;
+    if (is_tc(cfg->gram) || is_tc(cfg->wx)) {
+        if (!(prop.major == 10 && prop.minor == 3)) {
+            delete h;
+            return fail(ENSF_EUNSUPPORTED, "tensor-core precisions need an sm_103 device (found sm_%d%d)",
+                        prop.major, prop.minor);
+        }
+        cudaError_t e = ensf::tc_context_create(&h->tc);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "tc_context_create");
+        }
+    }
+    cudaError_t e = cudaMemset(h->err(), 0, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+        ensf::tc_context_destroy(h->tc);
+        delete h;
+        return cuda_fail(e, "cudaMemset(error word)");
+    }
+    *out = h;
+    return ENSF_OK;
+}
+
+ensf_status ensf_destroy(ensf_handle *h) {
+    if (!h) return fail(ENSF_EINVAL, "ensf_destroy: NULL handle");
+    for (cudaEvent_t e : h->prof.events) cudaEventDestroy(e);
+    ensf::tc_context_destroy(h->tc);
+    delete h;
+    return ENSF_OK;
+}
+
+ensf_status ensf_analysis(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                          const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
+                          const ensf_noise *noise, float *out, void *stream) {
+    if (!h) return fail(ENSF_EINVAL, "ensf_analysis: NULL handle");
+    if (!aligned16(prior) || !aligned16(y) || !aligned16(out))
+        return fail(ENSF_EINVAL, "ensf_analysis: prior, y and out must be non-NULL and 16-byte aligned");
+    if (obs_mask && (reinterpret_cast<uintptr_t>(obs_mask) & 3u))
+        return fail(ENSF_EINVAL, "ensf_analysis: obs_mask must be 4-byte aligned");
+    if (n < 1 || n > h->cfg.max_n) return fail(ENSF_EINVAL, "ensf_analysis: n=%d outside [1, %d]", n, h->cfg.max_n);
+    if (d < 8 || d > h->cfg.max_d || d % 8 != 0)
+        return fail(ENSF_EINVAL, "ensf_analysis: d=%lld must be a multiple of 8 in [8, %lld]", (long long)d,
+                    (long long)h->cfg.max_d);
+    if (K < 1) return fail(ENSF_EINVAL, "ensf_analysis: K=%d < 1", K);
+    if (!(eps > 0.0f && eps < 1.0f)) return fail(ENSF_EINVAL, "ensf_analysis: eps must lie in (0, 1)");
+    if (!(sigma_obs > 0.0f) || !std::isfinite(sigma_obs)) return fail(ENSF_EINVAL, "ensf_analysis: sigma_obs must be > 0");
+    if (obs_op != ENSF_OBS_IDENTITY && obs_op != ENSF_OBS_ARCTAN) return fail(ENSF_EINVAL, "ensf_analysis: bad obs_op");
+    if (!noise) return fail(ENSF_EINVAL, "ensf_analysis: noise is NULL");
+    if (noise->buf && !aligned16(noise->buf)) return fail(ENSF_EINVAL, "ensf_analysis: noise buffer must be 16-byte aligned");
+    if (static_cast<const void *>(prior) == static_cast<const void *>(out))
+        return fail(ENSF_EINVAL, "ensf_analysis: out must not alias prior");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout &L = h->L;
+    const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
+
+    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, h->at<double>(L.norms), s));
+    ENSF_LAUNCH(h, P_INIT, s, ensf::launch_init_particles(out, n, d, noise->buf, noise->seed, noise->offset, s));
+    __nv_bfloat16 *zb_hi = nullptr, *zb_lo = nullptr;
+    if (tc_gram) {
+        zb_hi = h->at<__nv_bfloat16>(L.zb_hi);
+        zb_lo = L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
+        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(prior, n, d, h->at<__nv_bfloat16>(L.xb_hi),
+                                                           L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s));
+        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, zb_hi, zb_lo, d, s));
+    }
+    const int ldt = (int)round_up(n, 8);
+    if (tc_wx)
+        ENSF_LAUNCH(h, P_SPLIT, s,
+                    ensf::launch_split_bf16_transpose(prior, n, d, h->at<__nv_bfloat16>(L.xt_hi),
+                                                      L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) : nullptr, ldt, s));
+    for (int k = 0; k < K; ++k) {
+        ensf::StepCoef c = step_coef(k, K, eps, sigma_obs, obs_op);
+        ensf_status st = gram_softmax(h, out, n, prior, n, d, c, !tc_wx, s);
+        if (st != ENSF_OK) return st;
+        if (!tc_wx) {
+            ENSF_LAUNCH(h, P_WXEM, s,
+                        ensf::launch_wx_em_fp32(h->at<float>(L.w), n, prior, n, n, d, out, y, obs_mask, noise->buf,
+                                                noise->seed, noise->offset, c, s));
+            if (tc_gram) ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, zb_hi, zb_lo, d, s));
+        } else {
+            ensf::TcWxArgs a;
+            a.wb_hi = h->at<__nv_bfloat16>(L.wb_hi);
+            a.wb_lo = L.wb_lo ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
+            a.xt_hi = h->at<__nv_bfloat16>(L.xt_hi);
+            a.xt_lo = L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) : nullptr;
+            a.ldw = ldt;
+            a.n = n;
+            a.d = d;
+            a.z = out;
+            a.zb_hi = zb_hi;
+            a.zb_lo = zb_lo;
+            a.y = y;
+            a.mask = obs_mask;
+            a.noise_buf = noise->buf;
+            a.seed = noise->seed;
+            a.offset = noise->offset;
+            a.coef = c;
+            a.err = h->err();
+            ENSF_LAUNCH(h, P_WXEM, s, ensf::launch_wx_em_tc(h->tc, a, h->sms, s));
+        }
+    }
+    if (h->cfg.flags & ENSF_FLAG_CHECK_FINITE)
+        ENSF_LAUNCH(h, P_CHECK, s, ensf::launch_check_finite(out, (int64_t)n * d, h->err(), s));
+    return ENSF_OK;
+}
+
+ensf_status ensf_weights(ensf_handle *h, const float *z, int n, const float *prior, int n_x, int64_t d,
+                         float t, float eps, float *w, void *stream) {
+    if (!h) return fail(ENSF_EINVAL, "ensf_weights: NULL handle");
+    if (!aligned16(z) || !aligned16(prior) || !aligned16(w))
+        return fail(ENSF_EINVAL, "ensf_weights: z, prior and w must be non-NULL and 16-byte aligned");
+    if (n < 1 || n > h->cfg.max_n || n_x < 1 || n_x > h->cfg.max_n)
+        return fail(ENSF_EINVAL, "ensf_weights: n, n_x must lie in [1, %d]", h->cfg.max_n);
+    if (d < 8 || d > h->cfg.max_d || d % 8 != 0) return fail(ENSF_EINVAL, "ensf_weights: bad d");
+    if (!(t > 0.0f && t <= 1.0f) || !(eps > 0.0f && eps < 1.0f))
+        return fail(ENSF_EINVAL, "ensf_weights: need t in (0, 1] and eps in (0, 1)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout &L = h->L;
+    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n_x, d, h->at<double>(L.norms), s));
+    if (is_tc(h->cfg.gram)) {
+        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(prior, n_x, d, h->at<__nv_bfloat16>(L.xb_hi),
+                                                           L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s));
+        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(z, n, d, h->at<__nv_bfloat16>(L.zb_hi),
+                                                           L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s));
+    }
+    const double td = (double)t, alpha = 1.0 - td * (1.0 - (double)eps);
+    ensf::StepCoef c{};
+    c.alpha_d = alpha;
+    c.inv_2beta2_d = 1.0 / (2.0 * td);
+    // the FP32 weights go to the handle's W scratch, then to the caller
+    ensf_status st = gram_softmax(h, z, n, prior, n_x, d, c, true, s);
+    if (st != ENSF_OK) return st;
+    ENSF_CUDA(cudaMemcpyAsync(w, h->at<float>(L.w), sizeof(float) * (size_t)n * n_x, cudaMemcpyDeviceToDevice, s));
+    return ENSF_OK;
+}
+
+ensf_status ensf_philox_normal(uint64_t seed, uint32_t offset, int k0, int count, int n, int64_t d, float *out,
+                               void *stream) {
+    if (!aligned16(out) || k0 < 0 || count < 1 || n < 1 || d < 4 || d % 4 != 0)
+        return fail(ENSF_EINVAL, "ensf_philox_normal: bad arguments");
+    ENSF_CUDA(ensf::launch_philox_normal(seed, offset, k0, count, n, d, out, static_cast<cudaStream_t>(stream)));
+    return ENSF_OK;
+}
+
+ensf_status ensf_row_norms(const float *x, int n, int64_t d, double *out, void *stream) {
+    if (!aligned16(x) || !out || n < 1 || d < 4 || d % 4 != 0)
+        return fail(ENSF_EINVAL, "ensf_row_norms: bad arguments");
+    ENSF_CUDA(ensf::launch_row_norms(x, n, d, out, static_cast<cudaStream_t>(stream)));
+    return ENSF_OK;
+}
+
+size_t ensf_stats_scratch_bytes(int64_t d) {
+    return d < 1 ? 0 : sizeof(double) * (size_t)ensf::stats_blocks(d);
+}
+
+ensf_status ensf_ensemble_stats(const float *z, int n, int64_t d, const float *truth, double *mean, double *rmse,
+                                void *scratch, void *stream) {
+    if (!z || n < 1 || d < 1 || !scratch || (truth && !rmse))
+        return fail(ENSF_EINVAL, "ensf_ensemble_stats: bad arguments");
+    ENSF_CUDA(ensf::launch_ensemble_stats(z, n, d, truth, mean, rmse, static_cast<double *>(scratch),
+                                          static_cast<cudaStream_t>(stream)));
+    return ENSF_OK;
+}
+
+ensf_status ensf_profile_enable(ensf_handle *h, int on) {
+    if (!h) return fail(ENSF_EINVAL, "ensf_profile_enable: NULL handle");
+    if (on && h->prof.events.empty()) {
+        h->prof.events.resize(2 * kProfPairs);
+        for (cudaEvent_t &e : h->prof.events) ENSF_CUDA(cudaEventCreate(&e));
+    }
+    h->prof.on = on != 0;
+    h->prof.kinds.clear();
+    for (int64_t &c : h->prof.launches) c = 0;
+    h->prof.dropped = 0;
+    return ENSF_OK;
+}
+
+ensf_status ensf_profile_read(ensf_handle *h, ensf_profile_entry *out, int max_entries, int *count) {
+    if (!h || !count || (max_entries > 0 && !out)) return fail(ENSF_EINVAL, "ensf_profile_read: bad arguments");
+    double total[P_COUNT] = {};
+    int64_t timed[P_COUNT] = {};
+    for (size_t p = 0; p < h->prof.kinds.size(); ++p) {
+        ENSF_CUDA(cudaEventSynchronize(h->prof.events[2 * p + 1]));
+        float ms = 0.f;
+        ENSF_CUDA(cudaEventElapsedTime(&ms, h->prof.events[2 * p], h->prof.events[2 * p + 1]));
+        total[h->prof.kinds[p]] += ms;
+        timed[h->prof.kinds[p]]++;
+    }
+    int m = 0;
+    for (int k = 0; k < P_COUNT; ++k) {
+        if (h->prof.launches[k] == 0) continue;
+        if (m < max_entries) {
+            snprintf(out[m].name, sizeof out[m].name, "%s", kProfNames[k]);
+            out[m].launches = h->prof.launches[k];
+            out[m].timed_launches = timed[k];
+            out[m].total_ms = total[k];
+        }
+        ++m;
+    }
+    *count = m;
+    return ENSF_OK;
+}
+
+ensf_status ensf_status_sync(ensf_handle *h, void *stream) {
+    if (!h) return fail(ENSF_EINVAL, "ensf_status_sync: NULL handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int word = 0;
+    ENSF_CUDA(cudaMemcpyAsync(&word, h->err(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    ENSF_CUDA(cudaStreamSynchronize(s));
+    if (word != 0) {
+        ENSF_CUDA(cudaMemsetAsync(h->err(), 0, sizeof(int), s));
+        ENSF_CUDA(cudaStreamSynchronize(s));
+        return fail(static_cast<ensf_status>(word), "device reported %s", ensf_status_string(static_cast<ensf_status>(word)));
+    }
+    return ENSF_OK;
+}
+
+}  // extern "C"

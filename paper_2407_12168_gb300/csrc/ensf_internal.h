@@ -1,0 +1,46 @@
+// ensf_internal.h -- launchers shared between the host runtime and the
+// kernel translation units.  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "ensf_device.cuh"
+
+namespace ensf {
+
+// ---- CUDA-core kernels (ensf_simt.cu) ----------------------------------
+// z[i][c] <- xi[0][i][c] (noise buffer or Philox stream)
+cudaError_t launch_init_particles(float *z, int n, int64_t d, const float *noise_buf,
+                                  uint64_t seed, uint32_t offset, cudaStream_t s);
+cudaError_t launch_philox_normal(uint64_t seed, uint32_t offset, int k0, int count, int n,
+                                 int64_t d, float *out, cudaStream_t s);
+cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s);
+// partial[s][i][j] = sum over slice s of z[i][c] x[j][c]   (FP32 CUDA cores)
+cudaError_t launch_gram_fp32(const float *z, int n, const float *x, int n_x, int64_t d,
+                             int splits, float *partial, cudaStream_t s);
+// logits from `splits` partial Grams (row stride ldp) + FP64 norms, row softmax;
+// writes W FP32 [n][ldw] and, if w_hi != NULL, BF16 W_hi/W_lo [n][ldwb].
+cudaError_t launch_softmax_rows(const float *partial, int splits, int64_t part_stride, int ldp,
+                                int n, int n_x, const double *norms, double alpha,
+                                double inv_2beta2, float *w, int ldw, __nv_bfloat16 *w_hi,
+                                __nv_bfloat16 *w_lo, int ldwb, cudaStream_t s);
+// z <- EM step with u = W X computed on FP32 CUDA cores, fused epilogue.
+cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, int n_x, int64_t d,
+                              float *z, const float *y, const uint8_t *mask,
+                              const float *noise_buf, uint64_t seed, uint32_t offset,
+                              const StepCoef &c, cudaStream_t s);
+// FP32 -> (hi, lo) BF16 split, row-major copy with output row stride ldo
+cudaError_t launch_split_bf16(const float *x, int rows, int64_t cols, __nv_bfloat16 *hi,
+                              __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s);
+// Transposed split: xT_hi[c][j] = bf16(x[j][c]), xT_lo likewise (ldo = row stride of xT)
+cudaError_t launch_split_bf16_transpose(const float *x, int rows, int64_t cols,
+                                        __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ldo,
+                                        cudaStream_t s);
+cudaError_t launch_check_finite(const float *z, int64_t count, int *err_word, cudaStream_t s);
+cudaError_t launch_ensemble_stats(const float *z, int n, int64_t d, const float *truth,
+                                  double *mean, double *rmse, double *scratch, cudaStream_t s);
+int stats_blocks(int64_t d);
+
+}  // namespace ensf

@@ -1,0 +1,403 @@
+// ensf_simt.cu -- CUDA-core kernels of the EnSF analysis step:
+//   * FP64 squared row norms |x_j|^2 (used in the expanded logit)
+//   * the counter-based Gaussian noise stream (Philox4x32-10 + Box-Muller)
+//   * the plain FP32 path: Gram Z X^T, row softmax, W X with the fused
+//     Euler-Maruyama epilogue
+//   * FP32 -> BF16 hi/lo splits feeding the tensor-core path
+//   * finite-value scan and FP64 ensemble mean / RMSE
+#include <cfloat>
+#include <cmath>
+
+#include "ensf_internal.h"
+
+namespace ensf {
+namespace {
+
+constexpr int kTile = 64;    // output tile edge of the CUDA-core GEMMs
+constexpr int kTileK = 16;   // reduction depth per shared-memory stage
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// ---------------------------------------------------------------------------
+// |x_j|^2 in FP64: one block per row, float4 loads, fixed-order tree reduce.
+__global__ void __launch_bounds__(256) k_row_norms(const float *__restrict__ x, int64_t d,
+                                                   double *__restrict__ out) {
+    const float *row = x + (int64_t)blockIdx.x * d;
+    double acc = 0.0;
+    for (int64_t c = (int64_t)threadIdx.x * 4; c < d; c += 256 * 4) {
+        float4 v = ld4(row + c);
+        acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// ---------------------------------------------------------------------------
+// out[kk][i][c] = xi[k0 + kk][i][c]; one thread per 4 consecutive columns.
+__global__ void k_philox_normal(uint64_t seed, uint32_t offset, int k0, int n, int64_t d,
+                                float *__restrict__ out) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // column quad
+    int i = blockIdx.y;
+    int kk = blockIdx.z;
+    if (q * 4 >= d) return;
+    float4 v = noise4(seed, offset, k0 + kk, i, q);
+    *reinterpret_cast<float4 *>(out + ((int64_t)kk * n + i) * d + q * 4) = v;
+}
+
+// z[i][c] <- xi[0][i][c]
+__global__ void k_init_particles(float *__restrict__ z, int n, int64_t d,
+                                 const float *__restrict__ noise_buf, uint64_t seed,
+                                 uint32_t offset) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (q * 4 >= d) return;
+    int64_t off = (int64_t)i * d + q * 4;
+    float4 v = noise_buf ? ld4(noise_buf + off) : noise4(seed, offset, 0, i, q);
+    *reinterpret_cast<float4 *>(z + off) = v;
+}
+
+// ---------------------------------------------------------------------------
+// partial[s][i][j] = sum_{c in slice s} z[i][c] x[j][c], FP32 FMA.
+// 64x64 output tile per block, 4x4 per thread, reduction staged 16 deep.
+__global__ void __launch_bounds__(256)
+k_gram_fp32(const float *__restrict__ z, int n, const float *__restrict__ x, int n_x, int64_t d,
+            int64_t slice_len, float *__restrict__ partial) {
+    __shared__ __align__(16) float As[kTileK][kTile + 4];
+    __shared__ __align__(16) float Bs[kTileK][kTile + 4];
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
+    const int64_t c_begin = (int64_t)blockIdx.z * slice_len;
+    const int64_t c_end = min(d, c_begin + slice_len);
+    const int tx = tid & 15, ty = tid >> 4;
+    const int lr = tid >> 2, lk = (tid & 3) * 4;
+    float acc[4][4] = {};
+    for (int64_t c0 = c_begin; c0 < c_end; c0 += kTileK) {
+        const int64_t c = c0 + lk;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (i0 + lr < n && c < c_end) a = ld4(z + (int64_t)(i0 + lr) * d + c);
+        if (j0 + lr < n_x && c < c_end) b = ld4(x + (int64_t)(j0 + lr) * d + c);
+        As[lk + 0][lr] = a.x; As[lk + 1][lr] = a.y; As[lk + 2][lr] = a.z; As[lk + 3][lr] = a.w;
+        Bs[lk + 0][lr] = b.x; Bs[lk + 1][lr] = b.y; Bs[lk + 2][lr] = b.z; Bs[lk + 3][lr] = b.w;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kTileK; ++kk) {
+            float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
+        }
+        __syncthreads();
+    }
+    float *out = partial + (int64_t)blockIdx.z * n * n_x;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int i = i0 + ty * 4 + r;
+        if (i >= n) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int j = j0 + tx * 4 + q;
+            if (j < n_x) out[(int64_t)i * n_x + j] = acc[r][q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row softmax of the logits  l_ij = (2 alpha G_ij - alpha^2 |x_j|^2) / (2 beta^2)
+// (Eq. 12 expanded; the row constant -|z_i|^2/(2 beta^2) cancels in Eq. 16).
+__global__ void __launch_bounds__(256)
+k_softmax_rows(const float *__restrict__ partial, int splits, int64_t part_stride, int ldp,
+               int n_x, const double *__restrict__ norms, double alpha, double inv_2beta2,
+               float *__restrict__ w, int ldw, __nv_bfloat16 *__restrict__ w_hi,
+               __nv_bfloat16 *__restrict__ w_lo, int ldwb) {
+    extern __shared__ double lg[];
+    __shared__ double red[256];
+    const int i = blockIdx.x, tid = threadIdx.x;
+    double lmax = -DBL_MAX;
+    for (int j = tid; j < n_x; j += 256) {
+        double g = 0.0;
+        for (int s = 0; s < splits; ++s) g += (double)partial[s * part_stride + (int64_t)i * ldp + j];
+        double l = (2.0 * alpha * g - alpha * alpha * norms[j]) * inv_2beta2;
+        lg[j] = l;
+        lmax = fmax(lmax, l);
+    }
+    red[tid] = lmax;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
+        __syncthreads();
+    }
+    const double m = red[0];
+    __syncthreads();
+    double sum = 0.0;
+    for (int j = tid; j < n_x; j += 256) {
+        double e = (double)expf((float)(lg[j] - m));
+        lg[j] = e;
+        sum += e;
+    }
+    red[tid] = sum;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s) red[tid] += red[tid + s];
+        __syncthreads();
+    }
+    const double inv = 1.0 / red[0];
+    for (int j = tid; j < n_x; j += 256) {
+        float wv = (float)(lg[j] * inv);
+        if (w) w[(int64_t)i * ldw + j] = wv;
+        if (w_hi) {
+            __nv_bfloat16 hi = __float2bfloat16_rn(wv);
+            w_hi[(int64_t)i * ldwb + j] = hi;
+            if (w_lo) w_lo[(int64_t)i * ldwb + j] = __float2bfloat16_rn(wv - __bfloat162float(hi));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// u = W X on FP32 CUDA cores (64 particles x 64 state columns per block),
+// fused with the score and the Euler-Maruyama update of Eq. 7 / Eq. 17.
+__global__ void __launch_bounds__(256)
+k_wx_em_fp32(const float *__restrict__ w, int ldw, const float *__restrict__ x, int n, int n_x,
+             int64_t d, float *__restrict__ z, const float *__restrict__ y,
+             const uint8_t *__restrict__ mask, const float *__restrict__ noise_buf, uint64_t seed,
+             uint32_t offset, StepCoef cf) {
+    __shared__ __align__(16) float Ws[kTileK][kTile + 4];  // Ws[j][i]
+    __shared__ __align__(16) float Xs[kTileK][kTile + 4];  // Xs[j][c]
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.y * kTile;
+    const int64_t c0 = (int64_t)blockIdx.x * kTile;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int wr = tid >> 2, wk = (tid & 3) * 4;    // W loader: row, 4 consecutive j
+    const int xr = tid >> 4, xc = (tid & 15) * 4;   // X loader: j row, 4 consecutive c
+    float acc[4][4] = {};
+    for (int j0 = 0; j0 < n_x; j0 += kTileK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int j = j0 + wk + q;
+            Ws[wk + q][wr] = (i0 + wr < n && j < n_x) ? w[(int64_t)(i0 + wr) * ldw + j] : 0.f;
+        }
+        float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j0 + xr < n_x && c0 + xc < d) xv = ld4(x + (int64_t)(j0 + xr) * d + c0 + xc);
+        *reinterpret_cast<float4 *>(&Xs[xr][xc]) = xv;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kTileK; ++kk) {
+            float4 av = *reinterpret_cast<const float4 *>(&Ws[kk][ty * 4]);
+            float4 bv = *reinterpret_cast<const float4 *>(&Xs[kk][tx * 4]);
+            float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
+        }
+        __syncthreads();
+    }
+    const int64_t c = c0 + tx * 4;
+    if (c >= d) return;
+    const float4 yv = ld4(y + c);
+    uchar4 mv = make_uchar4(1, 1, 1, 1);
+    if (mask) mv = *reinterpret_cast<const uchar4 *>(mask + c);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty * 4 + r;
+        if (i >= n) continue;
+        float *zp = z + (int64_t)i * d + c;
+        float4 zv = ld4(zp);
+        float4 xi = noise_buf ? ld4(noise_buf + ((int64_t)(cf.k + 1) * n + i) * d + c)
+                              : noise4(seed, offset, cf.k + 1, i, c >> 2);
+        float4 o;
+        o.x = em_update(cf, zv.x, acc[r][0], mv.x ? lik_score(cf.obs_op, zv.x, yv.x, cf.inv_r) : 0.f, xi.x);
+        o.y = em_update(cf, zv.y, acc[r][1], mv.y ? lik_score(cf.obs_op, zv.y, yv.y, cf.inv_r) : 0.f, xi.y);
+        o.z = em_update(cf, zv.z, acc[r][2], mv.z ? lik_score(cf.obs_op, zv.z, yv.z, cf.inv_r) : 0.f, xi.z);
+        o.w = em_update(cf, zv.w, acc[r][3], mv.w ? lik_score(cf.obs_op, zv.w, yv.w, cf.inv_r) : 0.f, xi.w);
+        *reinterpret_cast<float4 *>(zp) = o;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x = hi + lo with hi = bf16(x), lo = bf16(x - hi); row-major, out stride ldo.
+__global__ void k_split_bf16(const float *__restrict__ x, int64_t cols, __nv_bfloat16 *__restrict__ hi,
+                             __nv_bfloat16 *__restrict__ lo, int64_t ldo) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int r = blockIdx.y;
+    if (q * 4 >= cols) return;
+    float4 v = ld4(x + (int64_t)r * cols + q * 4);
+    float vv[4] = {v.x, v.y, v.z, v.w};
+    __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        h[e] = __float2bfloat16_rn(vv[e]);
+        l[e] = __float2bfloat16_rn(vv[e] - __bfloat162float(h[e]));
+    }
+    *reinterpret_cast<uint2 *>(hi + (int64_t)r * ldo + q * 4) = *reinterpret_cast<uint2 *>(h);
+    if (lo) *reinterpret_cast<uint2 *>(lo + (int64_t)r * ldo + q * 4) = *reinterpret_cast<uint2 *>(l);
+}
+
+// Transposed split through a 32x32 shared tile: xT[c][j] from x[j][c].
+__global__ void k_split_bf16_t(const float *__restrict__ x, int rows, int64_t cols,
+                               __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+                               int64_t ldo) {
+    __shared__ float tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        int j = j0 + r;
+        int64_t c = c0 + tx;
+        tile[r][tx] = (j < rows && c < cols) ? x[(int64_t)j * cols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        int64_t c = c0 + r;
+        int j = j0 + tx;
+        if (c < cols && j < rows) {
+            float v = tile[tx][r];
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            hi[c * ldo + j] = h;
+            if (lo) lo[c * ldo + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_check_finite(const float *__restrict__ z, int64_t count, int *err_word) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < count; i += stride) bad |= !isfinite(z[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(err_word, 0, 4 /*ENSF_ENUMERIC*/);
+}
+
+// FP64 column means over the n rows and per-block partial sums of (mean - truth)^2.
+__global__ void __launch_bounds__(256)
+k_stats_mean(const float *__restrict__ z, int n, int64_t d, const float *__restrict__ truth,
+             double *__restrict__ mean, double *__restrict__ block_sq) {
+    int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    double sq = 0.0;
+    if (c < d) {
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) acc += (double)z[(int64_t)i * d + c];
+        double m = acc / (double)n;
+        if (mean) mean[c] = m;
+        if (truth) {
+            double e = m - (double)truth[c];
+            sq = e * e;
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = sq;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_sq[blockIdx.x] = red[0];
+}
+
+__global__ void k_stats_rmse(const double *__restrict__ block_sq, int blocks, int64_t d,
+                             double *__restrict__ rmse) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < blocks; b += 256) acc += block_sq[b];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *rmse = sqrt(red[0] / (double)d);
+}
+
+}  // namespace
+
+// ===========================================================================
+cudaError_t launch_init_particles(float *z, int n, int64_t d, const float *noise_buf,
+                                  uint64_t seed, uint32_t offset, cudaStream_t s) {
+    dim3 grid((unsigned)((d / 4 + 255) / 256), (unsigned)n);
+    k_init_particles<<<grid, 256, 0, s>>>(z, n, d, noise_buf, seed, offset);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox_normal(uint64_t seed, uint32_t offset, int k0, int count, int n,
+                                 int64_t d, float *out, cudaStream_t s) {
+    dim3 grid((unsigned)((d / 4 + 255) / 256), (unsigned)n, (unsigned)count);
+    k_philox_normal<<<grid, 256, 0, s>>>(seed, offset, k0, n, d, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s) {
+    k_row_norms<<<n, 256, 0, s>>>(x, d, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_fp32(const float *z, int n, const float *x, int n_x, int64_t d, int splits,
+                             float *partial, cudaStream_t s) {
+    int64_t slice = (d + splits - 1) / splits;
+    slice = (slice + kTileK - 1) / kTileK * kTileK;
+    dim3 grid((unsigned)((n_x + kTile - 1) / kTile), (unsigned)((n + kTile - 1) / kTile), (unsigned)splits);
+    k_gram_fp32<<<grid, 256, 0, s>>>(z, n, x, n_x, d, slice, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_softmax_rows(const float *partial, int splits, int64_t part_stride, int ldp, int n,
+                                int n_x, const double *norms, double alpha, double inv_2beta2,
+                                float *w, int ldw, __nv_bfloat16 *w_hi, __nv_bfloat16 *w_lo, int ldwb,
+                                cudaStream_t s) {
+    size_t smem = sizeof(double) * (size_t)n_x;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_softmax_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_softmax_rows<<<n, 256, smem, s>>>(partial, splits, part_stride, ldp, n_x, norms, alpha, inv_2beta2,
+                                        w, ldw, w_hi, w_lo, ldwb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, int n_x, int64_t d,
+                              float *z, const float *y, const uint8_t *mask, const float *noise_buf,
+                              uint64_t seed, uint32_t offset, const StepCoef &c, cudaStream_t s) {
+    dim3 grid((unsigned)((d + kTile - 1) / kTile), (unsigned)((n + kTile - 1) / kTile));
+    k_wx_em_fp32<<<grid, 256, 0, s>>>(w, ldw, x, n, n_x, d, z, y, mask, noise_buf, seed, offset, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float *x, int rows, int64_t cols, __nv_bfloat16 *hi,
+                              __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s) {
+    dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)rows);
+    k_split_bf16<<<grid, 256, 0, s>>>(x, cols, hi, lo, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16_transpose(const float *x, int rows, int64_t cols, __nv_bfloat16 *hi,
+                                        __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    k_split_bf16_t<<<grid, dim3(32, 8), 0, s>>>(x, rows, cols, hi, lo, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const float *z, int64_t count, int *err_word, cudaStream_t s) {
+    k_check_finite<<<1024, 256, 0, s>>>(z, count, err_word);
+    return cudaGetLastError();
+}
+
+int stats_blocks(int64_t d) { return (int)((d + 255) / 256); }
+
+cudaError_t launch_ensemble_stats(const float *z, int n, int64_t d, const float *truth, double *mean,
+                                  double *rmse, double *scratch, cudaStream_t s) {
+    int blocks = stats_blocks(d);
+    k_stats_mean<<<blocks, 256, 0, s>>>(z, n, d, truth, mean, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !truth || !rmse) return e;
+    k_stats_rmse<<<1, 256, 0, s>>>(scratch, blocks, d, rmse);
+    return cudaGetLastError();
+}
+
+}  // namespace ensf

@@ -1,0 +1,250 @@
+"""Python binding of the EnSF C ABI (``include/ensf.h``).
+
+Argument marshalling only: every step of the analysis runs in the CUDA
+library ``_lib/libensf.so``.  PyTorch provides device memory and the current
+stream.  There is no CPU fallback: if the library cannot be built or loaded,
+or no CUDA device is present, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from typing import Optional
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = range(7)
+OBS_IDENTITY, OBS_ARCTAN = 0, 1
+PREC_FP32, PREC_SPLIT_BF16X3, PREC_BF16 = 0, 1, 2
+FLAG_CHECK_FINITE = 1
+
+PRECISIONS = {"fp32": PREC_FP32, "split": PREC_SPLIT_BF16X3, "bf16": PREC_BF16}
+
+
+class EnsfConfig(ctypes.Structure):
+    _fields_ = [("max_n", ctypes.c_int), ("max_d", ctypes.c_int64), ("gram", ctypes.c_int),
+                ("wx", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+class EnsfNoise(ctypes.Structure):
+    _fields_ = [("buf", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("offset", ctypes.c_uint32)]
+
+
+class EnsfProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+class EnsfError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+# (name, restype, argtypes) of every exported entry point
+_SIGNATURES = [
+    ("ensf_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(EnsfConfig)]),
+    ("ensf_create", ctypes.c_int, [ctypes.POINTER(EnsfConfig), ctypes.c_void_p, ctypes.c_size_t,
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    ("ensf_analysis", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
+                                     ctypes.c_int, ctypes.c_float, ctypes.POINTER(EnsfNoise),
+                                     ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_philox_normal", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_row_norms", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    ("ensf_stats_scratch_bytes", ctypes.c_size_t, [ctypes.c_int64]),
+    ("ensf_ensemble_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    ("ensf_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("ensf_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EnsfProfileEntry), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    ("ensf_status_sync", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("ensf_last_error", ctypes.c_char_p, []),
+    ("ensf_destroy", ctypes.c_int, [ctypes.c_void_p]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load (building first if needed) the CUDA library and declare signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_needed else _build.LIB
+        lib = ctypes.CDLL(path)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != OK:
+        lib = load()
+        raise EnsfError(status, where, lib.ensf_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the EnSF library needs a CUDA device; none is available")
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Filter:
+    """An EnSF handle plus its device workspace (a torch uint8 tensor).
+
+    ``gram`` and ``wx`` choose the arithmetic of the Gram Z X^T and of the
+    weighted sum W X: ``"fp32"`` (CUDA cores), ``"split"`` (BF16x3 on tensor
+    cores) or ``"bf16"`` (one BF16 product on tensor cores)."""
+
+    def __init__(self, max_n: int, max_d: int, gram: str = "fp32", wx: str = "fp32",
+                 check_finite: bool = False):
+        torch = _torch()
+        lib = load()
+        self.cfg = EnsfConfig(int(max_n), int(max_d), PRECISIONS[gram], PRECISIONS[wx],
+                              FLAG_CHECK_FINITE if check_finite else 0)
+        nbytes = lib.ensf_workspace_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0:
+            raise ValueError("invalid EnSF configuration")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        _check(lib.ensf_create(ctypes.byref(self.cfg), ctypes.c_void_p(aligned), nbytes, ctypes.byref(h)),
+               "ensf_create")
+        self._h = h
+        self.gram, self.wx = gram, wx
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ensf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def analysis(self, prior, y, mask, sigma_obs: float, K: int, eps: float, obs_op: int = OBS_IDENTITY,
+                 seed: int = 0, offset: int = 0, noise=None, out=None, stream=None):
+        """Run the analysis step; returns ``out`` [n][d] (allocated if None)."""
+        torch = _torch()
+        _dev(prior, torch.float32, "prior")
+        n, d = prior.shape
+        _dev(y, torch.float32, "y")
+        if mask is not None:
+            _dev(mask, torch.uint8, "mask")
+        if noise is not None:
+            _dev(noise, torch.float32, "noise")
+            if tuple(noise.shape) != (K + 1, n, d):
+                raise ValueError(f"noise must have shape {(K + 1, n, d)}")
+        if out is None:
+            out = torch.empty_like(prior)
+        _dev(out, torch.float32, "out")
+        nz = EnsfNoise(noise.data_ptr() if noise is not None else None, int(seed) & (2 ** 64 - 1),
+                       int(offset) & 0xFFFFFFFF)
+        st = load().ensf_analysis(self._h, prior.data_ptr(), n, d, y.data_ptr(),
+                                  mask.data_ptr() if mask is not None else None, int(obs_op),
+                                  float(sigma_obs), int(K), float(eps), ctypes.byref(nz), out.data_ptr(),
+                                  _stream_ptr(stream))
+        _check(st, "ensf_analysis")
+        return out
+
+    def weights(self, z, prior, t: float, eps: float, stream=None):
+        """Weights w_ij of Eq. 16 at pseudo-time t; returns [n][n_x] FP32."""
+        torch = _torch()
+        _dev(z, torch.float32, "z")
+        _dev(prior, torch.float32, "prior")
+        n, d = z.shape
+        n_x = prior.shape[0]
+        w = torch.empty((n, n_x), dtype=torch.float32, device=z.device)
+        _check(load().ensf_weights(self._h, z.data_ptr(), n, prior.data_ptr(), n_x, d, float(t), float(eps),
+                                   w.data_ptr(), _stream_ptr(stream)), "ensf_weights")
+        return w
+
+    def profile_enable(self, on: bool = True) -> None:
+        _check(load().ensf_profile_enable(self._h, 1 if on else 0), "ensf_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kind: (launches, timed_launches, total_ms)} since the last enable."""
+        arr = (EnsfProfileEntry * 16)()
+        cnt = ctypes.c_int()
+        _check(load().ensf_profile_read(self._h, arr, 16, ctypes.byref(cnt)), "ensf_profile_read")
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].timed_launches, arr[i].total_ms)
+                for i in range(min(cnt.value, 16))}
+
+    def status_sync(self, stream=None) -> int:
+        return int(load().ensf_status_sync(self._h, _stream_ptr(stream)))
+
+
+def philox_normal(seed: int, offset: int, k0: int, count: int, n: int, d: int, stream=None):
+    torch = _torch()
+    out = torch.empty((count, n, d), dtype=torch.float32, device="cuda")
+    _check(load().ensf_philox_normal(int(seed) & (2 ** 64 - 1), int(offset), int(k0), int(count), int(n), int(d),
+                                     out.data_ptr(), _stream_ptr(stream)), "ensf_philox_normal")
+    return out
+
+
+def row_norms(x, stream=None):
+    torch = _torch()
+    _dev(x, torch.float32, "x")
+    out = torch.empty(x.shape[0], dtype=torch.float64, device=x.device)
+    _check(load().ensf_row_norms(x.data_ptr(), x.shape[0], x.shape[1], out.data_ptr(), _stream_ptr(stream)),
+           "ensf_row_norms")
+    return out
+
+
+def ensemble_stats(z, truth: Optional[object] = None, stream=None):
+    """FP64 ensemble mean [d] and, with ``truth``, the RMSE of the mean."""
+    torch = _torch()
+    _dev(z, torch.float32, "z")
+    n, d = z.shape
+    lib = load()
+    scratch = torch.empty(lib.ensf_stats_scratch_bytes(d) // 8 + 1, dtype=torch.float64, device=z.device)
+    mean = torch.empty(d, dtype=torch.float64, device=z.device)
+    rmse = torch.empty(1, dtype=torch.float64, device=z.device)
+    if truth is not None:
+        _dev(truth, torch.float32, "truth")
+    _check(lib.ensf_ensemble_stats(z.data_ptr(), n, d, truth.data_ptr() if truth is not None else None,
+                                   mean.data_ptr(), rmse.data_ptr() if truth is not None else None,
+                                   scratch.data_ptr(), _stream_ptr(stream)), "ensf_ensemble_stats")
+    return mean, (rmse if truth is not None else None)
+
+
+# (gram, wx, tolerance) combinations exercised by the package smoke check
+SMOKE_PATHS = [("fp32", "fp32", 1e-4)]

@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 CPU
+oracle on the same seeded inputs, element by element (tolerances and the
+near-tie clause are documented in parity_util)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_2407_12168_gb300 import inputs
+from tests.parity_util import TOL_BF16, TOL_FP32, compare_members, conditioning, describe, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+PATHS = {
+    # name: (gram, wx, tolerance)
+    "fp32": ("fp32", "fp32", TOL_FP32),
+}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _gpu_analysis(p, gram="fp32", wx="fp32", noise_buf=None, filt=None):
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    f = filt or ensf.Filter(p.n, p.d, gram=gram, wx=wx, check_finite=True)
+    prior = torch.from_numpy(p.prior).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    mask = torch.from_numpy(p.mask).cuda() if p.mask is not None else None
+    nb = torch.from_numpy(noise_buf).cuda() if noise_buf is not None else None
+    out = f.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed, offset=p.offset, noise=nb)
+    assert f.status_sync() == 0
+    return out.cpu().numpy()
+
+
+# ------------------------------------------------------------------ noise ---
+def test_philox_stream_matches_oracle():
+    from paper_2407_12168_gb300 import ensf
+    seed, offset = 0x1234_5678_9ABC_DEF0, 7
+    out = ensf.philox_normal(seed, offset, k0=3, count=2, n=3, d=1000).cpu().numpy()
+    for kk in range(2):
+        for i in range(3):
+            ref = o.noise(seed, offset, 3 + kk, i, 1000)
+            np.testing.assert_allclose(out[kk, i], ref, rtol=2e-6, atol=2e-6)
+
+
+def test_row_norms_fp64():
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    x = np.random.default_rng(0).standard_normal((37, 1032)).astype(np.float32)
+    got = ensf.row_norms(torch.from_numpy(x).cuda()).cpu().numpy()
+    np.testing.assert_allclose(got, np.sum(x.astype(np.float64) ** 2, axis=1), rtol=1e-13)
+
+
+def test_ensemble_stats_fp64():
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    g = np.random.default_rng(1)
+    z = g.standard_normal((13, 5000)).astype(np.float32)
+    truth = g.standard_normal(5000).astype(np.float32)
+    mean, rmse = ensf.ensemble_stats(torch.from_numpy(z).cuda(), torch.from_numpy(truth).cuda())
+    ref_mean, ref_rmse = o.mean_rmse(z, truth)
+    np.testing.assert_allclose(mean.cpu().numpy(), ref_mean, rtol=1e-12, atol=1e-14)
+    assert float(rmse.item()) == pytest.approx(ref_rmse, rel=1e-12)
+
+
+# ---------------------------------------------------------------- weights ---
+@pytest.mark.parametrize("path", list(PATHS))
+@pytest.mark.parametrize("n,n_x,d", [(1, 1, 8), (3, 5, 72), (20, 20, 1296), (70, 33, 4104)])
+def test_weights_match_oracle(path, n, n_x, d):
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    gram, wx, _ = PATHS[path]
+    g = np.random.default_rng(n * 1000 + d)
+    X = (g.standard_normal((n_x, d)) * 0.5 + 0.2).astype(np.float32)
+    f = ensf.Filter(max(n, n_x), d, gram=gram, wx=wx)
+    for t in [1.0, 0.5, 0.1, 0.02]:
+        s = o.schedule(t, 0.05)
+        # particles near the forecast members so that the weights are not one-hot
+        Z = (s["alpha"] * X[g.integers(0, n_x, n)] + np.sqrt(t) * 0.05 * g.standard_normal((n, d)))
+        Z = Z.astype(np.float32)
+        w = f.weights(torch.from_numpy(Z).cuda(), torch.from_numpy(X).cuda(), t, 0.05).cpu().numpy()
+        for i in range(n):
+            ref, logit = o.weights(X, Z[i], s["alpha"], s["beta2"])
+            gap = np.sort(logit)[-1] - np.sort(logit)[-2] if n_x > 1 else np.inf
+            assert abs(w[i].sum() - 1.0) < 1e-5
+            if gap > 1e-2:
+                np.testing.assert_allclose(w[i], ref, atol=2e-4)
+
+
+# --------------------------------------------------------------- analysis ---
+SMALL = [
+    # (seed, n, grid, layers, K, obs_op, obs_frac, sigma)
+    (11, 1, 2, 2, 6, 0, 1.0, 1.0),       # d = 8, N = 1
+    (12, 2, 6, 2, 8, 1, 0.5, 0.3),       # d = 72: one full tile + ragged tail
+    (13, 3, 36, 1, 10, 0, 0.25, 0.5),    # d = 1296
+    (14, 20, 64, 2, 10, 0, 1.0, 1.0),    # the 64x64x2 grid, 10 steps
+    (15, 33, 36, 1, 12, 1, 0.25, 0.1),   # N not a tile multiple, arctan
+    (16, 70, 44, 1, 10, 1, 0.6, 0.2),    # N spans two 64-row tiles, d = 1936
+]
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+@pytest.mark.parametrize("case", SMALL, ids=[f"n{c[1]}-d{c[3] * c[2] ** 2}" for c in SMALL])
+@pytest.mark.parametrize("noise_mode", ["philox", "buffer"])
+def test_analysis_small_matches_oracle(path, case, noise_mode):
+    seed, n, grid, layers, K, op, frac, sigma = case
+    gram, wx, tol = PATHS[path]
+    p = inputs.small_case(seed=seed, n=n, grid=grid, layers=layers, K=K, obs_op=op, obs_frac=frac,
+                          sigma_obs=sigma)
+    nb = inputs.noise_buffer(seed, K, n, p.d) if noise_mode == "buffer" else None
+    ref = run_oracle(p, noise_buf=nb)
+    cond = conditioning(p, ref, noise_buf=nb, prec=wx)
+    got = _gpu_analysis(p, gram, wx, noise_buf=nb)
+    rel, tie, bad = compare_members(got, ref, cond, tol)
+    assert not bad.any(), describe(rel, tie, bad)
+    assert tie.sum() <= max(1, n // 10), describe(rel, tie, bad)
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_analysis_plain_64_full(path):
+    """The paper's 64x64x2, N = 20, H = I, R = I setup, all K = 100 steps."""
+    gram, wx, tol = PATHS[path]
+    p = inputs.plain_64()
+    ref = run_oracle(p)
+    cond = conditioning(p, ref, prec=wx)
+    got = _gpu_analysis(p, gram, wx)
+    rel, tie, bad = compare_members(got, ref, cond, tol)
+    assert not bad.any(), describe(rel, tie, bad)
+    assert tie.sum() == 0, describe(rel, tie, bad)
+    _, rmse_ref = o.mean_rmse(ref, p.truth)
+    _, rmse_gpu = o.mean_rmse(got, p.truth)
+    assert rmse_gpu == pytest.approx(rmse_ref, rel=1e-2)
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_analysis_sparse_arctan_128_rows(path):
+    """d = 2x128x128, N = 128, 25 % arctan observations: 12 sampled rows
+    (rows are independent given the forecast ensemble, so the oracle is exact
+    on them)."""
+    gram, wx, tol = PATHS[path]
+    p = inputs.sparse_arctan_128()
+    rows = np.array([0, 5, 17, 33, 64, 77, 90, 101, 111, 120, 126, 127])
+    ref = run_oracle(p, rows=rows)
+    cond = conditioning(p, ref, rows=rows, prec=wx)
+    got = _gpu_analysis(p, gram, wx)[rows]
+    rel, tie, bad = compare_members(got, ref, cond, tol)
+    assert not bad.any(), describe(rel, tie, bad)
+    assert tie.sum() <= 1, describe(rel, tie, bad)
+
+
+def test_analysis_is_deterministic():
+    p = inputs.small_case(seed=21, n=33, grid=36, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.2)
+    a = _gpu_analysis(p)
+    b = _gpu_analysis(p)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_nonfinite_input_is_reported():
+    """A NaN in the forecast ensemble propagates into the particles; with the
+    finite check on, ensf_status_sync returns ENSF_ENUMERIC."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    p = inputs.small_case(seed=22, n=4, grid=8, K=3)
+    prior = p.prior.copy()
+    prior[1, 5] = np.nan
+    f = ensf.Filter(p.n, p.d, check_finite=True)
+    f.analysis(torch.from_numpy(prior).cuda(), torch.from_numpy(p.y).cuda(), None, p.sigma_obs, p.K, p.eps,
+               seed=p.seed)
+    assert f.status_sync() == ensf.ENUMERIC
+    assert f.status_sync() == 0  # the error word is cleared once read
+
+
+def test_invalid_arguments_raise():
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    f = ensf.Filter(8, 64)
+    x = torch.zeros((4, 64), device="cuda")
+    y = torch.zeros(64, device="cuda")
+    with pytest.raises(ensf.EnsfError):
+        f.analysis(x, y, None, 0.0, 3, 0.05)
+    with pytest.raises(ensf.EnsfError):
+        f.analysis(torch.zeros((9, 64), device="cuda"), y, None, 1.0, 3, 0.05)
+    with pytest.raises(ensf.EnsfError):
+        f.analysis(x, y, None, 1.0, 3, 0.05, out=x)
