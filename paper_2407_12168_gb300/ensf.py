@@ -247,4 +247,4 @@ def ensemble_stats(z, truth: Optional[object] = None, stream=None):
 
 
 # (gram, wx, tolerance) combinations exercised by the package smoke check
-SMOKE_PATHS = [("fp32", "fp32", 1e-4)]
+SMOKE_PATHS = [("fp32", "fp32", 1e-4), ("split", "split", 1e-4), ("split", "bf16", 1e-2)]

@@ -13,6 +13,8 @@ pytestmark = pytest.mark.gpu
 PATHS = {
     # name: (gram, wx, tolerance)
     "fp32": ("fp32", "fp32", TOL_FP32),
+    "split": ("split", "split", TOL_FP32),
+    "split-bf16": ("split", "bf16", TOL_BF16),
 }
 
 
@@ -90,14 +92,18 @@ def test_weights_match_oracle(path, n, n_x, d):
 
 
 # --------------------------------------------------------------- analysis ---
+# Explicit Euler-Maruyama is stable on the likelihood term only while
+# dt * sigma^2(t) * h(t) / sigma_obs^2 stays below 2, so the short K of these
+# cases comes with sigma_obs large enough (sigma_obs^2 >= 0.6 / K).
 SMALL = [
     # (seed, n, grid, layers, K, obs_op, obs_frac, sigma)
     (11, 1, 2, 2, 6, 0, 1.0, 1.0),       # d = 8, N = 1
     (12, 2, 6, 2, 8, 1, 0.5, 0.3),       # d = 72: one full tile + ragged tail
     (13, 3, 36, 1, 10, 0, 0.25, 0.5),    # d = 1296
     (14, 20, 64, 2, 10, 0, 1.0, 1.0),    # the 64x64x2 grid, 10 steps
-    (15, 33, 36, 1, 12, 1, 0.25, 0.1),   # N not a tile multiple, arctan
-    (16, 70, 44, 1, 10, 1, 0.6, 0.2),    # N spans two 64-row tiles, d = 1936
+    (15, 33, 36, 1, 12, 1, 0.25, 0.3),   # N not a tile multiple, arctan
+    (16, 70, 44, 1, 10, 1, 0.6, 0.4),    # N spans two 64-row tiles, d = 1936
+    (17, 130, 16, 2, 8, 0, 1.0, 0.5),    # N spans two 128-row tiles, d = 512
 ]
 
 
