@@ -310,6 +310,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUte
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, split = blockIdx.z;
     const int kb0 = split * p.kb_per_split;
     const int nkb = min(p.kblocks, kb0 + p.kb_per_split) - kb0;
+    if (*reinterpret_cast<volatile int *>(p.err) != 0) return;  // an earlier launch failed: skip
     const uint32_t tmem = setup<BN, STAGES>(c, warp);
 
     if (warp == 0) {
@@ -365,6 +366,7 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUt
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM;
     const int64_t n0 = static_cast<int64_t>(blockIdx.y) * BN;
+    if (*reinterpret_cast<volatile int *>(p.err) != 0) return;  // an earlier launch failed: skip
     const uint32_t tmem = setup<BN, STAGES>(c, warp);
 
     if (warp == 0) {
