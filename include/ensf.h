@@ -120,6 +120,23 @@ ensf_status ensf_analysis(ensf_handle *h, const float *prior, int n, int64_t d, 
 ensf_status ensf_weights(ensf_handle *h, const float *z, int n, const float *prior, int n_x,
                          int64_t d, float t, float eps, float *w, void *stream);
 
+/* Allocation-free variant of ensf_weights (FP32 Gram), for callers that may
+ * not allocate device memory: applications whose own memory pool owns every
+ * device allocation, and loops that must never reach an allocation that could
+ * synchronise the device.  The paper has no counterpart; this is a property
+ * of the library, not of the method.  It needs no handle and no workspace:
+ * its scratch (row norms and split-K partial Grams) is one static device
+ * array of 2 MiB + 4 KiB that every device loading the library keeps until
+ * the process exits.  Limits: 1 <= n, n_x <= 256 (else ENSF_EINVAL with a
+ * message in ensf_last_error); d a positive multiple of 8; t in (0, 1].
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller.  Each call
+ * writes every scratch word it reads, so no state carries between calls. */
+ensf_status ensf_weights_static(const float *z, int n, const float *prior, int n_x, int64_t d, float t,
+                                float eps, float *w, void *stream);
+
 /* Standalone counter-based noise: out[k - k0][i][j] = xi[k][i][j] for
  * k = k0..k0+count-1, i < n, j < d (the stream used when ensf_noise.buf is
  * NULL). */

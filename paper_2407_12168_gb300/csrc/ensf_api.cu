@@ -131,6 +131,8 @@ bool aligned16(const void *p) { return p && (reinterpret_cast<uintptr_t>(p) & 15
 
 }  // namespace
 
+void ensf::set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
 // Per-handle launch accounting: every kernel launch is counted by kind; when
 // profiling is on, an event pair brackets each launch on its own stream.
 enum ProfKind { P_NORMS, P_INIT, P_SPLIT, P_GRAM, P_SOFTMAX, P_WXEM, P_CHECK, P_COUNT };

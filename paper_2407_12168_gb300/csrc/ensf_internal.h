@@ -43,4 +43,7 @@ cudaError_t launch_ensemble_stats(const float *z, int n, int64_t d, const float 
                                   double *mean, double *rmse, double *scratch, cudaStream_t s);
 int stats_blocks(int64_t d);
 
+// Host-side message returned by ensf_last_error() on this thread.
+void set_last_error(const char *msg);
+
 }  // namespace ensf

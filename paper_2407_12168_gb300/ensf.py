@@ -56,6 +56,9 @@ _SIGNATURES = [
     ("ensf_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_weights_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
     ("ensf_philox_normal", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_row_norms", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
@@ -210,6 +213,20 @@ class Filter:
 
     def status_sync(self, stream=None) -> int:
         return int(load().ensf_status_sync(self._h, _stream_ptr(stream)))
+
+
+def weights_static(z, prior, t: float, eps: float, out=None, stream=None):
+    """Weights of Eq. 16 (FP32 Gram) through the allocation-free entry point:
+    no handle, no workspace; at most 256 particles and 256 members."""
+    torch = _torch()
+    _dev(z, torch.float32, "z")
+    _dev(prior, torch.float32, "prior")
+    n, d = z.shape
+    n_x = prior.shape[0]
+    w = out if out is not None else torch.empty((n, n_x), dtype=torch.float32, device=z.device)
+    _check(load().ensf_weights_static(z.data_ptr(), n, prior.data_ptr(), n_x, d, float(t), float(eps),
+                                      w.data_ptr(), _stream_ptr(stream)), "ensf_weights_static")
+    return w
 
 
 def philox_normal(seed: int, offset: int, k0: int, count: int, n: int, d: int, stream=None):
