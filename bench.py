@@ -129,7 +129,7 @@ class ClockSampler:
 def make_problem(workload: str, rank: int):
     fn = inputs.WORKLOADS[workload]
     # every rank runs an independent filter (another seed: another truth, prior, noise)
-    return fn(seed={"plain-64": 1, "sparse-arctan-128": 2, "large-512": 4}[workload] + 1000 * rank)
+    return fn(seed={"plain-64": 1, "sparse-arctan-128": 2, "large-512": 4, "medium-192": 5}[workload] + 1000 * rank)
 
 
 def cpu_baseline(p, budget_s: float = 15.0):

@@ -27,7 +27,8 @@
  *   - particles start at z_i = xi_0,i ~ N(0, I) (Sec. III-A.2, the standard
  *     Gaussian sample at the terminal pseudo-time);
  *   - noise: either a caller buffer xi[K+1][N][d] or Philox4x32-10 (Salmon
- *     et al., SC'11) with Box-Muller, evaluated here in double precision.
+ *     et al., SC'11) with Box-Muller, counter (j, i/4, k, offset), evaluated
+ *     here in double precision.
  */
 #include <math.h>
 #include <stdint.h>
@@ -89,19 +90,20 @@ void ensf_oracle_philox4x32_10(const uint32_t *ctr_in, const uint32_t *key_in, u
 
 /*
  * Standard normal xi[k][i][j] of the counter-based noise stream.
- * Counter = (j / 4, i, k, offset), key = (seed low word, seed high word).
- * Output words (w0, w1) feed one Box-Muller pair for j % 4 in {0, 1} and
- * (w2, w3) the pair for j % 4 in {2, 3}:
+ * Counter = (j, i / 4, k, offset), key = (seed low word, seed high word): one
+ * Philox block serves particles 4q..4q+3 of state column j.  Output words
+ * (w0, w1) feed one Box-Muller pair for i % 4 in {0, 1} and (w2, w3) the pair
+ * for i % 4 in {2, 3}:
  *   u1 = ((w_a >> 8) + 1) 2^-24 in (0, 1],  u2 = (w_b >> 8) 2^-24 in [0, 1),
  *   first  = sqrt(-2 ln u1) cos(2 pi u2),  second = sqrt(-2 ln u1) sin(2 pi u2).
  */
 double ensf_oracle_noise(uint64_t seed, uint32_t offset, int k, int i, int64_t j)
 {
-    uint32_t ctr[4] = {(uint32_t)(j >> 2), (uint32_t)i, (uint32_t)k, offset};
+    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(i >> 2), (uint32_t)k, offset};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t w[4];
     ensf_oracle_philox4x32_10(ctr, key, w);
-    int lane = (int)(j & 3);
+    int lane = i & 3;
     uint32_t wa = (lane < 2) ? w[0] : w[2];
     uint32_t wb = (lane < 2) ? w[1] : w[3];
     double u1 = ((double)(wa >> 8) + 1.0) * (1.0 / 16777216.0);
@@ -207,6 +209,14 @@ void ensf_oracle_prior_score(const float *X, int n, int64_t d, const double *z, 
  *         full analysis; fewer only to time a bounded sample)
  *   out   [nrows][d] final particles;  traj optional [k_stop+1][nrows][d]
  *         with the particles before step 0 and after every step.
+ *   logit_perturb, perturb_seed
+ *         0 for the analysis itself.  A test of how well a result is
+ *         determined by its inputs sets logit_perturb > 0: every log-kernel
+ *         l_ij at every step then gets  +/- logit_perturb * alpha |z_i| |x_j| / beta^2
+ *         (sign from the Philox stream keyed by perturb_seed), the size of the
+ *         rounding error that a dot product z_i . x_j with relative accuracy
+ *         logit_perturb leaves in the expanded logit (2 alpha z.x - alpha^2
+ *         |x|^2) / (2 beta^2).
  *   diag  optional [k_stop][nrows][2]: per step and row, the gap between the
  *         largest and second-largest log-kernel (how close the weights are to
  *         a tie) and the scale alpha |z| max_j |x_j| / beta^2 that bounds how
@@ -216,7 +226,8 @@ void ensf_oracle_prior_score(const float *X, int n, int64_t d, const double *z, 
 int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const uint8_t *mask,
                          double sigma_obs, int K, double eps, int obs_op, const float *noise,
                          uint64_t seed, uint32_t offset, const int *rows, int nrows, int k_stop,
-                         double *out, double *traj, double *diag)
+                         double logit_perturb, uint64_t perturb_seed, double *out, double *traj,
+                         double *diag)
 {
     if (n < 1 || d < 1 || K < 1 || !(eps > 0.0 && eps < 1.0) || !(sigma_obs > 0.0))
         return -1;
@@ -231,12 +242,13 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
     double *l = (double *)malloc(sizeof(double) * (size_t)nrows * (size_t)n);
     double *g = (double *)malloc(sizeof(double) * (size_t)d);
     double xmax = 0.0;
-    if (diag) {
-        for (int j = 0; j < n; ++j) {
-            double acc = 0.0;
-            for (int64_t c = 0; c < d; ++c) acc += (double)X[(size_t)j * d + c] * X[(size_t)j * d + c];
-            if (sqrt(acc) > xmax) xmax = sqrt(acc);
-        }
+    double *xnorm = (double *)malloc(sizeof(double) * (size_t)n);
+    double *znorm = (double *)malloc(sizeof(double) * (size_t)nrows);
+    for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int64_t c = 0; c < d; ++c) acc += (double)X[(size_t)j * d + c] * X[(size_t)j * d + c];
+        xnorm[j] = sqrt(acc);
+        if (xnorm[j] > xmax) xmax = xnorm[j];
     }
 
     /* z_i <- xi_0,i : the standard Gaussian sample at pseudo-time T = 1. */
@@ -267,6 +279,25 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
                     dist2 += diff * diff;
                 }
                 l[(size_t)r * n + j] = -dist2 / (2.0 * beta2);
+            }
+        }
+        if (logit_perturb > 0.0) {
+            for (int r = 0; r < nrows; ++r) {
+                const double *z = out + (size_t)r * (size_t)d;
+                double zn = 0.0;
+                for (int64_t c = 0; c < d; ++c) zn += z[c] * z[c];
+                znorm[r] = sqrt(zn);
+            }
+            for (int r = 0; r < nrows; ++r) {
+                int i = rows ? rows[r] : r;
+                for (int j = 0; j < n; ++j) {
+                    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)i, (uint32_t)k, 0x51EDu};
+                    uint32_t key[2] = {(uint32_t)perturb_seed, (uint32_t)(perturb_seed >> 32)};
+                    uint32_t bits[4];
+                    ensf_oracle_philox4x32_10(ctr, key, bits);
+                    double sign = (bits[0] & 1u) ? 1.0 : -1.0;
+                    l[(size_t)r * n + j] += sign * logit_perturb * alpha * znorm[r] * xnorm[j] / beta2;
+                }
             }
         }
         /* normalised weights (Eq. 16) */
@@ -322,6 +353,8 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
     free(w);
     free(l);
     free(g);
+    free(xnorm);
+    free(znorm);
     return 0;
 }
 

@@ -47,12 +47,12 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
-// Four standard normals xi[k][i][4q .. 4q+3] of the noise stream: counter
-// (q, i, k, offset), key (seed low, seed high); words (x, y) and (z, w) each
-// feed one Box-Muller pair with u1 = ((a >> 8) + 1) 2^-24 in (0, 1] and
-// u2 = (b >> 8) 2^-24 in [0, 1).
-__device__ __forceinline__ float4 noise4(uint64_t seed, uint32_t offset, int k, int i, int64_t q) {
-    U4 c{(uint32_t)q, (uint32_t)i, (uint32_t)k, offset};
+// Four standard normals xi[k][4q .. 4q+3][j] of the noise stream (four
+// consecutive particles of state column j): counter (j, q, k, offset), key
+// (seed low, seed high); words (x, y) and (z, w) each feed one Box-Muller pair
+// with u1 = ((a >> 8) + 1) 2^-24 in (0, 1] and u2 = (b >> 8) 2^-24 in [0, 1).
+__device__ __forceinline__ float4 noise4(uint64_t seed, uint32_t offset, int k, int64_t j, int q) {
+    U4 c{(uint32_t)j, (uint32_t)q, (uint32_t)k, offset};
     U4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     const float two_m24 = 5.9604644775390625e-8f;  // 2^-24
     float u1a = (float)((r.x >> 8) + 1u) * two_m24;

@@ -39,27 +39,45 @@ __global__ void __launch_bounds__(256) k_row_norms(const float *__restrict__ x, 
 }
 
 // ---------------------------------------------------------------------------
-// out[kk][i][c] = xi[k0 + kk][i][c]; one thread per 4 consecutive columns.
+// out[kk][i][c] = xi[k0 + kk][i][c]; one thread per (column c, particle quad).
 __global__ void k_philox_normal(uint64_t seed, uint32_t offset, int k0, int n, int64_t d,
                                 float *__restrict__ out) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // column quad
-    int i = blockIdx.y;
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int qd = blockIdx.y;
     int kk = blockIdx.z;
-    if (q * 4 >= d) return;
-    float4 v = noise4(seed, offset, k0 + kk, i, q);
-    *reinterpret_cast<float4 *>(out + ((int64_t)kk * n + i) * d + q * 4) = v;
+    if (c >= d) return;
+    float4 v = noise4(seed, offset, k0 + kk, c, qd);
+    float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int i = qd * 4 + r;
+        if (i < n) out[((int64_t)kk * n + i) * d + c] = vv[r];
+    }
 }
 
-// z[i][c] <- xi[0][i][c]
+// z[i][c] <- xi[0][i][c]; one thread per (column c, particle quad).
 __global__ void k_init_particles(float *__restrict__ z, int n, int64_t d,
                                  const float *__restrict__ noise_buf, uint64_t seed,
                                  uint32_t offset) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
-    if (q * 4 >= d) return;
-    int64_t off = (int64_t)i * d + q * 4;
-    float4 v = noise_buf ? ld4(noise_buf + off) : noise4(seed, offset, 0, i, q);
-    *reinterpret_cast<float4 *>(z + off) = v;
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int qd = blockIdx.y;
+    if (c >= d) return;
+    float vv[4];
+    if (noise_buf) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int i = qd * 4 + r;
+            vv[r] = i < n ? noise_buf[(int64_t)i * d + c] : 0.f;
+        }
+    } else {
+        float4 v = noise4(seed, offset, 0, c, qd);
+        vv[0] = v.x; vv[1] = v.y; vv[2] = v.z; vv[3] = v.w;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int i = qd * 4 + r;
+        if (i < n) z[(int64_t)i * d + c] = vv[r];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -205,20 +223,36 @@ k_wx_em_fp32(const float *__restrict__ w, int ldw, const float *__restrict__ x, 
     const float4 yv = ld4(y + c);
     uchar4 mv = make_uchar4(1, 1, 1, 1);
     if (mask) mv = *reinterpret_cast<const uchar4 *>(mask + c);
+    const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
+    const unsigned char mm[4] = {mv.x, mv.y, mv.z, mv.w};
+    // noise xi[k+1][i][c]: one Philox block per column covers this thread's 4 particles
+    const int ib = i0 + ty * 4;
+    float xi[4][4];  // [row][column]
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (noise_buf) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                xi[r][q] = (ib + r < n) ? noise_buf[((int64_t)(cf.k + 1) * n + ib + r) * d + c + q] : 0.f;
+        } else {
+            float4 v = noise4(seed, offset, cf.k + 1, c + q, ib >> 2);
+            xi[0][q] = v.x; xi[1][q] = v.y; xi[2][q] = v.z; xi[3][q] = v.w;
+        }
+    }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const int i = i0 + ty * 4 + r;
+        const int i = ib + r;
         if (i >= n) continue;
         float *zp = z + (int64_t)i * d + c;
         float4 zv = ld4(zp);
-        float4 xi = noise_buf ? ld4(noise_buf + ((int64_t)(cf.k + 1) * n + i) * d + c)
-                              : noise4(seed, offset, cf.k + 1, i, c >> 2);
-        float4 o;
-        o.x = em_update(cf, zv.x, acc[r][0], mv.x ? lik_score(cf.obs_op, zv.x, yv.x, cf.inv_r) : 0.f, xi.x);
-        o.y = em_update(cf, zv.y, acc[r][1], mv.y ? lik_score(cf.obs_op, zv.y, yv.y, cf.inv_r) : 0.f, xi.y);
-        o.z = em_update(cf, zv.z, acc[r][2], mv.z ? lik_score(cf.obs_op, zv.z, yv.z, cf.inv_r) : 0.f, xi.z);
-        o.w = em_update(cf, zv.w, acc[r][3], mv.w ? lik_score(cf.obs_op, zv.w, yv.w, cf.inv_r) : 0.f, xi.w);
-        *reinterpret_cast<float4 *>(zp) = o;
+        float zz[4] = {zv.x, zv.y, zv.z, zv.w};
+        float o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float g = mm[q] ? lik_score(cf.obs_op, zz[q], yy[q], cf.inv_r) : 0.f;
+            o[q] = em_update(cf, zz[q], acc[r][q], g, xi[r][q]);
+        }
+        *reinterpret_cast<float4 *>(zp) = make_float4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -321,14 +355,14 @@ __global__ void k_stats_rmse(const double *__restrict__ block_sq, int blocks, in
 // ===========================================================================
 cudaError_t launch_init_particles(float *z, int n, int64_t d, const float *noise_buf,
                                   uint64_t seed, uint32_t offset, cudaStream_t s) {
-    dim3 grid((unsigned)((d / 4 + 255) / 256), (unsigned)n);
+    dim3 grid((unsigned)((d + 255) / 256), (unsigned)((n + 3) / 4));
     k_init_particles<<<grid, 256, 0, s>>>(z, n, d, noise_buf, seed, offset);
     return cudaGetLastError();
 }
 
 cudaError_t launch_philox_normal(uint64_t seed, uint32_t offset, int k0, int count, int n,
                                  int64_t d, float *out, cudaStream_t s) {
-    dim3 grid((unsigned)((d / 4 + 255) / 256), (unsigned)n, (unsigned)count);
+    dim3 grid((unsigned)((d + 255) / 256), (unsigned)((n + 3) / 4), (unsigned)count);
     k_philox_normal<<<grid, 256, 0, s>>>(seed, offset, k0, n, d, out);
     return cudaGetLastError();
 }

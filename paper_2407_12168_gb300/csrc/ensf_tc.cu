@@ -151,6 +151,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 // 32 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
+    __syncwarp();  // the load is warp-collective: reconverge after per-lane branches
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -341,10 +342,34 @@ k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUte
 }
 
 // ------------------------------------------------------- W X + EM update
+// Persistent kernel over tiles of U^T = X^T W^T: MMA rows (TMEM lanes) are 128
+// state columns c, MMA columns are BN particles i.  An epilogue thread owns one
+// state column, so for each particle the 32 lanes of a warp touch 32
+// consecutive floats of z[i][:] (coalesced), and y[c], mask[c] are read once
+// per tile.  Two TMEM accumulators (columns 0 and 256) let the epilogue of one
+// tile run while the MMAs of the next accumulate.
+constexpr int kEpiWarps = 8;                       // two per TMEM lane quarter
+constexpr int kWxThreads = 64 + 32 * kEpiWarps;    // producer, MMA, epilogue
+constexpr int kWxTmemCols = 512;
+
+template <int BN, int STAGES, bool SPLIT>
+struct WxPlan {
+    static constexpr int kA = BM * BK * 2;  // X^T rows (state columns)
+    static constexpr int kB = BN * BK * 2;  // W rows (particles)
+    static constexpr int kPlanes = SPLIT ? 2 : 1;
+    static constexpr int kStage = (kA + kB) * kPlanes;
+    static constexpr int kBarOff = kStage * STAGES;
+    static constexpr int kBytes = kBarOff + 512 + 1024;
+    static_assert(kBytes <= 227 * 1024, "shared memory plan too large");
+    static_assert(BN == 64 || BN == 128 || BN == 256, "BN");
+};
+
 struct WxParams {
     int n;
     int64_t d;
-    int kblocks;  // ceil(n_x / BK)
+    int kblocks;   // ceil(n_x / BK)
+    int m_tiles;   // ceil(d / 128)
+    int n_tiles;   // ceil(n / BN)
     float *z;
     __nv_bfloat16 *zb_hi, *zb_lo;
     const float *y;
@@ -356,83 +381,184 @@ struct WxParams {
     int *err;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 template <int BN, int STAGES, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 1)
-k_wx_em_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
-           const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, WxParams p) {
-    using P = Plan<BN, STAGES, SPLIT>;
+__global__ void __launch_bounds__(kWxThreads, 1)
+k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CUtensorMap xt_lo,
+           const __grid_constant__ CUtensorMap w_hi, const __grid_constant__ CUtensorMap w_lo, WxParams p) {
+    using P = WxPlan<BN, STAGES, SPLIT>;
     extern __shared__ uint8_t smem_raw[];
-    const Ctl c = carve<P>(smem_raw, STAGES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM;
-    const int64_t n0 = static_cast<int64_t>(blockIdx.y) * BN;
     if (*reinterpret_cast<volatile int *>(p.err) != 0) return;  // an earlier launch failed: skip
-    const uint32_t tmem = setup<BN, STAGES>(c, warp);
+
+    uintptr_t base = reinterpret_cast<uintptr_t>(smem_raw);
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    uint8_t *tiles = reinterpret_cast<uint8_t *>(base + pad);
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;   // [2] accumulator ready
+    uint64_t *tempty = tfull + 2;       // [2] accumulator drained
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], kEpiWarps);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kWxTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int total = p.m_tiles * p.n_tiles;
 
     if (warp == 0) {
-        if (lane == 0)
-            produce<BN, STAGES, SPLIT>(c, &a_hi, &a_lo, &b_hi, &b_lo, m0, static_cast<int>(n0), 0, p.kblocks, p.err);
-    } else if (warp == 1) {
-        if (lane == 0) mma_loop<BN, STAGES, SPLIT>(c, tmem, p.kblocks, p.err);
-    } else {
-        const int q = warp & 3;
-        const int i = m0 + q * 32 + lane;  // particle row of this thread
-        const bool ok = mbar_wait(c.accum, 0, c.abort_flag, p.err);
-        tc_fence_after();
-        if (ok) {
-            const StepCoef &cf = p.coef;
-            const int64_t noise_row = (static_cast<int64_t>(cf.k + 1) * p.n + i) * p.d;
-#pragma unroll 1
-            for (int cc = 0; cc < BN; cc += 32) {
-                float u[32];
-                tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + cc, u);
-                const int64_t col0 = n0 + cc;
-                if (i >= p.n || col0 >= p.d) continue;
-                const int64_t rest = p.d - col0;
-                const int valid = rest < 32 ? static_cast<int>(rest) : 32;  // multiple of 8
-                float *zrow = p.z + static_cast<int64_t>(i) * p.d + col0;
-#pragma unroll
-                for (int e8 = 0; e8 < 4; ++e8) {
-                    if (e8 * 8 >= valid) break;
-                    float out[8];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int e = e8 * 8 + h * 4;
-                        const int64_t col = col0 + e;
-                        const float4 zv = *reinterpret_cast<const float4 *>(zrow + e);
-                        const float4 yv = *reinterpret_cast<const float4 *>(p.y + col);
-                        uchar4 mv = make_uchar4(1, 1, 1, 1);
-                        if (p.mask) mv = *reinterpret_cast<const uchar4 *>(p.mask + col);
-                        const float4 xi = p.noise_buf ? *reinterpret_cast<const float4 *>(p.noise_buf + noise_row + col)
-                                                      : noise4(p.seed, p.offset, cf.k + 1, i, col >> 2);
-                        const float zz[4] = {zv.x, zv.y, zv.z, zv.w};
-                        const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
-                        const unsigned char mm[4] = {mv.x, mv.y, mv.z, mv.w};
-                        const float nn[4] = {xi.x, xi.y, xi.z, xi.w};
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const float g = mm[t] ? lik_score(cf.obs_op, zz[t], yy[t], cf.inv_r) : 0.f;
-                            out[h * 4 + t] = em_update(cf, zz[t], u[e + t], g, nn[t]);
-                        }
-                    }
-                    *reinterpret_cast<float4 *>(zrow + e8 * 8) = make_float4(out[0], out[1], out[2], out[3]);
-                    *reinterpret_cast<float4 *>(zrow + e8 * 8 + 4) = make_float4(out[4], out[5], out[6], out[7]);
-                    if (p.zb_hi) {
-                        __align__(16) __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) {
-                            hi[t] = __float2bfloat16_rn(out[t]);
-                            lo[t] = __float2bfloat16_rn(out[t] - __bfloat162float(hi[t]));
-                        }
-                        const int64_t off = static_cast<int64_t>(i) * p.d + col0 + e8 * 8;
-                        *reinterpret_cast<uint4 *>(p.zb_hi + off) = *reinterpret_cast<const uint4 *>(hi);
-                        if (p.zb_lo) *reinterpret_cast<uint4 *>(p.zb_lo + off) = *reinterpret_cast<const uint4 *>(lo);
+        if (lane == 0) {
+            int it = 0;
+            int issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int m0 = (t / p.n_tiles) * BM, n0 = (t % p.n_tiles) * BN;
+                for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) { ok = false; break; }
+                    const uint32_t st = smem_u32(tiles + s * P::kStage);
+                    mbar_expect_tx(&full[s], P::kStage);
+                    const int kx = kb * BK;
+                    tma_load_2d(st, &xt_hi, &full[s], kx, m0);
+                    if (SPLIT) tma_load_2d(st + P::kA, &xt_lo, &full[s], kx, m0);
+                    tma_load_2d(st + P::kA * P::kPlanes, &w_hi, &full[s], kx, n0);
+                    if (SPLIT) tma_load_2d(st + P::kA * P::kPlanes + P::kB, &w_lo, &full[s], kx, n0);
+                    issued = it + 1;
+                }
+            }
+            if (*abort_flag) {
+                const uint64_t t0 = globaltimer();
+                for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i) {
+                    const int s = i % STAGES;
+                    while (!mbar_try_wait(&full[s], (i / STAGES) & 1) && globaltimer() - t0 < kTimeoutNs) {
                     }
                 }
             }
         }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int it = 0, lt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++lt) {
+                const int slot = lt & 1;
+                const uint32_t use = lt >> 1;
+                if (!mbar_wait(&tempty[slot], (use & 1u) ^ 1u, abort_flag, p.err)) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + slot * 256;
+                for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_hi = smem_u32(tiles + s * P::kStage);
+                    const uint32_t a_lo = a_hi + P::kA;
+                    const uint32_t b_hi = a_hi + P::kA * P::kPlanes;
+                    const uint32_t b_lo = b_hi + P::kB;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        mma_bf16(acc, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                        if (SPLIT) {
+                            mma_bf16(acc, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
+                            mma_bf16(acc, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[slot]);
+            }
+        }
+    } else {
+        const int ew = warp - 2;            // 0 .. kEpiWarps-1
+        const int q = warp & 3;             // TMEM lane quarter this warp may read
+        const int half = ew >> 2;           // which half of the BN particle columns
+        constexpr int kCols = BN / 2;
+        const StepCoef &cf = p.coef;
+        int lt = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
+            const int slot = lt & 1;
+            const uint32_t use = lt >> 1;
+            const int m0 = (t / p.n_tiles) * BM, n0 = (t % p.n_tiles) * BN;
+            if (!mbar_wait(&tfull[slot], use & 1u, abort_flag, p.err)) break;
+            tc_fence_after();
+            const int64_t c = static_cast<int64_t>(m0) + q * 32 + lane;  // this thread's state column
+            const bool cok = c < p.d;
+            const float yc = cok ? p.y[c] : 0.f;
+            const bool obs = cok && (p.mask == nullptr || p.mask[c] != 0);
+#pragma unroll 1
+            for (int cc = half * kCols; cc < (half + 1) * kCols; cc += 32) {
+                float u[32];
+                tmem_ld32(tmem + slot * 256 + (static_cast<uint32_t>(q * 32) << 16) + cc, u);
+                const int i0 = n0 + cc;
+                if (!cok || i0 >= p.n) continue;
+                float zv[32];
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    zv[e] = (i0 + e < p.n) ? p.z[static_cast<int64_t>(i0 + e) * p.d + c] : 0.f;
+#pragma unroll
+                for (int e4 = 0; e4 < 8; ++e4) {
+                    const int ib = i0 + e4 * 4;
+                    if (ib >= p.n) break;
+                    float xi[4];
+                    if (p.noise_buf) {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            xi[r] = (ib + r < p.n)
+                                        ? p.noise_buf[(static_cast<int64_t>(cf.k + 1) * p.n + ib + r) * p.d + c]
+                                        : 0.f;
+                    } else {
+                        const float4 v = noise4(p.seed, p.offset, cf.k + 1, c, ib >> 2);
+                        xi[0] = v.x; xi[1] = v.y; xi[2] = v.z; xi[3] = v.w;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int i = ib + r;
+                        if (i >= p.n) break;
+                        const int e = e4 * 4 + r;
+                        const float g = obs ? lik_score(cf.obs_op, zv[e], yc, cf.inv_r) : 0.f;
+                        const float zn = em_update(cf, zv[e], u[e], g, xi[r]);
+                        const int64_t off = static_cast<int64_t>(i) * p.d + c;
+                        p.z[off] = zn;
+                        if (p.zb_hi) {
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(zn);
+                            p.zb_hi[off] = hi;
+                            if (p.zb_lo) p.zb_lo[off] = __float2bfloat16_rn(zn - __bfloat162float(hi));
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[slot]);
+        }
     }
-    teardown<BN>(tmem, warp);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kWxTmemCols);
+    }
 }
 
 }  // namespace
@@ -498,12 +624,15 @@ cudaError_t run_gram(const CUtensorMap (&maps)[4], const GramParams &p, dim3 gri
 }
 
 template <int BN, int STAGES, bool SPLIT>
-cudaError_t run_wx(const CUtensorMap (&maps)[4], const WxParams &p, dim3 grid, cudaStream_t s) {
-    using P = Plan<BN, STAGES, SPLIT>;
+cudaError_t run_wx(const CUtensorMap (&maps)[4], WxParams p, int sms, cudaStream_t s) {
+    using P = WxPlan<BN, STAGES, SPLIT>;
     auto kern = k_wx_em_tc<BN, STAGES, SPLIT>;
     cudaError_t e = set_smem(kern, P::kBytes);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
+    p.n_tiles = (p.n + BN - 1) / BN;
+    const int total = p.m_tiles * p.n_tiles;
+    const int grid = total < sms ? total : sms;
+    kern<<<grid, kWxThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
     return cudaGetLastError();
 }
 
@@ -561,22 +690,23 @@ cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *sp
 }
 
 cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStream_t s) {
-    (void)sms;
     if (!ctx) return cudaErrorInvalidValue;
     const bool split = a.wb_lo != nullptr && a.xt_lo != nullptr;
-    const int BN = split ? 128 : 256;
-    // A = W [n][ldw] (K = n_x = the valid columns), B = X^T [d][ldw]
+    const int BN = a.n <= 64 ? 64 : (a.n <= 128 ? 128 : 256);
+    // A = X^T [d][ldw] (state columns; K = n_x members), B = W [n][ldw] (particles)
     const int n_x = a.n;
     CUtensorMap maps[4];
     cudaError_t e;
-    if ((e = make_map(ctx, &maps[0], a.wb_hi, n_x, a.n, a.ldw, BM)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[1], split ? a.wb_lo : nullptr, n_x, a.n, a.ldw, BM)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[2], a.xt_hi, n_x, a.d, a.ldw, BN)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[3], split ? a.xt_lo : nullptr, n_x, a.d, a.ldw, BN)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[0], a.xt_hi, n_x, a.d, a.ldw, BM)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[1], split ? a.xt_lo : nullptr, n_x, a.d, a.ldw, BM)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[2], a.wb_hi, n_x, a.n, a.ldw, BN)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[3], split ? a.wb_lo : nullptr, n_x, a.n, a.ldw, BN)) != cudaSuccess) return e;
     WxParams p;
     p.n = a.n;
     p.d = a.d;
     p.kblocks = (n_x + BK - 1) / BK;
+    p.m_tiles = static_cast<int>((a.d + BM - 1) / BM);
+    p.n_tiles = 0;
     p.z = a.z;
     p.zb_hi = a.zb_hi;
     p.zb_lo = a.zb_lo;
@@ -587,9 +717,14 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     p.offset = a.offset;
     p.coef = a.coef;
     p.err = a.err;
-    dim3 grid((a.n + BM - 1) / BM, static_cast<unsigned>((a.d + BN - 1) / BN));
-    if (split) return run_wx<128, 3, true>(maps, p, grid, s);
-    return run_wx<256, 2, false>(maps, p, grid, s);
+    if (split) {
+        if (BN == 256) return run_wx<256, 2, true>(maps, p, sms, s);
+        if (BN == 128) return run_wx<128, 3, true>(maps, p, sms, s);
+        return run_wx<64, 4, true>(maps, p, sms, s);
+    }
+    if (BN == 256) return run_wx<256, 4, false>(maps, p, sms, s);
+    if (BN == 128) return run_wx<128, 6, false>(maps, p, sms, s);
+    return run_wx<64, 8, false>(maps, p, sms, s);
 }
 
 }  // namespace ensf

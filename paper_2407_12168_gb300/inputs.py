@@ -117,6 +117,12 @@ def large_512(seed: int = 4, n: int = 1024, K: int = 100) -> Problem:
     return _problem("large-512", 2, 512, n, K, 0.5, 0, 1.0, 0.5, 0.0, seed)
 
 
+def medium_192(seed: int = 5, n: int = 1024, K: int = 10) -> Problem:
+    """Profiling size of the large case: N = 1024, d = 2*192*192 (a 302 MB
+    state, larger than L2), 10 Euler-Maruyama steps."""
+    return _problem("medium-192", 2, 192, n, K, 0.5, 0, 1.0, 0.5, 0.0, seed)
+
+
 def small_case(seed: int, n: int, grid: int, layers: int = 1, K: int = 10, obs_op: int = 0,
                obs_frac: float = 1.0, sigma_obs: float = 1.0, eps: float = 0.05) -> Problem:
     """A small problem for parity tests: any n, d = layers*grid*grid."""
@@ -144,4 +150,5 @@ WORKLOADS = {
     "plain-64": plain_64,
     "sparse-arctan-128": sparse_arctan_128,
     "large-512": large_512,
+    "medium-192": medium_192,
 }

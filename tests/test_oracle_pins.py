@@ -46,8 +46,11 @@ def test_noise_is_standard_normal():
     for a in range(len(rows)):
         for b in range(a + 1, len(rows)):
             assert abs(np.corrcoef(rows[a], rows[b])[0, 1]) < 5.0 / np.sqrt(d)
-    # neighbouring lanes of one Philox block are distinct draws
-    assert abs(np.corrcoef(rows[0][0::4], rows[0][1::4])[0, 1]) < 5.0 / np.sqrt(d / 4)
+    # the four lanes of one Philox block (particles 4q..4q+3 of one column) are distinct draws
+    lanes = [o.noise(seed=12345, offset=0, k=0, i=i, d=d) for i in range(4)]
+    for a in range(4):
+        for b in range(a + 1, 4):
+            assert abs(np.corrcoef(lanes[a], lanes[b])[0, 1]) < 5.0 / np.sqrt(d)
     # the offset and the seed change the stream
     assert not np.allclose(o.noise(12345, 1, 0, 0, 64), rows[0][:64])
     assert not np.allclose(o.noise(12346, 0, 0, 0, 64), rows[0][:64])
