@@ -191,6 +191,49 @@ def _config(p, path, world):
             "parallelism": f"{world} independent filter(s), one per GPU"}
 
 
+def _roofline(kernel, rec, p, gram, wx, args, peaks):
+    """Roofline entry of one kernel kind from its event-timed launches.
+
+    gram (Z X^T, 2 N^2 d FLOP algorithmic per launch; split-BF16x3 executes
+    three BF16 products) is a dense contraction: tensor (or FP32 ALU) bound.
+    wx_em (W X + score + Euler-Maruyama) moves per launch 8 N d bytes of
+    particle state (read + write), 4 N d of noise, 2 N d of X^T (BF16), and
+    4 N d of BF16 Z planes when the Gram runs on tensor cores: at N = 1024 its
+    2 N^2 d FLOP sit below the BF16 ridge, so it is HBM bound."""
+    launches, timed, tot_ms = rec
+    avg_ms = tot_ms / timed
+    n, d = p.n, p.d
+    prec = gram if kernel == "gram" else wx
+    flops = 2.0 * n * n * d
+    if kernel == "wx_em" and prec != "fp32":
+        nbytes = (8 + 4 + 2 * (2 if prec == "split" else 1) + (4 if gram != "fp32" else 0)) * n * d + 5 * d
+        peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
+        achieved = nbytes / (avg_ms / 1e3) / 1e9
+        return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic_record(kernel, p.name, args.path),
+                "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback",
+                "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms,
+                "tflops": flops / (avg_ms / 1e3) / 1e12}
+    if kernel not in ("gram", "wx_em"):
+        return {"kernel": kernel, "bound": None, "avg_launch_ms": avg_ms}
+    split_factor = {"split": 3.0, "bf16": 1.0, "fp32": 1.0}[prec]
+    executed = flops * split_factor
+    if prec == "fp32":
+        bound, peak, src = "alu", FP32_SIMT_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+    else:
+        bound = "tensor"
+        if peaks:
+            peak, src = float(peaks["bf16_tflops_sustained"]), "measured bf16 sustained (MEASURED_PEAKS.json)"
+        else:
+            peak, src = 1700.0, "fallback bf16 sustained"
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": _traffic_record(kernel, p.name, args.path), "peak_source": src,
+            "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms,
+            "executed_flops_per_launch": executed, "executed_tflops": executed / (avg_ms / 1e3) / 1e12,
+            "executed_frac": executed / (avg_ms / 1e3) / 1e12 / peak}
+
+
 def run_ours(args):
     import torch
     rank, local_rank, world = _dist_env()
@@ -208,8 +251,11 @@ def run_ours(args):
     y = torch.from_numpy(p.y).to(dev)
     mask = torch.from_numpy(p.mask).to(dev) if p.mask is not None else None
     out = torch.empty_like(prior)
-    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx)
+    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, graph=args.graph)
     stream = torch.cuda.current_stream()
+    tuning = None
+    if gram != "fp32" or wx != "fp32":
+        tuning = f.autotune(prior, y, mask, p.sigma_obs, p.eps, p.obs_op, seed=p.seed, out=out)
     small = p.n * p.d * 4 <= 256 << 20
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if small else None
 
@@ -221,7 +267,6 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- device-timed region: inputs resident in HBM ----
-    f.profile_enable(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
@@ -237,10 +282,20 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ms = float(sum(a.elapsed_time(b) for a, b in ev))
-    prof = f.profile_read()
-    f.profile_enable(False)
     if f.status_sync() != 0:
         raise RuntimeError("device error during the benchmark")
+
+    # ---- per-kernel timing: the same steps again, every launch bracketed by
+    # CUDA events on its stream (kept out of the timed region above, whose
+    # small kernels the extra events would slow down) ----
+    f.profile_enable(True)
+    for s_ in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        one(100 + s_)
+    torch.cuda.synchronize()
+    prof = f.profile_read()
+    f.profile_enable(False)
 
     # ---- end to end: host buffers, copies inside the timed region ----
     h_prior = torch.from_numpy(p.prior).pin_memory()
@@ -281,32 +336,13 @@ def run_ours(args):
     value = world * member_steps / (ms_per_step / 1e3)
     e2e_value = world * member_steps / (e2e_ms / 1e3)
 
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant kernel (and of the other contraction) ----
     kernels = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(kernels, key=lambda k: kernels[k][2])
-    launches, timed, tot_ms = kernels[dom]
-    avg_ms = tot_ms / timed
     peaks = _peaks()
-    flops_gemm = 2.0 * p.n * p.n * p.d        # algorithmic FLOPs of one Gram or one W X
-    split_factor = {"split": 3.0, "bf16": 1.0, "fp32": 1.0}
-    prec = gram if dom == "gram" else wx
-    executed = flops_gemm * split_factor[prec]
-    if prec == "fp32":
-        bound, peak, peak_src = "alu", FP32_SIMT_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-    else:
-        bound = "tensor"
-        if peaks:
-            peak, peak_src = float(peaks["bf16_tflops_sustained"]), "measured bf16 sustained (MEASURED_PEAKS.json)"
-        else:
-            peak, peak_src = 1700.0, "fallback bf16 sustained"
-    achieved = flops_gemm / (avg_ms / 1e3) / 1e12
-    traffic = _traffic_record(dom, p.name, args.path)
-    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-            "algorithmic_flops_per_launch": flops_gemm, "avg_launch_ms": avg_ms,
-            "executed_flops_per_launch": executed,
-            "executed_tflops": executed / (avg_ms / 1e3) / 1e12,
-            "executed_frac": executed / (avg_ms / 1e3) / 1e12 / peak}
+    rooflines = {k: _roofline(k, kernels[k], p, gram, wx, args, peaks) for k in ("gram", "wx_em") if k in kernels}
+    dom = max(kernels, key=lambda k: kernels[k][2])
+    roof = rooflines.get(dom) or _roofline(dom, kernels[dom], p, gram, wx, args, peaks)
+    other = {k: v for k, v in rooflines.items() if k != dom}
     gpu_launches = int(sum(v[0] for v in prof.values()))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -314,9 +350,10 @@ def run_ours(args):
             "vs_baseline": None, "dtype": {"split-bf16": "bf16x3+bf16 (fp32 acc)", "split": "bf16x3 (fp32 acc)",
                                           "fp32": "f32"}[args.path],
             "data": "synthetic", "config": _config(p, args.path, world), "roofline": roof,
+            "roofline_other": other,
             "kernels": {k: {"launches": v[0], "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": gpu_launches, "clocks": clk.summary()}
+            "gpu_launches": gpu_launches, "clocks": clk.summary(), "tuning": tuning, "cuda_graph": args.graph}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget_s)
     print(json.dumps(line))
@@ -334,6 +371,7 @@ def main(argv=None):
     ap.add_argument("--path", default="split-bf16", choices=sorted(PATHS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="replay each analysis as one captured CUDA graph")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     args = ap.parse_args(argv)

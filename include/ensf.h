@@ -65,6 +65,11 @@ typedef enum {
 } ensf_precision;
 
 #define ENSF_FLAG_CHECK_FINITE 1u  /* scan the final particles for NaN/Inf */
+#define ENSF_FLAG_CUDA_GRAPH 2u    /* ensf_analysis captures its whole launch sequence (all K
+                                      Euler-Maruyama steps) into one CUDA graph and launches that;
+                                      the instantiated graph is kept in the handle and updated in
+                                      place when only scalars or pointers change.  Ignored on the
+                                      legacy default stream and inside a caller's own capture. */
 
 typedef struct {
     int max_n;        /* largest ensemble size N this handle will run (>= 1)          */
@@ -113,6 +118,27 @@ ensf_status ensf_analysis(ensf_handle *h, const float *prior, int n, int64_t d, 
                           const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
                           const ensf_noise *noise, float *out, void *stream);
 
+/* Launch shapes chosen by ensf_autotune. */
+typedef struct {
+    int gram_tile_n;   /* Gram output tile width (forecast members per tile)          */
+    int gram_stages;   /* shared-memory ring depth of the Gram                        */
+    int gram_splits;   /* split-K slices over the state dimension                     */
+    float gram_ms;     /* measured time of one Gram launch with that shape            */
+    int wx_tile_n;     /* W X tile width (particles per tile)                         */
+    float wx_ms;       /* measured time of one W X launch with that shape            */
+} ensf_tuning;
+
+/* Autotuner for the tensor-core stages: times the candidate launch shapes of
+ * the Gram (tile width, ring depth, split count) and of W X (tile width) on
+ * these operands (same arguments as ensf_analysis, without K) and records the
+ * fastest for this (n, d) in the handle; later analyses of that shape use it.
+ * Overwrites `out` and the workspace, synchronises `stream`, and must not be
+ * called while the stream is being captured.  `report` may be NULL.  A handle
+ * with only CUDA-core precisions returns ENSF_OK with a zeroed report. */
+ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                          const uint8_t *obs_mask, int obs_op, float sigma_obs, float eps,
+                          const ensf_noise *noise, float *out, ensf_tuning *report, void *stream);
+
 /* Normalised weights w_ij of Eq. 16 for given particles z [n][d] at pseudo-
  * time t, against the forecast ensemble prior [n_x][d], written to
  * w [n][n_x] FP32.  Uses the handle's Gram precision; this is the Gram +
@@ -156,7 +182,7 @@ ensf_status ensf_ensemble_stats(const float *z, int n, int64_t d, const float *t
 
 /* Launch accounting of a handle.  Every kernel launch is counted by kind
  * ("row_norms", "init_particles", "split_bf16", "gram", "softmax_rows",
- * "wx_em", "check_finite").  While profiling is on, each launch is also
+ * "wx_em", "check_finite", "noise").  While profiling is on, each launch is also
  * bracketed by a CUDA event pair recorded on the launching stream (at most
  * 16384 pairs; later launches are counted but not timed).  Enabling or
  * disabling clears the counters; the first enable creates the events. */

@@ -46,8 +46,9 @@ bool is_tc(int p) { return p == ENSF_PREC_SPLIT_BF16X3 || p == ENSF_PREC_BF16; }
 
 // Offsets of every scratch array inside the workspace.
 struct Layout {
-    size_t err = 0, norms = 0, w = 0, partial = 0;
+    size_t err = 0, norms = 0, w = 0, partial = 0, xbar = 0;
     size_t xb_hi = 0, xb_lo = 0, zb_hi = 0, zb_lo = 0, xt_hi = 0, xt_lo = 0, wb_hi = 0, wb_lo = 0;
+    size_t noise = 0;  // one [N][d] FP32 noise slice, generated a step ahead (tensor-core W X)
     size_t total = 0;
     int64_t partial_floats = 0;
 };
@@ -73,6 +74,7 @@ Layout make_layout(const ensf_config *c) {
     const int64_t N = c->max_n, D = c->max_d;
     L.err = take(sizeof(int) * 4);
     L.norms = take(sizeof(double) * N);
+    L.xbar = take(sizeof(float) * D);
     L.w = take(sizeof(float) * N * N);
     // split-K Gram partials: splits * n * n_x <= (target CTAs + tiles) * tile area
     int64_t tiles_simt = ((N + kSimtTile - 1) / kSimtTile) * ((N + kSimtTile - 1) / kSimtTile);
@@ -93,6 +95,7 @@ Layout make_layout(const ensf_config *c) {
         if (is_tc(c->wx)) {
             L.xt_hi = take(2 * D * NP);
             L.wb_hi = take(2 * N * NP);
+            L.noise = take(4 * N * D);
             if (c->wx == ENSF_PREC_SPLIT_BF16X3) {
                 L.xt_lo = take(2 * D * NP);
                 L.wb_lo = take(2 * N * NP);
@@ -135,9 +138,9 @@ void ensf::set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_las
 
 // Per-handle launch accounting: every kernel launch is counted by kind; when
 // profiling is on, an event pair brackets each launch on its own stream.
-enum ProfKind { P_NORMS, P_INIT, P_SPLIT, P_GRAM, P_SOFTMAX, P_WXEM, P_CHECK, P_COUNT };
+enum ProfKind { P_NORMS, P_INIT, P_SPLIT, P_GRAM, P_SOFTMAX, P_WXEM, P_CHECK, P_NOISE, P_COUNT };
 const char *const kProfNames[P_COUNT] = {"row_norms", "init_particles", "split_bf16", "gram",
-                                         "softmax_rows", "wx_em", "check_finite"};
+                                         "softmax_rows", "wx_em", "check_finite", "noise"};
 constexpr size_t kProfPairs = 16384;
 
 struct Prof {
@@ -158,6 +161,7 @@ struct ensf_handle {
     int sms = 0;
     int device = 0;
     ensf::TcContext *tc = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;  // ENSF_FLAG_CUDA_GRAPH: last instantiated analysis
 
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
     int *err() const { return at<int>(L.err); }
@@ -195,8 +199,16 @@ cudaError_t prof_end(ensf_handle *h, cudaStream_t s) {
 // Gram + row softmax for particles z [n][d] against prior [n_x][d] at step
 // coefficients c.  Writes W FP32 into h->w when want_fp32, and the BF16
 // weight planes when the W X contraction runs on tensor cores.
+struct NoiseRequest {
+    float *slice = nullptr;  // write xi[k] [n][d] here during the Gram (tensor-core Gram only)
+    uint64_t seed = 0;
+    uint32_t offset = 0;
+    int k = 0;
+};
+
 ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *prior, int n_x, int64_t d,
-                         const ensf::StepCoef &c, bool want_fp32, cudaStream_t s) {
+                         const ensf::StepCoef &c, bool want_fp32, cudaStream_t s,
+                         const NoiseRequest &nr = NoiseRequest()) {
     const Layout &L = h->L;
     float *partial = h->at<float>(L.partial);
     int splits = 0;
@@ -204,7 +216,8 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
     int ldp = 0;
     if (h->cfg.gram == ENSF_PREC_FP32) {
         splits = simt_splits(n, n_x, d, h->sms);
-        ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_fp32(z, n, prior, n_x, d, splits, partial, s));
+        ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_fp32(z, n, prior, n_x, d, splits, partial, s,
+                                                         h->at<float>(L.xbar), c.alpha));
         part_stride = (int64_t)n * n_x;
         ldp = n_x;
     } else {
@@ -220,6 +233,10 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
         a.partial = partial;
         a.partial_cap = L.partial_floats;
         a.err = h->err();
+        a.noise = nr.slice;
+        a.seed = nr.seed;
+        a.offset = nr.offset;
+        a.noise_k = nr.k;
         ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_tc(h->tc, a, h->sms, &splits, &part_stride, &ldp, s));
     }
     __nv_bfloat16 *wb_hi = nullptr, *wb_lo = nullptr;
@@ -293,6 +310,7 @@ ensf_status ensf_create(const ensf_config *cfg, void *workspace, size_t ws_bytes
             return cuda_fail(e, "tc_context_create");
         }
     }
+
     cudaError_t e = cudaMemset(h->err(), 0, sizeof(int) * 4);
     if (e != cudaSuccess) {
         ensf::tc_context_destroy(h->tc);
@@ -306,14 +324,19 @@ ensf_status ensf_create(const ensf_config *cfg, void *workspace, size_t ws_bytes
 ensf_status ensf_destroy(ensf_handle *h) {
     if (!h) return fail(ENSF_EINVAL, "ensf_destroy: NULL handle");
     for (cudaEvent_t e : h->prof.events) cudaEventDestroy(e);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     ensf::tc_context_destroy(h->tc);
     delete h;
     return ENSF_OK;
 }
 
-ensf_status ensf_analysis(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
-                          const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
-                          const ensf_noise *noise, float *out, void *stream) {
+}  // extern "C"
+
+namespace {
+
+ensf_status analysis_validate(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                              const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
+                              const ensf_noise *noise, const float *out) {
     if (!h) return fail(ENSF_EINVAL, "ensf_analysis: NULL handle");
     if (!aligned16(prior) || !aligned16(y) || !aligned16(out))
         return fail(ENSF_EINVAL, "ensf_analysis: prior, y and out must be non-NULL and 16-byte aligned");
@@ -331,58 +354,239 @@ ensf_status ensf_analysis(ensf_handle *h, const float *prior, int n, int64_t d, 
     if (noise->buf && !aligned16(noise->buf)) return fail(ENSF_EINVAL, "ensf_analysis: noise buffer must be 16-byte aligned");
     if (static_cast<const void *>(prior) == static_cast<const void *>(out))
         return fail(ENSF_EINVAL, "ensf_analysis: out must not alias prior");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return ENSF_OK;
+}
+
+// Everything of one analysis before its first Euler-Maruyama step: centre and
+// norms of the forecast ensemble, the initial particles, the BF16 planes.
+ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, int K, float eps, float sigma_obs,
+                          int obs_op, const ensf_noise *noise, float *out, cudaStream_t s) {
     const Layout &L = h->L;
     const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
-
-    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, h->at<double>(L.norms), s));
+    float *xbar = h->at<float>(L.xbar);
+    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_col_mean(prior, n, d, xbar, s));
+    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, h->at<double>(L.norms), s, xbar));
     ENSF_LAUNCH(h, P_INIT, s, ensf::launch_init_particles(out, n, d, noise->buf, noise->seed, noise->offset, s));
-    __nv_bfloat16 *zb_hi = nullptr, *zb_lo = nullptr;
     if (tc_gram) {
-        zb_hi = h->at<__nv_bfloat16>(L.zb_hi);
-        zb_lo = L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
         ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(prior, n, d, h->at<__nv_bfloat16>(L.xb_hi),
-                                                           L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s));
-        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, zb_hi, zb_lo, d, s));
+                                                           L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s,
+                                                           xbar, 1.0f));
+        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, h->at<__nv_bfloat16>(L.zb_hi),
+                                                           L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s,
+                                                           xbar, step_coef(0, K, eps, sigma_obs, obs_op).alpha));
     }
-    const int ldt = (int)round_up(n, 8);
     if (tc_wx)
         ENSF_LAUNCH(h, P_SPLIT, s,
                     ensf::launch_split_bf16_transpose(prior, n, d, h->at<__nv_bfloat16>(L.xt_hi),
-                                                      L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) : nullptr, ldt, s));
+                                                      L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) : nullptr,
+                                                      (int)round_up(n, 8), s));
+    return ENSF_OK;
+}
+
+// Arguments of the tensor-core W X of step k (the noise slice is the handle's
+// pre-generated one unless the caller supplied a buffer).
+ensf::TcWxArgs wx_args(ensf_handle *h, int n, int64_t d, const float *y, const uint8_t *obs_mask,
+                       const ensf_noise *noise, float *out, const ensf::StepCoef &c, float alpha_next, int k) {
+    const Layout &L = h->L;
+    ensf::TcWxArgs a;
+    a.wb_hi = h->at<__nv_bfloat16>(L.wb_hi);
+    a.wb_lo = L.wb_lo ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
+    a.xt_hi = h->at<__nv_bfloat16>(L.xt_hi);
+    a.xt_lo = L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) : nullptr;
+    a.ldw = (int)round_up(n, 8);
+    a.n = n;
+    a.d = d;
+    a.z = out;
+    a.zb_hi = is_tc(h->cfg.gram) ? h->at<__nv_bfloat16>(L.zb_hi) : nullptr;
+    a.zb_lo = (is_tc(h->cfg.gram) && L.zb_lo) ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
+    a.y = y;
+    a.mask = obs_mask;
+    a.noise = noise->buf ? noise->buf + (size_t)(k + 1) * n * d : h->at<float>(L.noise);
+    a.centre = h->at<float>(L.xbar);
+    a.alpha_next = alpha_next;
+    a.coef = c;
+    a.err = h->err();
+    return a;
+}
+
+ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                             const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
+                             const ensf_noise *noise, float *out, cudaStream_t s) {
+    const Layout &L = h->L;
+    const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
+
+    // The Gram runs on centred operands z - alpha m and x_j - m, m = the forecast
+    // mean: |z - alpha x_j|^2 is unchanged, the magnitudes entering the expanded
+    // logit (and so its rounding error) shrink.
+    ensf_status st0 = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s);
+    if (st0 != ENSF_OK) return st0;
+    float *xbar = h->at<float>(L.xbar);
+    __nv_bfloat16 *zb_hi = tc_gram ? h->at<__nv_bfloat16>(L.zb_hi) : nullptr;
+    __nv_bfloat16 *zb_lo = (tc_gram && L.zb_lo) ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
+    // The tensor-core W X reads the step's noise as a pre-generated [n][d]
+    // slice: with a tensor-core Gram its idle epilogue warps write xi[k+1]
+    // while the MMAs of step k run; otherwise a separate launch does.
+    float *nslice = tc_wx ? h->at<float>(L.noise) : nullptr;
+    const bool pregen = tc_wx && !noise->buf;
     for (int k = 0; k < K; ++k) {
         ensf::StepCoef c = step_coef(k, K, eps, sigma_obs, obs_op);
-        ensf_status st = gram_softmax(h, out, n, prior, n, d, c, !tc_wx, s);
+        NoiseRequest nr;
+        if (pregen && tc_gram) {
+            nr.slice = nslice;
+            nr.seed = noise->seed;
+            nr.offset = noise->offset;
+            nr.k = k + 1;
+        } else if (pregen) {
+            ENSF_LAUNCH(h, P_NOISE, s,
+                        ensf::launch_noise_slice(noise->seed, noise->offset, k + 1, n, d, nslice, 1 << 30, s));
+        }
+        ensf_status st = gram_softmax(h, out, n, prior, n, d, c, !tc_wx, s, nr);
         if (st != ENSF_OK) return st;
         if (!tc_wx) {
             ENSF_LAUNCH(h, P_WXEM, s,
                         ensf::launch_wx_em_fp32(h->at<float>(L.w), n, prior, n, n, d, out, y, obs_mask, noise->buf,
                                                 noise->seed, noise->offset, c, s));
-            if (tc_gram) ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, zb_hi, zb_lo, d, s));
+            if (tc_gram)
+                ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, zb_hi, zb_lo, d, s, xbar,
+                                                                   step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha));
         } else {
-            ensf::TcWxArgs a;
-            a.wb_hi = h->at<__nv_bfloat16>(L.wb_hi);
-            a.wb_lo = L.wb_lo ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
-            a.xt_hi = h->at<__nv_bfloat16>(L.xt_hi);
-            a.xt_lo = L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) : nullptr;
-            a.ldw = ldt;
-            a.n = n;
-            a.d = d;
-            a.z = out;
-            a.zb_hi = zb_hi;
-            a.zb_lo = zb_lo;
-            a.y = y;
-            a.mask = obs_mask;
-            a.noise_buf = noise->buf;
-            a.seed = noise->seed;
-            a.offset = noise->offset;
-            a.coef = c;
-            a.err = h->err();
+            ensf::TcWxArgs a = wx_args(h, n, d, y, obs_mask, noise, out, c,
+                                       step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha, k);
             ENSF_LAUNCH(h, P_WXEM, s, ensf::launch_wx_em_tc(h->tc, a, h->sms, s));
         }
     }
     if (h->cfg.flags & ENSF_FLAG_CHECK_FINITE)
         ENSF_LAUNCH(h, P_CHECK, s, ensf::launch_check_finite(out, (int64_t)n * d, h->err(), s));
+    return ENSF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ensf_status ensf_analysis(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                          const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
+                          const ensf_noise *noise, float *out, void *stream) {
+    ensf_status st = analysis_validate(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, K, eps, noise, out);
+    if (st != ENSF_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!(h->cfg.flags & ENSF_FLAG_CUDA_GRAPH) || s == nullptr ||
+        cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return analysis_enqueue(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, K, eps, noise, out, s);
+    // capture the whole analysis into one graph; reuse the instantiated graph
+    // when only parameters changed (cudaGraphExecUpdate), else re-instantiate
+    ENSF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    st = analysis_enqueue(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, K, eps, noise, out, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != ENSF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    bool updated = false;
+    if (h->graph_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(h->graph_exec, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+    }
+    if (!updated) e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph_exec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    ENSF_CUDA(cudaGraphLaunch(h->graph_exec, s));
+    return ENSF_OK;
+}
+
+ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                          const uint8_t *obs_mask, int obs_op, float sigma_obs, float eps, const ensf_noise *noise,
+                          float *out, ensf_tuning *report, void *stream) {
+    ensf_status st = analysis_validate(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, 2, eps, noise, out);
+    if (st != ENSF_OK) return st;
+    if (report) memset(report, 0, sizeof(*report));
+    const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
+    if (!tc_gram && !tc_wx) return ENSF_OK;  // the CUDA-core path has nothing to tune
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(ENSF_EINVAL, "ensf_autotune: the stream is capturing; tune before capture");
+    const int K = 100;
+    st = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s);
+    if (st != ENSF_OK) return st;
+    ensf::StepCoef c = step_coef(K / 2, K, eps, sigma_obs, obs_op);
+    NoiseRequest nr;
+    const bool pregen = tc_wx && !noise->buf;
+    if (pregen && tc_gram) {
+        nr.slice = h->at<float>(h->L.noise);
+        nr.seed = noise->seed;
+        nr.offset = noise->offset;
+        nr.k = K / 2 + 1;
+    }
+    st = gram_softmax(h, out, n, prior, n, d, c, !tc_wx, s, nr);  // fills W for the W X trials
+    if (st != ENSF_OK) return st;
+    ensf::TcGramArgs ga;
+    if (tc_gram) {
+        const Layout &L = h->L;
+        ga.zb_hi = h->at<__nv_bfloat16>(L.zb_hi);
+        ga.zb_lo = L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
+        ga.xb_hi = h->at<__nv_bfloat16>(L.xb_hi);
+        ga.xb_lo = L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr;
+        ga.n = n;
+        ga.n_x = n;
+        ga.d = d;
+        ga.split3 = (h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
+        ga.partial = h->at<float>(L.partial);
+        ga.partial_cap = L.partial_floats;
+        ga.err = h->err();
+        ga.noise = nr.slice;
+        ga.seed = nr.seed;
+        ga.offset = nr.offset;
+        ga.noise_k = nr.k;
+    }
+    ensf::TcWxArgs wa;
+    if (tc_wx) {
+        if (pregen && !tc_gram)
+            ENSF_CUDA(ensf::launch_noise_slice(noise->seed, noise->offset, K / 2 + 1, n, d, h->at<float>(h->L.noise),
+                                               1 << 30, s));
+        wa = wx_args(h, n, d, y, obs_mask, noise, out, c, step_coef(K / 2 + 1, K, eps, sigma_obs, obs_op).alpha, K / 2);
+        if (noise->buf) wa.noise = noise->buf;  // any valid slice will do for timing
+    }
+    // judge each Gram shape by Gram + the softmax that consumes its partials
+    struct SoftmaxCtx {
+        ensf_handle *h;
+        int n;
+        ensf::StepCoef c;
+        bool tc_wx;
+    } sctx{h, n, c, tc_wx};
+    auto after = [](void *vp, int splits, int64_t part_stride, int ldp, cudaStream_t st) -> cudaError_t {
+        const SoftmaxCtx &x = *static_cast<const SoftmaxCtx *>(vp);
+        const Layout &L = x.h->L;
+        return ensf::launch_softmax_rows(x.h->at<float>(L.partial), splits, part_stride, ldp, x.n, x.n,
+                                         x.h->at<double>(L.norms), x.c.alpha_d, x.c.inv_2beta2_d,
+                                         x.tc_wx ? nullptr : x.h->at<float>(L.w), x.n,
+                                         x.tc_wx ? x.h->at<__nv_bfloat16>(L.wb_hi) : nullptr,
+                                         (x.tc_wx && L.wb_lo) ? x.h->at<__nv_bfloat16>(L.wb_lo) : nullptr,
+                                         (int)round_up(x.n, 8), st);
+    };
+    ensf::TcTuneReport r;
+    cudaError_t e = ensf::tc_autotune(h->tc, tc_gram ? &ga : nullptr, tc_wx ? &wa : nullptr, h->sms, s, &r,
+                                      tc_gram ? +after : nullptr, &sctx);
+    if (e != cudaSuccess) return cuda_fail(e, "tc_autotune");
+    if (report) {
+        report->gram_tile_n = r.gram_bn;
+        report->gram_stages = r.gram_stages;
+        report->gram_splits = r.gram_splits;
+        report->gram_ms = r.gram_ms;
+        report->wx_tile_n = r.wx_bn;
+        report->wx_ms = r.wx_ms;
+    }
     return ENSF_OK;
 }
 
@@ -398,15 +602,20 @@ ensf_status ensf_weights(ensf_handle *h, const float *z, int n, const float *pri
         return fail(ENSF_EINVAL, "ensf_weights: need t in (0, 1] and eps in (0, 1)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Layout &L = h->L;
-    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n_x, d, h->at<double>(L.norms), s));
+    const double td = (double)t, alpha = 1.0 - td * (1.0 - (double)eps);
+    float *xbar = h->at<float>(L.xbar);
+    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_col_mean(prior, n_x, d, xbar, s));
+    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n_x, d, h->at<double>(L.norms), s, xbar));
     if (is_tc(h->cfg.gram)) {
         ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(prior, n_x, d, h->at<__nv_bfloat16>(L.xb_hi),
-                                                           L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s));
+                                                           L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s,
+                                                           xbar, 1.0f));
         ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(z, n, d, h->at<__nv_bfloat16>(L.zb_hi),
-                                                           L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s));
+                                                           L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s,
+                                                           xbar, (float)alpha));
     }
-    const double td = (double)t, alpha = 1.0 - td * (1.0 - (double)eps);
     ensf::StepCoef c{};
+    c.alpha = (float)alpha;
     c.alpha_d = alpha;
     c.inv_2beta2_d = 1.0 / (2.0 * td);
     // the FP32 weights go to the handle's W scratch, then to the caller

@@ -16,10 +16,19 @@ cudaError_t launch_init_particles(float *z, int n, int64_t d, const float *noise
                                   uint64_t seed, uint32_t offset, cudaStream_t s);
 cudaError_t launch_philox_normal(uint64_t seed, uint32_t offset, int k0, int count, int n,
                                  int64_t d, float *out, cudaStream_t s);
-cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s);
-// partial[s][i][j] = sum over slice s of z[i][c] x[j][c]   (FP32 CUDA cores)
+// out[i][c] = xi[k][i][c] (one slice), at most max_blocks blocks of 256 threads
+cudaError_t launch_noise_slice(uint64_t seed, uint32_t offset, int k, int n, int64_t d, float *out,
+                               int max_blocks, cudaStream_t s);
+// out[j] = |x_j - centre|^2 in FP64 (centre may be NULL)
+cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s,
+                             const float *centre = nullptr);
+// m[c] = mean over the n rows of x[.][c]
+cudaError_t launch_col_mean(const float *x, int n, int64_t d, float *m, cudaStream_t s);
+// partial[s][i][j] = sum over slice s of (z[i][c] - alpha m[c]) (x[j][c] - m[c])
+// (FP32 CUDA cores; m = centre, NULL for none)
 cudaError_t launch_gram_fp32(const float *z, int n, const float *x, int n_x, int64_t d,
-                             int splits, float *partial, cudaStream_t s);
+                             int splits, float *partial, cudaStream_t s, const float *centre = nullptr,
+                             float alpha = 0.0f);
 // logits from `splits` partial Grams (row stride ldp) + FP64 norms, row softmax;
 // writes W FP32 [n][ldw] and, if w_hi != NULL, BF16 W_hi/W_lo [n][ldwb].
 cudaError_t launch_softmax_rows(const float *partial, int splits, int64_t part_stride, int ldp,
@@ -31,9 +40,11 @@ cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, in
                               float *z, const float *y, const uint8_t *mask,
                               const float *noise_buf, uint64_t seed, uint32_t offset,
                               const StepCoef &c, cudaStream_t s);
-// FP32 -> (hi, lo) BF16 split, row-major copy with output row stride ldo
+// FP32 -> (hi, lo) BF16 split of x - scale * centre (centre may be NULL),
+// row-major copy with output row stride ldo
 cudaError_t launch_split_bf16(const float *x, int rows, int64_t cols, __nv_bfloat16 *hi,
-                              __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s);
+                              __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s,
+                              const float *centre = nullptr, float scale = 0.0f);
 // Transposed split: xT_hi[c][j] = bf16(x[j][c]), xT_lo likewise (ldo = row stride of xT)
 cudaError_t launch_split_bf16_transpose(const float *x, int rows, int64_t cols,
                                         __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ldo,

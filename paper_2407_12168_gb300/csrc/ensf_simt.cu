@@ -19,13 +19,19 @@ constexpr int kTileK = 16;   // reduction depth per shared-memory stage
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
 // ---------------------------------------------------------------------------
-// |x_j|^2 in FP64: one block per row, float4 loads, fixed-order tree reduce.
+// |x_j - m|^2 in FP64 (m = the centre vector, or 0): one block per row,
+// float4 loads, the difference rounded to FP32 as the Gram operands are,
+// fixed-order tree reduce.
 __global__ void __launch_bounds__(256) k_row_norms(const float *__restrict__ x, int64_t d,
-                                                   double *__restrict__ out) {
+                                                   const float *__restrict__ centre, double *__restrict__ out) {
     const float *row = x + (int64_t)blockIdx.x * d;
     double acc = 0.0;
     for (int64_t c = (int64_t)threadIdx.x * 4; c < d; c += 256 * 4) {
         float4 v = ld4(row + c);
+        if (centre) {
+            const float4 m = ld4(centre + c);
+            v.x -= m.x; v.y -= m.y; v.z -= m.z; v.w -= m.w;
+        }
         acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
     }
     __shared__ double red[256];
@@ -36,6 +42,16 @@ __global__ void __launch_bounds__(256) k_row_norms(const float *__restrict__ x, 
         __syncthreads();
     }
     if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// Column means m[c] = (1/n) sum_j x[j][c], FP64 accumulation, FP32 result.
+__global__ void __launch_bounds__(256) k_col_mean(const float *__restrict__ x, int n, int64_t d,
+                                                  float *__restrict__ m) {
+    const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (c >= d) return;
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc += (double)x[(int64_t)j * d + c];
+    m[c] = (float)(acc / (double)n);
 }
 
 // ---------------------------------------------------------------------------
@@ -52,6 +68,27 @@ __global__ void k_philox_normal(uint64_t seed, uint32_t offset, int k0, int n, i
     for (int r = 0; r < 4; ++r) {
         int i = qd * 4 + r;
         if (i < n) out[((int64_t)kk * n + i) * d + c] = vv[r];
+    }
+}
+
+// One noise slice out[i][c] = xi[k][i][c] with a bounded grid (grid-stride
+// over (particle quad, column) pairs) so that it can share the SMs with a
+// concurrently running Gram without crowding out its blocks.
+__global__ void __launch_bounds__(256) k_noise_slice(uint64_t seed, uint32_t offset, int k, int n, int64_t d,
+                                                     float *__restrict__ out) {
+    const int64_t quads = (n + 3) / 4;
+    const int64_t total = quads * d;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int qd = (int)(idx / d);
+        const int64_t c = idx - (int64_t)qd * d;
+        float4 v = noise4(seed, offset, k, c, qd);
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = qd * 4 + r;
+            if (i < n) out[(int64_t)i * d + c] = vv[r];
+        }
     }
 }
 
@@ -85,7 +122,7 @@ __global__ void k_init_particles(float *__restrict__ z, int n, int64_t d,
 // 64x64 output tile per block, 4x4 per thread, reduction staged 16 deep.
 __global__ void __launch_bounds__(256)
 k_gram_fp32(const float *__restrict__ z, int n, const float *__restrict__ x, int n_x, int64_t d,
-            int64_t slice_len, float *__restrict__ partial) {
+            int64_t slice_len, const float *__restrict__ centre, float alpha, float *__restrict__ partial) {
     __shared__ __align__(16) float As[kTileK][kTile + 4];
     __shared__ __align__(16) float Bs[kTileK][kTile + 4];
     const int tid = threadIdx.x;
@@ -100,6 +137,11 @@ k_gram_fp32(const float *__restrict__ z, int n, const float *__restrict__ x, int
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
         if (i0 + lr < n && c < c_end) a = ld4(z + (int64_t)(i0 + lr) * d + c);
         if (j0 + lr < n_x && c < c_end) b = ld4(x + (int64_t)(j0 + lr) * d + c);
+        if (centre && c < c_end) {  // z - alpha m and x - m: the distance is unchanged
+            const float4 m = ld4(centre + c);
+            a.x -= alpha * m.x; a.y -= alpha * m.y; a.z -= alpha * m.z; a.w -= alpha * m.w;
+            b.x -= m.x; b.y -= m.y; b.z -= m.z; b.w -= m.w;
+        }
         As[lk + 0][lr] = a.x; As[lk + 1][lr] = a.y; As[lk + 2][lr] = a.z; As[lk + 3][lr] = a.w;
         Bs[lk + 0][lr] = b.x; Bs[lk + 1][lr] = b.y; Bs[lk + 2][lr] = b.z; Bs[lk + 3][lr] = b.w;
         __syncthreads();
@@ -139,13 +181,37 @@ k_softmax_rows(const float *__restrict__ partial, int splits, int64_t part_strid
     extern __shared__ double lg[];
     __shared__ double red[256];
     const int i = blockIdx.x, tid = threadIdx.x;
+    // sum of the split-K partials: when the row is short, `groups` threads
+    // share one column j, each summing a fixed range of splits; the group
+    // sums are then added in group order (deterministic)
+    const int groups = n_x >= 256 ? 1 : min(256 / n_x, splits);
+    const int per = (splits + groups - 1) / groups;
     double lmax = -DBL_MAX;
-    for (int j = tid; j < n_x; j += 256) {
-        double g = 0.0;
-        for (int s = 0; s < splits; ++s) g += (double)partial[s * part_stride + (int64_t)i * ldp + j];
-        double l = (2.0 * alpha * g - alpha * alpha * norms[j]) * inv_2beta2;
-        lg[j] = l;
-        lmax = fmax(lmax, l);
+    if (groups == 1) {
+        for (int j = tid; j < n_x; j += 256) {
+            double g = 0.0;
+            for (int s = 0; s < splits; ++s) g += (double)partial[s * part_stride + (int64_t)i * ldp + j];
+            double l = (2.0 * alpha * g - alpha * alpha * norms[j]) * inv_2beta2;
+            lg[j] = l;
+            lmax = fmax(lmax, l);
+        }
+    } else {
+        const int j = tid % n_x, grp = tid / n_x;
+        if (grp < groups) {
+            double g = 0.0;
+            const int s0 = grp * per, s1 = min(splits, s0 + per);
+            for (int s = s0; s < s1; ++s) g += (double)partial[s * part_stride + (int64_t)i * ldp + j];
+            red[grp * n_x + j] = g;
+        }
+        __syncthreads();
+        if (tid < n_x) {
+            double g = 0.0;
+            for (int q = 0; q < groups; ++q) g += red[q * n_x + tid];
+            double l = (2.0 * alpha * g - alpha * alpha * norms[tid]) * inv_2beta2;
+            lg[tid] = l;
+            lmax = l;
+        }
+        __syncthreads();
     }
     red[tid] = lmax;
     __syncthreads();
@@ -259,11 +325,16 @@ k_wx_em_fp32(const float *__restrict__ w, int ldw, const float *__restrict__ x, 
 // ---------------------------------------------------------------------------
 // x = hi + lo with hi = bf16(x), lo = bf16(x - hi); row-major, out stride ldo.
 __global__ void k_split_bf16(const float *__restrict__ x, int64_t cols, __nv_bfloat16 *__restrict__ hi,
-                             __nv_bfloat16 *__restrict__ lo, int64_t ldo) {
+                             __nv_bfloat16 *__restrict__ lo, int64_t ldo, const float *__restrict__ centre,
+                             float scale) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     if (q * 4 >= cols) return;
     float4 v = ld4(x + (int64_t)r * cols + q * 4);
+    if (centre) {  // split x - scale * m
+        const float4 m = ld4(centre + q * 4);
+        v.x -= scale * m.x; v.y -= scale * m.y; v.z -= scale * m.z; v.w -= scale * m.w;
+    }
     float vv[4] = {v.x, v.y, v.z, v.w};
     __align__(8) __nv_bfloat16 h[4], l[4];
 #pragma unroll
@@ -367,17 +438,26 @@ cudaError_t launch_philox_normal(uint64_t seed, uint32_t offset, int k0, int cou
     return cudaGetLastError();
 }
 
-cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s) {
-    k_row_norms<<<n, 256, 0, s>>>(x, d, out);
+cudaError_t launch_noise_slice(uint64_t seed, uint32_t offset, int k, int n, int64_t d, float *out,
+                               int max_blocks, cudaStream_t s) {
+    const int64_t total = (int64_t)((n + 3) / 4) * d;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > max_blocks) blocks = max_blocks;
+    k_noise_slice<<<(unsigned)blocks, 256, 0, s>>>(seed, offset, k, n, d, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s, const float *centre) {
+    k_row_norms<<<n, 256, 0, s>>>(x, d, centre, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gram_fp32(const float *z, int n, const float *x, int n_x, int64_t d, int splits,
-                             float *partial, cudaStream_t s) {
+                             float *partial, cudaStream_t s, const float *centre, float alpha) {
     int64_t slice = (d + splits - 1) / splits;
     slice = (slice + kTileK - 1) / kTileK * kTileK;
     dim3 grid((unsigned)((n_x + kTile - 1) / kTile), (unsigned)((n + kTile - 1) / kTile), (unsigned)splits);
-    k_gram_fp32<<<grid, 256, 0, s>>>(z, n, x, n_x, d, slice, partial);
+    k_gram_fp32<<<grid, 256, 0, s>>>(z, n, x, n_x, d, slice, centre, alpha, partial);
     return cudaGetLastError();
 }
 
@@ -404,9 +484,9 @@ cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, in
 }
 
 cudaError_t launch_split_bf16(const float *x, int rows, int64_t cols, __nv_bfloat16 *hi,
-                              __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s) {
+                              __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s, const float *centre, float scale) {
     dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)rows);
-    k_split_bf16<<<grid, 256, 0, s>>>(x, cols, hi, lo, ldo);
+    k_split_bf16<<<grid, 256, 0, s>>>(x, cols, hi, lo, ldo, centre, scale);
     return cudaGetLastError();
 }
 
@@ -423,6 +503,11 @@ cudaError_t launch_check_finite(const float *z, int64_t count, int *err_word, cu
 }
 
 int stats_blocks(int64_t d) { return (int)((d + 255) / 256); }
+
+cudaError_t launch_col_mean(const float *x, int n, int64_t d, float *m, cudaStream_t s) {
+    k_col_mean<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(x, n, d, m);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ensemble_stats(const float *z, int n, int64_t d, const float *truth, double *mean,
                                   double *rmse, double *scratch, cudaStream_t s) {

@@ -14,7 +14,7 @@
 // a_hi = bf16(a), a_lo = bf16(a - a_hi); the product uses a_hi b_hi + a_hi b_lo
 // + a_lo b_hi (the a_lo b_lo term is below FP32 rounding), accumulated in FP32.
 //
-// Kernel structure (one output tile of 128 x BN per CTA, 6 warps):
+// Gram kernel structure (one output tile of 128 x BN per CTA, 10 warps):
 //   warp 0     TMA producer: 128B-swizzled tiles of A and B (hi, lo planes)
 //              into a STAGES-deep shared-memory ring, mbarrier transaction counts
 //   warp 1     allocates BN TMEM columns; one thread issues tcgen05.mma
@@ -23,12 +23,18 @@
 //              each ring slot and finally signals the accumulator
 //   warps 2-5  epilogue: tcgen05.ld 32 columns at a time from their TMEM lane
 //              quarter, then the per-kernel epilogue
+//   warps 6-9  (with warps 2-5 while the MMAs run) the next step's noise slice
+// The W X kernel is persistent with 16 epilogue warps (see below).
 // Every mbarrier wait is bounded by %globaltimer: on expiry the CTA records
 // ENSF_ETIMEOUT in the error word, drains its own copies, frees TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "ensf_tc.h"
 
@@ -38,7 +44,7 @@ namespace {
 
 constexpr int BM = 128;        // tile rows (particles)
 constexpr int BK = 64;         // k-block: 64 BF16 = one 128-byte swizzle row
-constexpr int kThreads = 192;  // 6 warps
+constexpr int kGramThreads = 320;  // Gram: 6 warps + 4 warps that only generate noise
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr int kStatusTimeout = 5;  // ENSF_ETIMEOUT
 
@@ -164,6 +170,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    __syncwarp();
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // ----------------------------------------------------- shared-memory plan
@@ -298,10 +319,48 @@ struct GramParams {
     int kb_per_split;  // k-blocks per split (last split may hold fewer)
     float *partial;    // [splits][n][n_x]
     int *err;
+    // optional: the noise slice xi[noise_k][i][c] of the next Euler-Maruyama
+    // step, written by the epilogue warps while the MMAs run (NULL: none)
+    float *noise;
+    uint64_t seed;
+    uint32_t offset;
+    int noise_k;
+    int64_t d;
 };
 
+// This CTA's share of the next step's noise slice, written by the 8 warps
+// (epilogue warps 2-5 and noise warps 6-9) that are idle while the MMAs run:
+// a contiguous range of state columns for every particle quad, two
+// independent Philox blocks per iteration.
+__device__ __forceinline__ void gram_noise_share(const GramParams &p) {
+    const int blocks = gridDim.x * gridDim.y * gridDim.z;
+    const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int64_t per = (p.d + blocks - 1) / blocks;
+    const int64_t c0 = static_cast<int64_t>(b) * per;
+    const int64_t c1 = c0 + per < p.d ? c0 + per : p.d;
+    const int quads = (p.n + 3) / 4;
+    const int et = threadIdx.x - 64;  // 0 .. 255
+    constexpr int kStride = kGramThreads - 64;
+    for (int qd = 0; qd < quads; ++qd) {
+        for (int64_t col = c0 + et; col < c1; col += 2 * kStride) {
+            const int64_t col2 = col + kStride;
+            const float4 v = noise4(p.seed, p.offset, p.noise_k, col, qd);
+            const float4 v2 = col2 < c1 ? noise4(p.seed, p.offset, p.noise_k, col2, qd) : v;
+            const float vv[4] = {v.x, v.y, v.z, v.w}, vv2[4] = {v2.x, v2.y, v2.z, v2.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = qd * 4 + r;
+                if (i < p.n) {
+                    p.noise[static_cast<int64_t>(i) * p.d + col] = vv[r];
+                    if (col2 < c1) p.noise[static_cast<int64_t>(i) * p.d + col2] = vv2[r];
+                }
+            }
+        }
+    }
+}
+
 template <int BN, int STAGES, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kGramThreads, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
           const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
     using P = Plan<BN, STAGES, SPLIT>;
@@ -319,6 +378,10 @@ k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUte
     } else if (warp == 1) {
         if (lane == 0) mma_loop<BN, STAGES, SPLIT>(c, tmem, nkb, p.err);
     } else {
+        if (p.noise) gram_noise_share(p);
+        if (warp >= 6) {
+            // noise-only warps: nothing else to do
+        } else {
         const int q = warp & 3;  // TMEM lane quarter this warp may read
         const int row = m0 + q * 32 + lane;
         const bool ok = mbar_wait(c.accum, 0, c.abort_flag, p.err);
@@ -337,6 +400,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUte
                 }
             }
         }
+        }
     }
     teardown<BN>(tmem, warp);
 }
@@ -345,10 +409,12 @@ k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUte
 // Persistent kernel over tiles of U^T = X^T W^T: MMA rows (TMEM lanes) are 128
 // state columns c, MMA columns are BN particles i.  An epilogue thread owns one
 // state column, so for each particle the 32 lanes of a warp touch 32
-// consecutive floats of z[i][:] (coalesced), and y[c], mask[c] are read once
-// per tile.  Two TMEM accumulators (columns 0 and 256) let the epilogue of one
-// tile run while the MMAs of the next accumulate.
-constexpr int kEpiWarps = 8;                       // two per TMEM lane quarter
+// consecutive floats of z[i][:] and of the noise slice (coalesced), and y[c],
+// mask[c] are read once per tile.  Two TMEM accumulators (columns 0 and 256)
+// let the epilogue of one tile run while the MMAs of the next accumulate.  The
+// noise of the step arrives pre-generated (a [n][d] slice), so the epilogue is
+// loads, the score, the update and stores.
+constexpr int kEpiWarps = 16;                      // four per TMEM lane quarter
 constexpr int kWxThreads = 64 + 32 * kEpiWarps;    // producer, MMA, epilogue
 constexpr int kWxTmemCols = 512;
 
@@ -374,9 +440,9 @@ struct WxParams {
     __nv_bfloat16 *zb_hi, *zb_lo;
     const float *y;
     const uint8_t *mask;
-    const float *noise_buf;
-    uint64_t seed;
-    uint32_t offset;
+    const float *noise;  // xi[k+1] slice [n][d]
+    const float *centre; // Gram centre m [d] or NULL
+    float alpha_next;    // z_hi/z_lo carry z - alpha_next m for the next Gram
     StepCoef coef;
     int *err;
 };
@@ -492,8 +558,8 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
     } else {
         const int ew = warp - 2;            // 0 .. kEpiWarps-1
         const int q = warp & 3;             // TMEM lane quarter this warp may read
-        const int half = ew >> 2;           // which half of the BN particle columns
-        constexpr int kCols = BN / 2;
+        const int part = ew >> 2;           // which quarter of the BN particle columns
+        constexpr int kCols = BN / 4;       // 16, 32 or 64 particle columns per warp
         const StepCoef &cf = p.coef;
         int lt = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++lt) {
@@ -506,45 +572,35 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
             const bool cok = c < p.d;
             const float yc = cok ? p.y[c] : 0.f;
             const bool obs = cok && (p.mask == nullptr || p.mask[c] != 0);
+            const float shift = (cok && p.centre) ? p.alpha_next * p.centre[c] : 0.f;
 #pragma unroll 1
-            for (int cc = half * kCols; cc < (half + 1) * kCols; cc += 32) {
-                float u[32];
-                tmem_ld32(tmem + slot * 256 + (static_cast<uint32_t>(q * 32) << 16) + cc, u);
+            for (int cc = part * kCols; cc < (part + 1) * kCols; cc += 16) {
+                float u[16];
+                tmem_ld16(tmem + slot * 256 + (static_cast<uint32_t>(q * 32) << 16) + cc, u);
                 const int i0 = n0 + cc;
                 if (!cok || i0 >= p.n) continue;
-                float zv[32];
+                const int cnt = p.n - i0 < 16 ? p.n - i0 : 16;
+                const int64_t base = static_cast<int64_t>(i0) * p.d + c;
+                float zv[16], xi[16];
 #pragma unroll
-                for (int e = 0; e < 32; ++e)
-                    zv[e] = (i0 + e < p.n) ? p.z[static_cast<int64_t>(i0 + e) * p.d + c] : 0.f;
-#pragma unroll
-                for (int e4 = 0; e4 < 8; ++e4) {
-                    const int ib = i0 + e4 * 4;
-                    if (ib >= p.n) break;
-                    float xi[4];
-                    if (p.noise_buf) {
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-                            xi[r] = (ib + r < p.n)
-                                        ? p.noise_buf[(static_cast<int64_t>(cf.k + 1) * p.n + ib + r) * p.d + c]
-                                        : 0.f;
-                    } else {
-                        const float4 v = noise4(p.seed, p.offset, cf.k + 1, c, ib >> 2);
-                        xi[0] = v.x; xi[1] = v.y; xi[2] = v.z; xi[3] = v.w;
+                for (int e = 0; e < 16; ++e) {
+                    if (e < cnt) {
+                        zv[e] = p.z[base + e * p.d];
+                        xi[e] = p.noise[base + e * p.d];
                     }
+                }
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int i = ib + r;
-                        if (i >= p.n) break;
-                        const int e = e4 * 4 + r;
-                        const float g = obs ? lik_score(cf.obs_op, zv[e], yc, cf.inv_r) : 0.f;
-                        const float zn = em_update(cf, zv[e], u[e], g, xi[r]);
-                        const int64_t off = static_cast<int64_t>(i) * p.d + c;
-                        p.z[off] = zn;
-                        if (p.zb_hi) {
-                            const __nv_bfloat16 hi = __float2bfloat16_rn(zn);
-                            p.zb_hi[off] = hi;
-                            if (p.zb_lo) p.zb_lo[off] = __float2bfloat16_rn(zn - __bfloat162float(hi));
-                        }
+                for (int e = 0; e < 16; ++e) {
+                    if (e >= cnt) break;
+                    const float g = obs ? lik_score(cf.obs_op, zv[e], yc, cf.inv_r) : 0.f;
+                    const float zn = em_update(cf, zv[e], u[e], g, xi[e]);
+                    const int64_t off = base + e * p.d;
+                    p.z[off] = zn;
+                    if (p.zb_hi) {
+                        const float zc = zn - shift;
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
+                        p.zb_hi[off] = hi;
+                        if (p.zb_lo) p.zb_lo[off] = __float2bfloat16_rn(zc - __bfloat162float(hi));
                     }
                 }
             }
@@ -566,6 +622,10 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
 // =================================================================== host
 struct TcContext {
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    // launch shapes picked by tc_autotune, keyed by problem shape
+    std::mutex mu;
+    std::map<std::tuple<int, int, int64_t, bool>, GramChoice> gram_tuned;  // (n, n_x, d, split3)
+    std::map<std::tuple<int, int64_t, bool>, int> wx_tuned;                 // (n, d, split) -> BN
 };
 
 cudaError_t tc_context_create(TcContext **out) {
@@ -619,7 +679,7 @@ cudaError_t run_gram(const CUtensorMap (&maps)[4], const GramParams &p, dim3 gri
     auto kern = k_gram_tc<BN, STAGES, SPLIT>;
     cudaError_t e = set_smem(kern, P::kBytes);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
+    kern<<<grid, kGramThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
     return cudaGetLastError();
 }
 
@@ -658,10 +718,19 @@ int choose_splits(int tiles, int kblocks, int sms, int64_t per_split_floats, int
 
 }  // namespace
 
-cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *splits, int64_t *part_stride, int *ldp,
-                           cudaStream_t s) {
-    if (!ctx) return cudaErrorInvalidValue;
-    const int BN = a.n_x <= 128 ? 128 : 256;
+namespace {
+
+GramChoice default_gram_choice(const TcGramArgs &a) {
+    GramChoice g;
+    g.bn = a.n_x <= 128 ? 128 : 256;
+    g.stages = a.split3 ? (g.bn == 256 ? 2 : 3) : (g.bn == 256 ? 4 : 6);
+    g.splits = 0;  // cost model
+    return g;
+}
+
+cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const GramChoice &ch, int *splits,
+                        int64_t *part_stride, int *ldp, cudaStream_t s) {
+    const int BN = ch.bn;
     CUtensorMap maps[4];
     cudaError_t e;
     if ((e = make_map(ctx, &maps[0], a.zb_hi, a.d, a.n, a.d, BM)) != cudaSuccess) return e;
@@ -673,12 +742,20 @@ cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *sp
     p.n = a.n;
     p.n_x = a.n_x;
     p.kblocks = static_cast<int>((a.d + BK - 1) / BK);
-    const int S = choose_splits(mt * nt, p.kblocks, sms, static_cast<int64_t>(a.n) * a.n_x, a.partial_cap);
+    const int64_t per_split = static_cast<int64_t>(a.n) * a.n_x;
+    int S = ch.splits > 0 ? ch.splits : choose_splits(mt * nt, p.kblocks, sms, per_split, a.partial_cap);
+    S = std::max(1, std::min<int>(S, static_cast<int>(std::min<int64_t>(p.kblocks, a.partial_cap / per_split))));
     p.kb_per_split = (p.kblocks + S - 1) / S;
+    S = (p.kblocks + p.kb_per_split - 1) / p.kb_per_split;  // splits that hold work
     p.partial = a.partial;
     p.err = a.err;
+    p.noise = a.noise;
+    p.seed = a.seed;
+    p.offset = a.offset;
+    p.noise_k = a.noise_k;
+    p.d = a.d;
     *splits = S;
-    *part_stride = static_cast<int64_t>(a.n) * a.n_x;
+    *part_stride = per_split;
     *ldp = a.n_x;
     dim3 grid(mt, nt, S);
     if (a.split3) {
@@ -689,10 +766,32 @@ cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *sp
     return run_gram<128, 6, false>(maps, p, grid, s);
 }
 
+}  // namespace
+
+cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *splits, int64_t *part_stride, int *ldp,
+                           cudaStream_t s) {
+    if (!ctx) return cudaErrorInvalidValue;
+    GramChoice ch = default_gram_choice(a);
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        auto it = ctx->gram_tuned.find(std::make_tuple(a.n, a.n_x, a.d, a.split3));
+        if (it != ctx->gram_tuned.end()) ch = it->second;
+    }
+    return gram_launch(ctx, a, sms, ch, splits, part_stride, ldp, s);
+}
+
 cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStream_t s) {
     if (!ctx) return cudaErrorInvalidValue;
     const bool split = a.wb_lo != nullptr && a.xt_lo != nullptr;
-    const int BN = a.n <= 64 ? 64 : (a.n <= 128 ? 128 : 256);
+    int BN = a.n <= 64 ? 64 : (a.n <= 128 ? 128 : 256);
+    if (a.force_bn) {
+        BN = a.force_bn;
+    } else {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        auto it = ctx->wx_tuned.find(std::make_tuple(a.n, a.d, split));
+        if (it != ctx->wx_tuned.end()) BN = it->second;
+    }
+    if (BN != 64 && BN != 128 && BN != 256) return cudaErrorInvalidValue;
     // A = X^T [d][ldw] (state columns; K = n_x members), B = W [n][ldw] (particles)
     const int n_x = a.n;
     CUtensorMap maps[4];
@@ -712,11 +811,12 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     p.zb_lo = a.zb_lo;
     p.y = a.y;
     p.mask = a.mask;
-    p.noise_buf = a.noise_buf;
-    p.seed = a.seed;
-    p.offset = a.offset;
+    p.noise = a.noise;
+    p.centre = a.centre;
+    p.alpha_next = a.alpha_next;
     p.coef = a.coef;
     p.err = a.err;
+    if (!p.noise) return cudaErrorInvalidValue;
     if (split) {
         if (BN == 256) return run_wx<256, 2, true>(maps, p, sms, s);
         if (BN == 128) return run_wx<128, 3, true>(maps, p, sms, s);
@@ -725,6 +825,93 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     if (BN == 256) return run_wx<256, 4, false>(maps, p, sms, s);
     if (BN == 128) return run_wx<128, 6, false>(maps, p, sms, s);
     return run_wx<64, 8, false>(maps, p, sms, s);
+}
+
+// Time `launch` (reps launches after one warm-up) with events on stream s; ms per launch.
+template <class F>
+static cudaError_t time_launches(F launch, int reps, cudaStream_t s, float *ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    if (e == cudaSuccess) *ms /= reps;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return e;
+}
+
+cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, int sms, cudaStream_t s,
+                        TcTuneReport *rep, AfterGram after_gram, void *after_ctx) {
+    if (!ctx) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    if (g) {
+        const GramChoice base = default_gram_choice(*g);
+        GramChoice best = base;
+        float best_ms = 1e30f;
+        for (int bn : {128, 256}) {
+            if (bn == 256 && g->n_x <= 128) continue;
+            const int stages = g->split3 ? (bn == 256 ? 2 : 3) : (bn == 256 ? 4 : 6);
+            const int mt = (g->n + BM - 1) / BM, nt = (g->n_x + bn - 1) / bn;
+            const int kblocks = static_cast<int>((g->d + BK - 1) / BK);
+            const int s0 = choose_splits(mt * nt, kblocks, sms, static_cast<int64_t>(g->n) * g->n_x, g->partial_cap);
+            for (int sp : {s0, std::max(1, s0 / 2), s0 * 2, std::max(1, (s0 * 3) / 4), (s0 * 3) / 2,
+                           std::max(1, s0 / 4), std::max(1, s0 / 8)}) {
+                GramChoice ch{bn, stages, sp};
+                int splits = 0, ldp = 0;
+                int64_t ps = 0;
+                float ms = 0.f;
+                e = time_launches(
+                    [&] {
+                        cudaError_t r = gram_launch(ctx, *g, sms, ch, &splits, &ps, &ldp, s);
+                        if (r == cudaSuccess && after_gram) r = after_gram(after_ctx, splits, ps, ldp, s);
+                        return r;
+                    },
+                    3, s, &ms);
+                if (e != cudaSuccess) return e;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = ch;
+                    best.splits = splits;
+                }
+            }
+        }
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        ctx->gram_tuned[std::make_tuple(g->n, g->n_x, g->d, g->split3)] = best;
+        if (rep) {
+            rep->gram_bn = best.bn;
+            rep->gram_stages = best.stages;
+            rep->gram_splits = best.splits;
+            rep->gram_ms = best_ms;
+        }
+    }
+    if (w) {
+        const bool split = w->wb_lo != nullptr && w->xt_lo != nullptr;
+        int best_bn = 0;
+        float best_ms = 1e30f;
+        for (int bn : {64, 128, 256}) {
+            TcWxArgs a = *w;
+            a.force_bn = bn;
+            float ms = 0.f;
+            e = time_launches([&] { return launch_wx_em_tc(ctx, a, sms, s); }, 3, s, &ms);
+            if (e != cudaSuccess) return e;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_bn = bn;
+            }
+        }
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        ctx->wx_tuned[std::make_tuple(w->n, w->d, split)] = best_bn;
+        if (rep) {
+            rep->wx_bn = best_bn;
+            rep->wx_ms = best_ms;
+        }
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ensf

@@ -12,6 +12,19 @@ namespace ensf {
 
 struct TcContext;  // tensor-map encoder and per-shape launch choices
 
+struct GramChoice {
+    int bn = 0;      // output tile width (128 or 256 forecast members)
+    int stages = 0;  // shared-memory ring depth
+    int splits = 0;  // split-K slices over d (0: cost model)
+};
+
+struct TcTuneReport {
+    int gram_bn = 0, gram_stages = 0, gram_splits = 0;
+    float gram_ms = 0.f;
+    int wx_bn = 0;
+    float wx_ms = 0.f;
+};
+
 cudaError_t tc_context_create(TcContext **out);
 void tc_context_destroy(TcContext *ctx);
 
@@ -27,6 +40,12 @@ struct TcGramArgs {
     float *partial;                      // [splits][n][ldp]
     int64_t partial_cap;                 // capacity in floats
     int *err;
+    // optional: write the noise slice xi[noise_k] [n][d] of the next step
+    // with the otherwise idle epilogue warps (noise NULL: skip)
+    float *noise;
+    uint64_t seed;
+    uint32_t offset;
+    int noise_k;
 };
 
 struct TcWxArgs {
@@ -39,15 +58,26 @@ struct TcWxArgs {
     __nv_bfloat16 *zb_hi, *zb_lo;        // split copies of the updated particles (NULL: skip)
     const float *y;
     const uint8_t *mask;
-    const float *noise_buf;
-    uint64_t seed;
-    uint32_t offset;
+    const float *noise;                  // xi[k+1] as a [n][d] slice (pre-generated)
+    const float *centre;                 // [d] Gram centre m (NULL: none); z_hi/z_lo split z - alpha_next m
+    float alpha_next;                    // alpha of the next step's Gram
     StepCoef coef;
     int *err;
+    int force_bn = 0;                    // autotuner: particle tile width to use (0: tuned/default)
 };
 
 cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *splits,
                            int64_t *part_stride, int *ldp, cudaStream_t s);
 cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStream_t s);
+
+// Times the candidate launch shapes of the Gram (tile width, ring depth,
+// split count) and of W X (particle tile width) on these very operands and
+// records the fastest per problem shape; later launches of that shape use it.
+// Synchronises `s`; either argument may be NULL.
+// `after_gram(splits, part_stride, ldp)` enqueues whatever consumes the
+// partials (the row softmax), so that a shape is judged by Gram + reduction.
+using AfterGram = cudaError_t (*)(void *ctx, int splits, int64_t part_stride, int ldp, cudaStream_t s);
+cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, int sms, cudaStream_t s,
+                        TcTuneReport *rep, AfterGram after_gram = nullptr, void *after_ctx = nullptr);
 
 }  // namespace ensf

@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = range(7)
 OBS_IDENTITY, OBS_ARCTAN = 0, 1
 PREC_FP32, PREC_SPLIT_BF16X3, PREC_BF16 = 0, 1, 2
 FLAG_CHECK_FINITE = 1
+FLAG_CUDA_GRAPH = 2
 
 PRECISIONS = {"fp32": PREC_FP32, "split": PREC_SPLIT_BF16X3, "bf16": PREC_BF16}
 
@@ -38,6 +39,11 @@ class EnsfProfileEntry(ctypes.Structure):
                 ("total_ms", ctypes.c_double)]
 
 
+class EnsfTuning(ctypes.Structure):
+    _fields_ = [("gram_tile_n", ctypes.c_int), ("gram_stages", ctypes.c_int), ("gram_splits", ctypes.c_int),
+                ("gram_ms", ctypes.c_float), ("wx_tile_n", ctypes.c_int), ("wx_ms", ctypes.c_float)]
+
+
 class EnsfError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: status {status}: {message}")
@@ -53,6 +59,10 @@ _SIGNATURES = [
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
                                      ctypes.c_int, ctypes.c_float, ctypes.POINTER(EnsfNoise),
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
+                                     ctypes.c_float, ctypes.POINTER(EnsfNoise), ctypes.c_void_p,
+                                     ctypes.POINTER(EnsfTuning), ctypes.c_void_p]),
     ("ensf_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_void_p, ctypes.c_void_p]),
@@ -135,11 +145,11 @@ class Filter:
     cores) or ``"bf16"`` (one BF16 product on tensor cores)."""
 
     def __init__(self, max_n: int, max_d: int, gram: str = "fp32", wx: str = "fp32",
-                 check_finite: bool = False):
+                 check_finite: bool = False, graph: bool = False):
         torch = _torch()
         lib = load()
         self.cfg = EnsfConfig(int(max_n), int(max_d), PRECISIONS[gram], PRECISIONS[wx],
-                              FLAG_CHECK_FINITE if check_finite else 0)
+                              (FLAG_CHECK_FINITE if check_finite else 0) | (FLAG_CUDA_GRAPH if graph else 0))
         nbytes = lib.ensf_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise ValueError("invalid EnSF configuration")
@@ -187,6 +197,22 @@ class Filter:
                                   _stream_ptr(stream))
         _check(st, "ensf_analysis")
         return out
+
+    def autotune(self, prior, y, mask, sigma_obs: float, eps: float, obs_op: int = OBS_IDENTITY, seed: int = 0,
+                 out=None, stream=None) -> dict:
+        """Pick the tensor-core launch shapes for this (n, d); overwrites ``out``."""
+        torch = _torch()
+        _dev(prior, torch.float32, "prior")
+        n, d = prior.shape
+        if out is None:
+            out = torch.empty_like(prior)
+        nz = EnsfNoise(None, int(seed) & (2 ** 64 - 1), 0)
+        rep = EnsfTuning()
+        _check(load().ensf_autotune(self._h, prior.data_ptr(), n, d, y.data_ptr(),
+                                    mask.data_ptr() if mask is not None else None, int(obs_op), float(sigma_obs),
+                                    float(eps), ctypes.byref(nz), out.data_ptr(), ctypes.byref(rep),
+                                    _stream_ptr(stream)), "ensf_autotune")
+        return {f: getattr(rep, f) for f, _ in EnsfTuning._fields_}
 
     def weights(self, z, prior, t: float, eps: float, stream=None):
         """Weights w_ij of Eq. 16 at pseudo-time t; returns [n][n_x] FP32."""

@@ -196,3 +196,45 @@ def test_invalid_arguments_raise():
         f.analysis(torch.zeros((9, 64), device="cuda"), y, None, 1.0, 3, 0.05)
     with pytest.raises(ensf.EnsfError):
         f.analysis(x, y, None, 1.0, 3, 0.05, out=x)
+
+
+@pytest.mark.parametrize("path", ["fp32", "split-bf16"])
+def test_graph_replay_matches_eager(path):
+    """ENSF_FLAG_CUDA_GRAPH: the captured and replayed analysis is bitwise the
+    eager one, across calls that change only the noise seed (graph update)
+    and a call with another shape (re-instantiation)."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    gram, wx, _ = PATHS[path]
+    eager = ensf.Filter(70, 1936, gram=gram, wx=wx)
+    graph = ensf.Filter(70, 1936, gram=gram, wx=wx, graph=True)
+    stream = torch.cuda.Stream()
+    for seed, (n, grid) in [(1, (70, 44)), (2, (70, 44)), (3, (33, 36)), (4, (70, 44))]:
+        p = inputs.small_case(seed=seed, n=n, grid=grid, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
+        prior = torch.from_numpy(p.prior).cuda()
+        y = torch.from_numpy(p.y).cuda()
+        mask = torch.from_numpy(p.mask).cuda()
+        with torch.cuda.stream(stream):
+            a = eager.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed)
+            b = graph.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed)
+        stream.synchronize()
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_autotuned_analysis_matches_oracle():
+    """After ensf_autotune picks the launch shapes, the split path still meets
+    the parity bar on the 64x64x2 case."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    p = inputs.plain_64()
+    f = ensf.Filter(p.n, p.d, gram="split", wx="split", check_finite=True)
+    prior = torch.from_numpy(p.prior).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    rep = f.autotune(prior, y, None, p.sigma_obs, p.eps, p.obs_op, seed=7)
+    assert rep["gram_tile_n"] in (128, 256) and rep["wx_tile_n"] in (64, 128, 256)
+    assert rep["gram_splits"] >= 1 and rep["gram_ms"] > 0 and rep["wx_ms"] > 0
+    got = _gpu_analysis(p, "split", "split", filt=f)
+    ref = run_oracle(p)
+    cond = conditioning(p, ref, prec="split")
+    rel, tie, bad = compare_members(got, ref, cond, TOL_FP32)
+    assert not bad.any(), describe(rel, tie, bad)
