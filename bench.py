@@ -127,6 +127,8 @@ class ClockSampler:
 
 
 def make_problem(workload: str, rank: int):
+    if workload == "batched-uneven":  # the reference arm samples the first filter of the batch
+        return inputs.batched_uneven(seed=3 + 1000 * rank)[0]
     fn = inputs.WORKLOADS[workload]
     # every rank runs an independent filter (another seed: another truth, prior, noise)
     return fn(seed={"plain-64": 1, "sparse-arctan-128": 2, "large-512": 4, "medium-192": 5}[workload] + 1000 * rank)
@@ -232,6 +234,108 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
             "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms,
             "executed_flops_per_launch": executed, "executed_tflops": executed / (avg_ms / 1e3) / 1e12,
             "executed_frac": executed / (avg_ms / 1e3) / 1e12 / peak}
+
+
+def run_batched(args):
+    """64 independent filters with uneven N and d (K = 50).  split paths: one
+    batched launch per stage for all filters; fp32: one analysis call per
+    filter (the plain one-launch-per-instance path)."""
+    import torch
+    rank, local_rank, world = _dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2407_12168_gb300 import ensf
+    gram, wx = PATHS[args.path]
+    probs = inputs.batched_uneven(seed=3 + 1000 * rank)
+    K, eps = probs[0].K, probs[0].eps
+    dev = torch.device("cuda", local_rank)
+    filters = [dict(prior=torch.from_numpy(p.prior).to(dev), y=torch.from_numpy(p.y).to(dev),
+                    mask=torch.from_numpy(p.mask).to(dev) if p.mask is not None else None,
+                    sigma_obs=p.sigma_obs, obs_op=p.obs_op, seed=p.seed) for p in probs]
+    outs = [torch.empty_like(f["prior"]) for f in filters]
+    max_n, max_d = max(p.n for p in probs), max(p.d for p in probs)
+    if gram == "fp32":
+        handles = [ensf.Filter(p.n, p.d, gram="fp32", wx="fp32", graph=args.graph) for p in probs]
+
+        def one(sd):
+            for f, fl, o in zip(handles, filters, outs):
+                f.analysis(fl["prior"], fl["y"], fl["mask"], fl["sigma_obs"], K, eps, fl["obs_op"],
+                           seed=fl["seed"] + sd, out=o)
+        prof_handles = handles
+    else:
+        h = ensf.Filter(max_n, max_d, gram=gram, wx=wx, graph=args.graph)
+
+        def one(sd):
+            h.analysis_batched([dict(fl, seed=fl["seed"] + sd) for fl in filters], K, eps, outs=outs)
+        prof_handles = [h]
+    stream = torch.cuda.current_stream()
+    for w in range(args.warmup):
+        one(w)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for s_ in range(args.steps):
+            ev[s_][0].record(stream)
+            one(100 + s_)
+            ev[s_][1].record(stream)
+        torch.cuda.synchronize()
+    ms = float(sum(a.elapsed_time(b) for a, b in ev)) / args.steps
+    for f in prof_handles:
+        f.profile_enable(True)
+    for s_ in range(args.steps):
+        one(100 + s_)
+    torch.cuda.synchronize()
+    prof = {}
+    for f in prof_handles:
+        for k, v in f.profile_read().items():
+            a = prof.get(k, (0, 0, 0.0))
+            prof[k] = (a[0] + v[0], a[1] + v[1], a[2] + v[2])
+        f.profile_enable(False)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if rank != 0:
+            dist.destroy_process_group()
+            return 0
+    ms = float(t[0])
+    member_steps = sum(p.n for p in probs) * K
+    flops = sum(2.0 * p.n * p.n * p.d for p in probs)
+    kern = {k: {"launches": v[0] // args.steps, "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()}
+    peaks = _peaks()
+    # Gram time per Euler-Maruyama step (all filters): one batched launch, or one launch per filter
+    gram_ms = prof["gram"][2] / (args.steps * K) if "gram" in prof and prof["gram"][1] else None
+    roof = None
+    if gram_ms:
+        per_step_gram_ms = gram_ms
+        peak = float(peaks["bf16_tflops_sustained"]) if peaks and gram != "fp32" else FP32_SIMT_PEAK_TFLOPS
+        ach = flops / (per_step_gram_ms / 1e3) / 1e12
+        roof = {"kernel": "gram", "bound": "tensor" if gram != "fp32" else "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "algorithmic_flops_per_step": flops, "gram_ms_per_step": per_step_gram_ms,
+                "note": "latency-bound sizes: the Gram of all 64 filters per Euler-Maruyama step"}
+    line = {"metric": METRIC, "value": world * member_steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"split-bf16": "bf16x3+bf16 (fp32 acc)", "split": "bf16x3 (fp32 acc)", "fp32": "f32"}[args.path],
+            "data": "synthetic",
+            "config": {"workload": "batched-uneven", "filters": len(probs), "K": K,
+                       "N": sorted(set(p.n for p in probs)), "d": sorted(set(p.d for p in probs)),
+                       "path": args.path + (" (one batched launch per stage)" if gram != "fp32"
+                                            else " (one analysis call per filter)"),
+                       "l2": "working set partly L2-resident (small filters)", "cuda_graph": args.graph,
+                       "parallelism": f"{world} independent batch(es), one per GPU"},
+            "roofline": roof, "kernels": kern, "gpu_launches": int(sum(v[0] for v in prof.values()) // args.steps),
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
 
 
 def run_ours(args):
@@ -367,7 +471,7 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="large-512", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default="large-512", choices=sorted(inputs.WORKLOADS) + ["batched-uneven"])
     ap.add_argument("--path", default="split-bf16", choices=sorted(PATHS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -378,7 +482,9 @@ def main(argv=None):
     if args.warmup < 3 and args.impl == "ours":
         print("note: warm-up raised to the minimum of 3", file=sys.stderr)
         args.warmup = 3
-    return run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_batched(args) if args.workload == "batched-uneven" else run_ours(args)
 
 
 if __name__ == "__main__":

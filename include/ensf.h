@@ -139,6 +139,36 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
                           const uint8_t *obs_mask, int obs_op, float sigma_obs, float eps,
                           const ensf_noise *noise, float *out, ensf_tuning *report, void *stream);
 
+/* One filter of a batched analysis. */
+typedef struct {
+    const float *prior;        /* [n][d] forecast ensemble (device)                 */
+    int n;                     /* ensemble size, 1 <= n <= 8192                     */
+    int64_t d;                 /* state dimension, multiple of 8                    */
+    const float *y;            /* [d] observations                                  */
+    const uint8_t *obs_mask;   /* [d] or NULL                                       */
+    int obs_op;                /* ensf_obs_op                                       */
+    float sigma_obs;           /* > 0                                               */
+    ensf_noise noise;          /* per-filter noise (buffer [K+1][n][d] or Philox)   */
+    float *out;                /* [n][d] analysis ensemble (device)                 */
+} ensf_instance;
+
+/* Device workspace a batched analysis of these instances needs with the
+ * handle configuration `cfg` (0 if a precision is not a tensor-core one). */
+size_t ensf_batch_workspace_bytes(const ensf_config *cfg, const ensf_instance *inst, int count);
+
+/* Independent analyses (Sec. III-A.2) of `count` filters with uneven n and d
+ * in one launch per stage: each Euler-Maruyama step is one batched Gram over
+ * the tiles of all filters, one batched row softmax and one persistent batched
+ * W X + score + update; all filters share K and eps.  Tensor-core precisions
+ * only (ENSF_EUNSUPPORTED otherwise).  `workspace` (256-byte aligned, at least
+ * ensf_batch_workspace_bytes) holds the per-filter scratch and the tile and
+ * descriptor tables; the tables are uploaded from a page-locked host buffer
+ * owned by the handle (allocated on the first batched call; the call waits
+ * for the previous batched call's upload before reusing it).  With
+ * ENSF_FLAG_CUDA_GRAPH the whole batched analysis is one CUDA graph. */
+ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int count, int K, float eps,
+                                  void *workspace, size_t ws_bytes, void *stream);
+
 /* Normalised weights w_ij of Eq. 16 for given particles z [n][d] at pseudo-
  * time t, against the forecast ensemble prior [n_x][d], written to
  * w [n][n_x] FP32.  Uses the handle's Gram precision; this is the Gram +

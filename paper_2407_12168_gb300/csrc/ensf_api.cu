@@ -162,6 +162,12 @@ struct ensf_handle {
     int device = 0;
     ensf::TcContext *tc = nullptr;
     cudaGraphExec_t graph_exec = nullptr;  // ENSF_FLAG_CUDA_GRAPH: last instantiated analysis
+    cudaGraphExec_t batch_exec = nullptr;  // ... and batched analysis
+    // batched analyses: page-locked staging of the device tables
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+    cudaEvent_t staging_done = nullptr;
+    bool staging_pending = false;
 
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
     int *err() const { return at<int>(L.err); }
@@ -325,6 +331,9 @@ ensf_status ensf_destroy(ensf_handle *h) {
     if (!h) return fail(ENSF_EINVAL, "ensf_destroy: NULL handle");
     for (cudaEvent_t e : h->prof.events) cudaEventDestroy(e);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
+    if (h->staging_done) cudaEventDestroy(h->staging_done);
+    if (h->staging) cudaFreeHost(h->staging);
     ensf::tc_context_destroy(h->tc);
     delete h;
     return ENSF_OK;
@@ -703,6 +712,258 @@ ensf_status ensf_status_sync(ensf_handle *h, void *stream) {
         ENSF_CUDA(cudaStreamSynchronize(s));
         return fail(static_cast<ensf_status>(word), "device reported %s", ensf_status_string(static_cast<ensf_status>(word)));
     }
+    return ENSF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched
+namespace {
+
+struct BatchLayout {
+    struct Inst {
+        size_t xbar, norms, xb_hi, xb_lo, zb_hi, zb_lo, xt_hi, xt_lo, wb_hi, wb_lo, partial;
+        int splits, ldw;
+    };
+    std::vector<Inst> inst;
+    size_t maps_gram = 0, maps_wx = 0, insts = 0, gram_items = 0, rows = 0, wx_items = 0;
+    size_t tables_begin = 0, tables_bytes = 0, total = 0;
+    int n_gram_items = 0, n_rows = 0, n_wx_items = 0, max_n = 0;
+};
+
+bool batch_ok(const ensf_config *cfg, const ensf_instance *inst, int count) {
+    if (!cfg || !inst || count < 1 || !is_tc(cfg->gram) || !is_tc(cfg->wx)) return false;
+    for (int i = 0; i < count; ++i)
+        if (inst[i].n < 1 || inst[i].n > 8192 || inst[i].d < 8 || inst[i].d % 8 != 0) return false;
+    return true;
+}
+
+BatchLayout batch_layout(const ensf_config *cfg, const ensf_instance *inst, int count) {
+    BatchLayout B;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
+    const bool gs = cfg->gram == ENSF_PREC_SPLIT_BF16X3, ws = cfg->wx == ENSF_PREC_SPLIT_BF16X3;
+    const int T = ensf::kBatchTileN;
+    for (int i = 0; i < count; ++i) {
+        const int64_t n = inst[i].n, d = inst[i].d;
+        BatchLayout::Inst L{};
+        L.ldw = (int)round_up(n, 8);
+        const int kblocks = (int)((d + 63) / 64);
+        L.splits = (kblocks + ensf::kBatchKbChunk - 1) / ensf::kBatchKbChunk;
+        L.xbar = take(4 * d);
+        L.norms = take(8 * n);
+        L.xb_hi = take(2 * n * d);
+        L.xb_lo = gs ? take(2 * n * d) : 0;
+        L.zb_hi = take(2 * n * d);
+        L.zb_lo = gs ? take(2 * n * d) : 0;
+        L.xt_hi = take(2 * d * L.ldw);
+        L.xt_lo = ws ? take(2 * d * L.ldw) : 0;
+        L.wb_hi = take(2 * n * L.ldw);
+        L.wb_lo = ws ? take(2 * n * L.ldw) : 0;
+        L.partial = take(4 * (size_t)L.splits * n * n);
+        B.inst.push_back(L);
+        const int mt = (int)((n + T - 1) / T);
+        B.n_gram_items += mt * mt * L.splits;
+        B.n_rows += (int)n;
+        B.n_wx_items += (int)((d + 127) / 128) * mt;
+        B.max_n = std::max<int>(B.max_n, (int)n);
+    }
+    B.tables_begin = off;
+    B.maps_gram = take(128 * 4 * (size_t)count);
+    B.maps_wx = take(128 * 4 * (size_t)count);
+    B.insts = take(sizeof(ensf::BInst) * count);
+    B.gram_items = take(sizeof(ensf::BGramItem) * B.n_gram_items);
+    B.rows = take(sizeof(ensf::BRow) * B.n_rows);
+    B.wx_items = take(sizeof(ensf::BWxItem) * B.n_wx_items);
+    B.tables_bytes = off - B.tables_begin;
+    B.total = off;
+    return B;
+}
+
+ensf_status batch_enqueue(ensf_handle *h, const ensf_instance *inst, int count, int K, float eps, char *ws,
+                          const BatchLayout &B, cudaStream_t s) {
+    const bool gs = h->cfg.gram == ENSF_PREC_SPLIT_BF16X3, wsp = h->cfg.wx == ENSF_PREC_SPLIT_BF16X3;
+    auto at = [&](size_t o) { return ws + o; };
+    // tables: upload from the page-locked staging buffer
+    ENSF_CUDA(cudaMemcpyAsync(at(B.tables_begin), h->staging, B.tables_bytes, cudaMemcpyHostToDevice, s));
+    // per-filter preparation (once per analysis)
+    const float alpha0 = step_coef(0, K, eps, 1.0, 0).alpha;
+    for (int i = 0; i < count; ++i) {
+        const ensf_instance &I = inst[i];
+        const BatchLayout::Inst &L = B.inst[i];
+        float *xbar = reinterpret_cast<float *>(at(L.xbar));
+        __nv_bfloat16 *xb_hi = reinterpret_cast<__nv_bfloat16 *>(at(L.xb_hi));
+        __nv_bfloat16 *xb_lo = gs ? reinterpret_cast<__nv_bfloat16 *>(at(L.xb_lo)) : nullptr;
+        __nv_bfloat16 *zb_hi = reinterpret_cast<__nv_bfloat16 *>(at(L.zb_hi));
+        __nv_bfloat16 *zb_lo = gs ? reinterpret_cast<__nv_bfloat16 *>(at(L.zb_lo)) : nullptr;
+        ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_col_mean(I.prior, I.n, I.d, xbar, s));
+        ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(I.prior, I.n, I.d, reinterpret_cast<double *>(at(L.norms)),
+                                                          s, xbar));
+        ENSF_LAUNCH(h, P_INIT, s, ensf::launch_init_particles(I.out, I.n, I.d, I.noise.buf, I.noise.seed,
+                                                               I.noise.offset, s));
+        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(I.prior, I.n, I.d, xb_hi, xb_lo, I.d, s, xbar, 1.0f));
+        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(I.out, I.n, I.d, zb_hi, zb_lo, I.d, s, xbar, alpha0));
+        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16_transpose(
+                                       I.prior, I.n, I.d, reinterpret_cast<__nv_bfloat16 *>(at(L.xt_hi)),
+                                       wsp ? reinterpret_cast<__nv_bfloat16 *>(at(L.xt_lo)) : nullptr, L.ldw, s));
+    }
+    const void *maps_gram = at(B.maps_gram), *maps_wx = at(B.maps_wx);
+    const ensf::BInst *binst = reinterpret_cast<const ensf::BInst *>(at(B.insts));
+    for (int k = 0; k < K; ++k) {
+        ensf::StepCoef c = step_coef(k, K, eps, 1.0, 0);
+        ENSF_LAUNCH(h, P_GRAM, s,
+                    ensf::launch_gram_tc_batched(maps_gram, reinterpret_cast<const ensf::BGramItem *>(at(B.gram_items)),
+                                                 B.n_gram_items, binst, gs, h->err(), s));
+        ENSF_LAUNCH(h, P_SOFTMAX, s,
+                    ensf::launch_softmax_batched(reinterpret_cast<const ensf::BRow *>(at(B.rows)), B.n_rows, binst,
+                                                 B.max_n, c.alpha_d, c.inv_2beta2_d, s));
+        ENSF_LAUNCH(h, P_WXEM, s,
+                    ensf::launch_wx_em_tc_batched(maps_wx, reinterpret_cast<const ensf::BWxItem *>(at(B.wx_items)),
+                                                  B.n_wx_items, binst, wsp, c, step_coef(k + 1, K, eps, 1.0, 0).alpha,
+                                                  h->err(), h->sms, s));
+    }
+    return ENSF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ensf_batch_workspace_bytes(const ensf_config *cfg, const ensf_instance *inst, int count) {
+    if (!config_ok(cfg) || !batch_ok(cfg, inst, count)) return 0;
+    return batch_layout(cfg, inst, count).total;
+}
+
+ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int count, int K, float eps,
+                                  void *workspace, size_t ws_bytes, void *stream) {
+    if (!h) return fail(ENSF_EINVAL, "ensf_analysis_batched: NULL handle");
+    if (!is_tc(h->cfg.gram) || !is_tc(h->cfg.wx))
+        return fail(ENSF_EUNSUPPORTED, "ensf_analysis_batched: needs tensor-core precisions for Gram and W X");
+    if (!inst || count < 1) return fail(ENSF_EINVAL, "ensf_analysis_batched: no instances");
+    if (K < 1 || !(eps > 0.0f && eps < 1.0f)) return fail(ENSF_EINVAL, "ensf_analysis_batched: bad K or eps");
+    for (int i = 0; i < count; ++i) {
+        const ensf_instance &I = inst[i];
+        if (!aligned16(I.prior) || !aligned16(I.y) || !aligned16(I.out) || I.prior == I.out)
+            return fail(ENSF_EINVAL, "ensf_analysis_batched: instance %d: bad pointers", i);
+        if (I.obs_mask && (reinterpret_cast<uintptr_t>(I.obs_mask) & 3u))
+            return fail(ENSF_EINVAL, "ensf_analysis_batched: instance %d: mask must be 4-byte aligned", i);
+        if (I.n < 1 || I.n > 8192 || I.d < 8 || I.d % 8 != 0)
+            return fail(ENSF_EINVAL, "ensf_analysis_batched: instance %d: bad n or d", i);
+        if (!(I.sigma_obs > 0.0f) || (I.obs_op != ENSF_OBS_IDENTITY && I.obs_op != ENSF_OBS_ARCTAN))
+            return fail(ENSF_EINVAL, "ensf_analysis_batched: instance %d: bad sigma_obs or obs_op", i);
+        if (I.noise.buf && !aligned16(I.noise.buf))
+            return fail(ENSF_EINVAL, "ensf_analysis_batched: instance %d: noise buffer misaligned", i);
+    }
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+        return fail(ENSF_EINVAL, "ensf_analysis_batched: workspace must be 256-byte aligned");
+    const BatchLayout B = batch_layout(&h->cfg, inst, count);
+    if (ws_bytes < B.total)
+        return fail(ENSF_ENOMEM, "ensf_analysis_batched: workspace has %zu bytes, needs %zu", ws_bytes, B.total);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    // fill the page-locked staging copy of the tables (after the previous upload finished)
+    if (!h->staging_done) ENSF_CUDA(cudaEventCreateWithFlags(&h->staging_done, cudaEventDisableTiming));
+    if (h->staging_pending) {
+        ENSF_CUDA(cudaEventSynchronize(h->staging_done));
+        h->staging_pending = false;
+    }
+    if (h->staging_bytes < B.tables_bytes) {
+        if (h->staging) cudaFreeHost(h->staging);
+        h->staging = nullptr;
+        h->staging_bytes = 0;
+        ENSF_CUDA(cudaMallocHost(&h->staging, B.tables_bytes));
+        h->staging_bytes = B.tables_bytes;
+    }
+    char *st = static_cast<char *>(h->staging);
+    auto tab = [&](size_t o) { return st + (o - B.tables_begin); };
+    const bool gs = h->cfg.gram == ENSF_PREC_SPLIT_BF16X3, wsp = h->cfg.wx == ENSF_PREC_SPLIT_BF16X3;
+    ensf::BInst *bi = reinterpret_cast<ensf::BInst *>(tab(B.insts));
+    ensf::BGramItem *gi = reinterpret_cast<ensf::BGramItem *>(tab(B.gram_items));
+    ensf::BRow *ri = reinterpret_cast<ensf::BRow *>(tab(B.rows));
+    ensf::BWxItem *wi = reinterpret_cast<ensf::BWxItem *>(tab(B.wx_items));
+    const int T = ensf::kBatchTileN;
+    int ng = 0, nr = 0, nw = 0;
+    for (int i = 0; i < count; ++i) {
+        const ensf_instance &I = inst[i];
+        const BatchLayout::Inst &L = B.inst[i];
+        auto dev = [&](size_t o) { return ws + o; };
+        ensf::BInst b{};
+        b.n = I.n;
+        b.ldw = L.ldw;
+        b.d = I.d;
+        b.splits = L.splits;
+        b.partial = reinterpret_cast<float *>(dev(L.partial));
+        b.norms = reinterpret_cast<const double *>(dev(L.norms));
+        b.wb_hi = reinterpret_cast<__nv_bfloat16 *>(dev(L.wb_hi));
+        b.wb_lo = wsp ? reinterpret_cast<__nv_bfloat16 *>(dev(L.wb_lo)) : nullptr;
+        b.z = I.out;
+        b.zb_hi = reinterpret_cast<__nv_bfloat16 *>(dev(L.zb_hi));
+        b.zb_lo = gs ? reinterpret_cast<__nv_bfloat16 *>(dev(L.zb_lo)) : nullptr;
+        b.y = I.y;
+        b.mask = I.obs_mask;
+        b.centre = reinterpret_cast<const float *>(dev(L.xbar));
+        b.noise_buf = I.noise.buf;
+        b.seed = I.noise.seed;
+        b.offset = I.noise.offset;
+        b.inv_r = (float)(1.0 / ((double)I.sigma_obs * I.sigma_obs));
+        b.obs_op = I.obs_op;
+        bi[i] = b;
+        char *mg = tab(B.maps_gram) + 512 * (size_t)i;
+        char *mw = tab(B.maps_wx) + 512 * (size_t)i;
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mg + 0, b.zb_hi, I.d, I.n, I.d, 128);
+        if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mg + 128, b.zb_lo, I.d, I.n, I.d, 128);
+        if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mg + 256, dev(L.xb_hi), I.d, I.n, I.d, T);
+        if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mg + 384, gs ? dev(L.xb_lo) : nullptr, I.d, I.n, I.d, T);
+        if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mw + 0, dev(L.xt_hi), I.n, I.d, L.ldw, 128);
+        if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mw + 128, wsp ? dev(L.xt_lo) : nullptr, I.n, I.d, L.ldw, 128);
+        if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mw + 256, b.wb_hi, I.n, I.n, L.ldw, T);
+        if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mw + 384, b.wb_lo, I.n, I.n, L.ldw, T);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor map encoding");
+        const int mt = (I.n + T - 1) / T;
+        for (int m = 0; m < mt; ++m)
+            for (int q = 0; q < mt; ++q)
+                for (int sp = 0; sp < L.splits; ++sp) gi[ng++] = ensf::BGramItem{i, m * T, q * T, sp};
+        for (int r = 0; r < I.n; ++r) ri[nr++] = ensf::BRow{i, r};
+        for (int64_t c0 = 0; c0 < I.d; c0 += 128)
+            for (int q = 0; q < mt; ++q) wi[nw++] = ensf::BWxItem{i, (int)c0, q * T};
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool graph = (h->cfg.flags & ENSF_FLAG_CUDA_GRAPH) && s != nullptr &&
+                       cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    if (!graph) {
+        ensf_status st2 = batch_enqueue(h, inst, count, K, eps, ws, B, s);
+        if (st2 != ENSF_OK) return st2;
+    } else {
+        ENSF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        ensf_status st2 = batch_enqueue(h, inst, count, K, eps, ws, B, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st2 != ENSF_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st2;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        bool updated = false;
+        if (h->batch_exec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(h->batch_exec, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(h->batch_exec);
+                h->batch_exec = nullptr;
+            }
+        }
+        if (!updated) e = cudaGraphInstantiate(&h->batch_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->batch_exec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        ENSF_CUDA(cudaGraphLaunch(h->batch_exec, s));
+    }
+    ENSF_CUDA(cudaEventRecord(h->staging_done, s));
+    h->staging_pending = true;
     return ENSF_OK;
 }
 

@@ -180,69 +180,8 @@ k_softmax_rows(const float *__restrict__ partial, int splits, int64_t part_strid
                __nv_bfloat16 *__restrict__ w_lo, int ldwb) {
     extern __shared__ double lg[];
     __shared__ double red[256];
-    const int i = blockIdx.x, tid = threadIdx.x;
-    // sum of the split-K partials: when the row is short, `groups` threads
-    // share one column j, each summing a fixed range of splits; the group
-    // sums are then added in group order (deterministic)
-    const int groups = n_x >= 256 ? 1 : min(256 / n_x, splits);
-    const int per = (splits + groups - 1) / groups;
-    double lmax = -DBL_MAX;
-    if (groups == 1) {
-        for (int j = tid; j < n_x; j += 256) {
-            double g = 0.0;
-            for (int s = 0; s < splits; ++s) g += (double)partial[s * part_stride + (int64_t)i * ldp + j];
-            double l = (2.0 * alpha * g - alpha * alpha * norms[j]) * inv_2beta2;
-            lg[j] = l;
-            lmax = fmax(lmax, l);
-        }
-    } else {
-        const int j = tid % n_x, grp = tid / n_x;
-        if (grp < groups) {
-            double g = 0.0;
-            const int s0 = grp * per, s1 = min(splits, s0 + per);
-            for (int s = s0; s < s1; ++s) g += (double)partial[s * part_stride + (int64_t)i * ldp + j];
-            red[grp * n_x + j] = g;
-        }
-        __syncthreads();
-        if (tid < n_x) {
-            double g = 0.0;
-            for (int q = 0; q < groups; ++q) g += red[q * n_x + tid];
-            double l = (2.0 * alpha * g - alpha * alpha * norms[tid]) * inv_2beta2;
-            lg[tid] = l;
-            lmax = l;
-        }
-        __syncthreads();
-    }
-    red[tid] = lmax;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
-        __syncthreads();
-    }
-    const double m = red[0];
-    __syncthreads();
-    double sum = 0.0;
-    for (int j = tid; j < n_x; j += 256) {
-        double e = (double)expf((float)(lg[j] - m));
-        lg[j] = e;
-        sum += e;
-    }
-    red[tid] = sum;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (tid < s) red[tid] += red[tid + s];
-        __syncthreads();
-    }
-    const double inv = 1.0 / red[0];
-    for (int j = tid; j < n_x; j += 256) {
-        float wv = (float)(lg[j] * inv);
-        if (w) w[(int64_t)i * ldw + j] = wv;
-        if (w_hi) {
-            __nv_bfloat16 hi = __float2bfloat16_rn(wv);
-            w_hi[(int64_t)i * ldwb + j] = hi;
-            if (w_lo) w_lo[(int64_t)i * ldwb + j] = __float2bfloat16_rn(wv - __bfloat162float(hi));
-        }
-    }
+    softmax_row(blockIdx.x, partial, splits, part_stride, ldp, n_x, norms, alpha, inv_2beta2, w, ldw, w_hi, w_lo,
+                ldwb, lg, red);
 }
 
 // ---------------------------------------------------------------------------

@@ -617,6 +617,236 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
     }
 }
 
+// ================================================================ batched
+// Gram tile of one instance; maps / parameters / k-range from device tables.
+template <int BN, int STAGES, bool SPLIT>
+__global__ void __launch_bounds__(192, 1)
+k_gram_tc_batched(const CUtensorMap *__restrict__ maps, const BGramItem *__restrict__ items,
+                  const BInst *__restrict__ insts, int *err) {
+    using P = Plan<BN, STAGES, SPLIT>;
+    extern __shared__ uint8_t smem_raw[];
+    const Ctl c = carve<P>(smem_raw, STAGES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*reinterpret_cast<volatile int *>(err) != 0) return;
+    const BGramItem it = items[blockIdx.x];
+    const BInst &I = insts[it.inst];
+    const int n = I.n;
+    const int kblocks = static_cast<int>((I.d + BK - 1) / BK);
+    const int kb0 = it.split * kBatchKbChunk;
+    const int nkb = min(kblocks, kb0 + kBatchKbChunk) - kb0;
+    const CUtensorMap *m = maps + 4 * it.inst;
+    const uint32_t tmem = setup<BN, STAGES>(c, warp);
+    if (warp == 0) {
+        if (lane == 0) produce<BN, STAGES, SPLIT>(c, m + 0, m + 1, m + 2, m + 3, it.m0, it.n0, kb0, nkb, err);
+    } else if (warp == 1) {
+        if (lane == 0) mma_loop<BN, STAGES, SPLIT>(c, tmem, nkb, err);
+    } else {
+        const int q = warp & 3;
+        const int row = it.m0 + q * 32 + lane;
+        const bool ok = mbar_wait(c.accum, 0, c.abort_flag, err);
+        tc_fence_after();
+        if (ok) {
+            float *dst = I.partial + (static_cast<int64_t>(it.split) * n + row) * n;
+#pragma unroll 1
+            for (int cc = 0; cc < BN; cc += 32) {
+                float v[32];
+                tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + cc, v);
+                const int col0 = it.n0 + cc;
+                if (row < n && col0 < n) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if (col0 + e < n) dst[col0 + e] = v[e];
+                }
+            }
+        }
+    }
+    teardown<BN>(tmem, warp);
+}
+
+__global__ void __launch_bounds__(256)
+k_softmax_batched(const BRow *__restrict__ rows, const BInst *__restrict__ insts, double alpha, double inv_2beta2) {
+    extern __shared__ double lg[];
+    __shared__ double red[256];
+    const BRow r = rows[blockIdx.x];
+    const BInst &I = insts[r.inst];
+    softmax_row(r.row, I.partial, I.splits, static_cast<int64_t>(I.n) * I.n, I.n, I.n, I.norms, alpha, inv_2beta2,
+                nullptr, 0, I.wb_hi, I.wb_lo, I.ldw, lg, red);
+}
+
+// Persistent W X + EM over the tile list of all instances (U^T = X^T W^T as in
+// the single-filter kernel); noise from the caller's buffer or Philox inline.
+template <int BN, int STAGES, bool SPLIT>
+__global__ void __launch_bounds__(kWxThreads, 1)
+k_wx_em_tc_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__restrict__ items, int n_items,
+                   const BInst *__restrict__ insts, StepCoef cf, float alpha_next, int *err) {
+    using P = WxPlan<BN, STAGES, SPLIT>;
+    extern __shared__ uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*reinterpret_cast<volatile int *>(err) != 0) return;
+
+    uintptr_t base = reinterpret_cast<uintptr_t>(smem_raw);
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    uint8_t *tiles = reinterpret_cast<uint8_t *>(base + pad);
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], kEpiWarps);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kWxTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it_count = 0, issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
+                const BWxItem w = items[t];
+                const int kblocks = (insts[w.inst].n + BK - 1) / BK;
+                const CUtensorMap *m = maps + 4 * w.inst;
+                for (int kb = 0; kb < kblocks; ++kb, ++it_count) {
+                    const int s = it_count % STAGES;
+                    const uint32_t ph = (it_count / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err)) { ok = false; break; }
+                    const uint32_t st = smem_u32(tiles + s * P::kStage);
+                    mbar_expect_tx(&full[s], P::kStage);
+                    const int kx = kb * BK;
+                    tma_load_2d(st, m + 0, &full[s], kx, w.m0);
+                    if (SPLIT) tma_load_2d(st + P::kA, m + 1, &full[s], kx, w.m0);
+                    tma_load_2d(st + P::kA * P::kPlanes, m + 2, &full[s], kx, w.n0);
+                    if (SPLIT) tma_load_2d(st + P::kA * P::kPlanes + P::kB, m + 3, &full[s], kx, w.n0);
+                    issued = it_count + 1;
+                }
+            }
+            if (*abort_flag) {
+                const uint64_t t0 = globaltimer();
+                for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i) {
+                    const int s = i % STAGES;
+                    while (!mbar_try_wait(&full[s], (i / STAGES) & 1) && globaltimer() - t0 < kTimeoutNs) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int it_count = 0, lt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x, ++lt) {
+                const int slot = lt & 1;
+                const uint32_t use = lt >> 1;
+                const int kblocks = (insts[items[t].inst].n + BK - 1) / BK;
+                if (!mbar_wait(&tempty[slot], (use & 1u) ^ 1u, abort_flag, err)) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + slot * 256;
+                for (int kb = 0; kb < kblocks; ++kb, ++it_count) {
+                    const int s = it_count % STAGES;
+                    const uint32_t ph = (it_count / STAGES) & 1;
+                    if (!mbar_wait(&full[s], ph, abort_flag, err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_hi = smem_u32(tiles + s * P::kStage);
+                    const uint32_t a_lo = a_hi + P::kA;
+                    const uint32_t b_hi = a_hi + P::kA * P::kPlanes;
+                    const uint32_t b_lo = b_hi + P::kB;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        mma_bf16(acc, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                        if (SPLIT) {
+                            mma_bf16(acc, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
+                            mma_bf16(acc, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[slot]);
+            }
+        }
+    } else {
+        const int ew = warp - 2;
+        const int q = warp & 3;
+        const int part = ew >> 2;
+        constexpr int kCols = BN / 4;
+        int lt = 0;
+        for (int t = blockIdx.x; t < n_items; t += gridDim.x, ++lt) {
+            const int slot = lt & 1;
+            const uint32_t use = lt >> 1;
+            const BWxItem w = items[t];
+            const BInst &I = insts[w.inst];
+            if (!mbar_wait(&tfull[slot], use & 1u, abort_flag, err)) break;
+            tc_fence_after();
+            const int64_t c = static_cast<int64_t>(w.m0) + q * 32 + lane;
+            const bool cok = c < I.d;
+            const float yc = cok ? I.y[c] : 0.f;
+            const bool obs = cok && (I.mask == nullptr || I.mask[c] != 0);
+            const float shift = cok ? alpha_next * I.centre[c] : 0.f;
+#pragma unroll 1
+            for (int cc = part * kCols; cc < (part + 1) * kCols; cc += 16) {
+                float u[16];
+                tmem_ld16(tmem + slot * 256 + (static_cast<uint32_t>(q * 32) << 16) + cc, u);
+                const int i0 = w.n0 + cc;
+                if (!cok || i0 >= I.n) continue;
+                const int cnt = I.n - i0 < 16 ? I.n - i0 : 16;
+                const int64_t base_off = static_cast<int64_t>(i0) * I.d + c;
+                float zv[16], xi[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    if (e < cnt) zv[e] = I.z[base_off + e * I.d];
+                if (I.noise_buf) {
+                    const float *nb = I.noise_buf + static_cast<int64_t>(cf.k + 1) * I.n * I.d;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (e < cnt) xi[e] = nb[base_off + e * I.d];
+                } else {
+#pragma unroll
+                    for (int e4 = 0; e4 < 4; ++e4) {
+                        const float4 v = noise4(I.seed, I.offset, cf.k + 1, c, (i0 >> 2) + e4);
+                        xi[e4 * 4 + 0] = v.x; xi[e4 * 4 + 1] = v.y; xi[e4 * 4 + 2] = v.z; xi[e4 * 4 + 3] = v.w;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    if (e >= cnt) break;
+                    const float g = obs ? lik_score(I.obs_op, zv[e], yc, I.inv_r) : 0.f;
+                    const float zn = em_update(cf, zv[e], u[e], g, xi[e]);
+                    const int64_t off = base_off + e * I.d;
+                    I.z[off] = zn;
+                    const float zc = zn - shift;
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
+                    I.zb_hi[off] = hi;
+                    if (I.zb_lo) I.zb_lo[off] = __float2bfloat16_rn(zc - __bfloat162float(hi));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[slot]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kWxTmemCols);
+    }
+}
+
 }  // namespace
 
 // =================================================================== host
@@ -825,6 +1055,67 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     if (BN == 256) return run_wx<256, 4, false>(maps, p, sms, s);
     if (BN == 128) return run_wx<128, 6, false>(maps, p, sms, s);
     return run_wx<64, 8, false>(maps, p, sms, s);
+}
+
+cudaError_t tc_encode_map(TcContext *ctx, void *out128, const void *base, int64_t cols, int64_t rows, int64_t pitch,
+                          int box_rows) {
+    if (!ctx) return cudaErrorInvalidValue;
+    return make_map(ctx, static_cast<CUtensorMap *>(out128), base, cols, rows, pitch, box_rows);
+}
+
+cudaError_t launch_gram_tc_batched(const void *maps, const BGramItem *items, int n_items, const BInst *insts,
+                                   bool split3, int *err, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
+    if (split3) {
+        using P = Plan<kBatchTileN, 3, true>;
+        auto kern = k_gram_tc_batched<kBatchTileN, 3, true>;
+        cudaError_t e = set_smem(kern, P::kBytes);
+        if (e != cudaSuccess) return e;
+        kern<<<n_items, 192, P::kBytes, s>>>(m, items, insts, err);
+    } else {
+        using P = Plan<kBatchTileN, 6, false>;
+        auto kern = k_gram_tc_batched<kBatchTileN, 6, false>;
+        cudaError_t e = set_smem(kern, P::kBytes);
+        if (e != cudaSuccess) return e;
+        kern<<<n_items, 192, P::kBytes, s>>>(m, items, insts, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_softmax_batched(const BRow *rows, int n_rows, const BInst *insts, int max_n, double alpha,
+                                   double inv_2beta2, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * static_cast<size_t>(max_n);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_softmax_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k_softmax_batched<<<n_rows, 256, smem, s>>>(rows, insts, alpha, inv_2beta2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wx_em_tc_batched(const void *maps, const BWxItem *items, int n_items, const BInst *insts,
+                                    bool split, const StepCoef &cf, float alpha_next, int *err, int sms,
+                                    cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
+    const int grid = n_items < sms ? n_items : sms;
+    if (split) {
+        using P = WxPlan<kBatchTileN, 3, true>;
+        auto kern = k_wx_em_tc_batched<kBatchTileN, 3, true>;
+        cudaError_t e = set_smem(kern, P::kBytes);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, kWxThreads, P::kBytes, s>>>(m, items, n_items, insts, cf, alpha_next, err);
+    } else {
+        using P = WxPlan<kBatchTileN, 6, false>;
+        auto kern = k_wx_em_tc_batched<kBatchTileN, 6, false>;
+        cudaError_t e = set_smem(kern, P::kBytes);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, kWxThreads, P::kBytes, s>>>(m, items, n_items, insts, cf, alpha_next, err);
+    }
+    return cudaGetLastError();
 }
 
 // Time `launch` (reps launches after one warm-up) with events on stream s; ms per launch.

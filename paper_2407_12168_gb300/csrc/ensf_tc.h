@@ -66,6 +66,48 @@ struct TcWxArgs {
     int force_bn = 0;                    // autotuner: particle tile width to use (0: tuned/default)
 };
 
+// ------------------------------------------------------------- batched
+// Many independent filters in one launch per stage.  Per-instance tensor
+// maps and parameters live in device memory (the batch workspace); the work
+// is a list of tiles over all instances.
+constexpr int kBatchTileN = 128;   // Gram member tile and W X particle tile of the batched kernels
+constexpr int kBatchKbChunk = 32;  // k-blocks (of 64 state columns) per batched Gram work item
+
+struct BInst {
+    int n;                           // particles = forecast members of this filter
+    int ldw;                         // row pitch (elements) of the W and X^T planes: n rounded up to 8
+    int64_t d;                       // state dimension
+    int splits;                      // split-K slices of this instance's Gram
+    float *partial;                  // [splits][n][n]
+    const double *norms;             // [n] |x_j - m|^2
+    __nv_bfloat16 *wb_hi, *wb_lo;    // [n][ldw] weights (lo NULL for plain BF16)
+    float *z;                        // [n][d] particles, updated in place
+    __nv_bfloat16 *zb_hi, *zb_lo;    // [n][d] split copies for the next Gram
+    const float *y;                  // [d]
+    const uint8_t *mask;             // [d] or NULL
+    const float *centre;             // [d] forecast mean m
+    const float *noise_buf;          // [K+1][n][d] caller noise, or NULL: Philox in the kernel
+    uint64_t seed;
+    uint32_t offset;
+    float inv_r;                     // 1 / sigma_obs^2
+    int obs_op;
+};
+struct BGramItem { int inst, m0, n0, split; };  // one 128 x 128 Gram tile over one k-range
+struct BWxItem { int inst, m0, n0; };           // 128 state columns x 128 particles
+struct BRow { int inst, row; };                 // one softmax row
+
+// Host: encode one 2-D BF16 tensor map (cols contiguous, row pitch `pitch`
+// elements, box 64 x box_rows, 128-byte swizzle) into `out` (NULL base: zeroed).
+cudaError_t tc_encode_map(TcContext *ctx, void *out128, const void *base, int64_t cols, int64_t rows,
+                          int64_t pitch, int box_rows);
+cudaError_t launch_gram_tc_batched(const void *maps, const BGramItem *items, int n_items, const BInst *insts,
+                                   bool split3, int *err, cudaStream_t s);
+cudaError_t launch_softmax_batched(const BRow *rows, int n_rows, const BInst *insts, int max_n, double alpha,
+                                   double inv_2beta2, cudaStream_t s);
+cudaError_t launch_wx_em_tc_batched(const void *maps, const BWxItem *items, int n_items, const BInst *insts,
+                                    bool split, const StepCoef &cf, float alpha_next, int *err, int sms,
+                                    cudaStream_t s);
+
 cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *splits,
                            int64_t *part_stride, int *ldp, cudaStream_t s);
 cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStream_t s);

@@ -34,6 +34,12 @@ class EnsfNoise(ctypes.Structure):
     _fields_ = [("buf", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("offset", ctypes.c_uint32)]
 
 
+class EnsfInstance(ctypes.Structure):
+    _fields_ = [("prior", ctypes.c_void_p), ("n", ctypes.c_int), ("d", ctypes.c_int64), ("y", ctypes.c_void_p),
+                ("obs_mask", ctypes.c_void_p), ("obs_op", ctypes.c_int), ("sigma_obs", ctypes.c_float),
+                ("noise", EnsfNoise), ("out", ctypes.c_void_p)]
+
+
 class EnsfProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double)]
@@ -63,6 +69,11 @@ _SIGNATURES = [
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
                                      ctypes.c_float, ctypes.POINTER(EnsfNoise), ctypes.c_void_p,
                                      ctypes.POINTER(EnsfTuning), ctypes.c_void_p]),
+    ("ensf_batch_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(EnsfConfig), ctypes.POINTER(EnsfInstance),
+                                                     ctypes.c_int]),
+    ("ensf_analysis_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EnsfInstance), ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.c_void_p]),
     ("ensf_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_void_p, ctypes.c_void_p]),
@@ -213,6 +224,44 @@ class Filter:
                                     float(eps), ctypes.byref(nz), out.data_ptr(), ctypes.byref(rep),
                                     _stream_ptr(stream)), "ensf_autotune")
         return {f: getattr(rep, f) for f, _ in EnsfTuning._fields_}
+
+    def analysis_batched(self, filters, K: int, eps: float, outs=None, stream=None):
+        """Batched analysis of independent filters.  ``filters`` is a list of
+        dicts with device tensors ``prior`` [n][d], ``y`` [d], optional ``mask``
+        [d], and ``sigma_obs``, ``obs_op``, ``seed``, ``offset``; returns the
+        list of analysis ensembles."""
+        torch = _torch()
+        lib = load()
+        insts = (EnsfInstance * len(filters))()
+        keep = []
+        outs = outs or [None] * len(filters)
+        results = []
+        for i, f in enumerate(filters):
+            prior = _dev(f["prior"], torch.float32, "prior")
+            y = _dev(f["y"], torch.float32, "y")
+            mask = f.get("mask")
+            if mask is not None:
+                _dev(mask, torch.uint8, "mask")
+            out = outs[i] if outs[i] is not None else torch.empty_like(prior)
+            n, d = prior.shape
+            noise = f.get("noise")
+            insts[i] = EnsfInstance(prior.data_ptr(), n, d, y.data_ptr(),
+                                    mask.data_ptr() if mask is not None else None, int(f.get("obs_op", 0)),
+                                    float(f["sigma_obs"]),
+                                    EnsfNoise(noise.data_ptr() if noise is not None else None,
+                                              int(f.get("seed", 0)) & (2 ** 64 - 1), int(f.get("offset", 0))),
+                                    out.data_ptr())
+            keep.append((prior, y, mask, noise))
+            results.append(out)
+        nbytes = lib.ensf_batch_workspace_bytes(ctypes.byref(self.cfg), insts, len(filters))
+        if nbytes == 0:
+            raise ValueError("batched analysis needs tensor-core precisions and valid shapes")
+        if getattr(self, "_batch_ws", None) is None or self._batch_ws.numel() < nbytes + 256:
+            self._batch_ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = (self._batch_ws.data_ptr() + 255) // 256 * 256
+        _check(lib.ensf_analysis_batched(self._h, insts, len(filters), int(K), float(eps), ctypes.c_void_p(base),
+                                         nbytes, _stream_ptr(stream)), "ensf_analysis_batched")
+        return results
 
     def weights(self, z, prior, t: float, eps: float, stream=None):
         """Weights w_ij of Eq. 16 at pseudo-time t; returns [n][n_x] FP32."""

@@ -238,3 +238,60 @@ def test_autotuned_analysis_matches_oracle():
     cond = conditioning(p, ref, prec="split")
     rel, tie, bad = compare_members(got, ref, cond, TOL_FP32)
     assert not bad.any(), describe(rel, tie, bad)
+
+
+BATCH = [
+    # (seed, n, grid, layers, obs_op, obs_frac, sigma)
+    (41, 20, 16, 2, 0, 1.0, 0.6),    # d = 512
+    (42, 33, 36, 1, 1, 0.25, 0.4),   # d = 1296
+    (43, 70, 44, 1, 1, 0.6, 0.4),    # d = 1936
+    (44, 130, 32, 2, 0, 1.0, 0.5),   # d = 2048, N over one 128 tile
+    (45, 256, 24, 1, 1, 0.5, 0.5),   # d = 576, N = two tiles
+]
+
+
+@pytest.mark.parametrize("path", ["split", "split-bf16"])
+def test_batched_analysis_matches_oracle(path):
+    """Five filters with uneven N and d in one batched analysis (one launch
+    per stage for all of them): each against the oracle, sampled rows."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    gram, wx, tol = PATHS[path]
+    K = 8
+    probs = [inputs.small_case(seed=c[0], n=c[1], grid=c[2], layers=c[3], K=K, obs_op=c[4], obs_frac=c[5],
+                               sigma_obs=c[6]) for c in BATCH]
+    f = ensf.Filter(256, 4096, gram=gram, wx=wx)
+    filters = [dict(prior=torch.from_numpy(p.prior).cuda(), y=torch.from_numpy(p.y).cuda(),
+                    mask=torch.from_numpy(p.mask).cuda() if p.mask is not None else None, sigma_obs=p.sigma_obs,
+                    obs_op=p.obs_op, seed=p.seed, offset=3) for p in probs]
+    outs = f.analysis_batched(filters, K, 0.05)
+    assert f.status_sync() == 0
+    for p, out in zip(probs, outs):
+        p.offset = 3
+        rows = np.unique(np.linspace(0, p.n - 1, min(p.n, 12)).astype(int))
+        ref = run_oracle(p, rows=rows)
+        cond = conditioning(p, ref, rows=rows, prec=_cond_prec(gram, wx))
+        got = out.cpu().numpy()[rows]
+        rel, tie, bad = compare_members(got, ref, cond, tol)
+        assert not bad.any(), f"{p.name}: " + describe(rel, tie, bad)
+        assert tie.sum() <= max(1, len(rows) // 6), f"{p.name}: " + describe(rel, tie, bad)
+
+
+def test_batched_graph_matches_eager():
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    probs = [inputs.small_case(seed=c[0], n=c[1], grid=c[2], layers=c[3], K=5, obs_op=c[4], obs_frac=c[5],
+                               sigma_obs=c[6]) for c in BATCH[:3]]
+    eager = ensf.Filter(256, 4096, gram="split", wx="bf16")
+    graph = ensf.Filter(256, 4096, gram="split", wx="bf16", graph=True)
+    stream = torch.cuda.Stream()
+    for rep in range(2):
+        filters = [dict(prior=torch.from_numpy(p.prior).cuda(), y=torch.from_numpy(p.y).cuda(),
+                        mask=torch.from_numpy(p.mask).cuda() if p.mask is not None else None,
+                        sigma_obs=p.sigma_obs, obs_op=p.obs_op, seed=p.seed + rep) for p in probs]
+        with torch.cuda.stream(stream):
+            a = eager.analysis_batched(filters, 5, 0.05)
+            b = graph.analysis_batched(filters, 5, 0.05)
+        stream.synchronize()
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
