@@ -210,6 +210,13 @@ size_t ensf_stats_scratch_bytes(int64_t d);
 ensf_status ensf_ensemble_stats(const float *z, int n, int64_t d, const float *truth,
                                 double *mean, double *rmse, void *scratch, void *stream);
 
+/* Spread relaxation used when cycling (Sec. IV-A: the analysis variance is
+ * relaxed to the prior (forecast) values): per state variable, the analysis
+ * anomalies z [n][d] about their mean are rescaled by (1 - factor) + factor *
+ * s_prior / s_analysis, s = ensemble standard deviation over the n members
+ * (FP64 accumulation); factor in [0, 1], 1 restores the forecast spread. */
+ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, float factor, void *stream);
+
 /* Launch accounting of a handle.  Every kernel launch is counted by kind
  * ("row_norms", "init_particles", "split_bf16", "gram", "softmax_rows",
  * "wx_em", "check_finite", "noise").  While profiling is on, each launch is also
@@ -228,6 +235,73 @@ ensf_status ensf_profile_enable(ensf_handle *h, int on);
 /* Waits for the recorded events; writes up to max_entries kinds with at least
  * one launch and sets *count to the number of such kinds. */
 ensf_status ensf_profile_read(ensf_handle *h, ensf_profile_entry *out, int max_entries, int *count);
+
+/* ---- Forecast-model companion: the two-level SQG integrator --------------
+ * The paper's forecast model (Sec. II-B): nonlinear Eady model on an f-plane
+ * with uniform stratification and shear, zero interior PV, the boundary
+ * potential temperatures theta (scaled so that d(psi)/dz = theta) advected on
+ * the two lids; doubly periodic pseudo-spectral discretisation (cuFFT), RK4,
+ * 2/3 dealiasing, hyperdiffusion del^8 applied implicitly after each step.
+ * Nondimensional: f = 1, lengths in units of N H / f when N_over_f = H = 1. */
+typedef struct {
+    int n;            /* grid points per side (even, >= 8)                         */
+    double L;         /* domain side                                                */
+    double H;         /* depth between the lids                                     */
+    double N_over_f;  /* buoyancy frequency / Coriolis parameter                    */
+    double shear;     /* Lambda = dU/dz of the mean flow U(z) = Lambda (z - H/2)    */
+    double dt;        /* RK4 time step                                              */
+    double tau_diss;  /* e-folding time of the hyperdiffusion at the largest wavenumber */
+    int diffusion;    /* 0 disables the hyperdiffusion                              */
+    double tau_relax; /* Newtonian relaxation time of theta, a large-scale sink (0: none) */
+} ensf_sqg_params;
+
+typedef struct ensf_sqg ensf_sqg;
+
+/* Device workspace for `batch` members (0 for invalid parameters).  The cuFFT
+ * plans keep their own small plan data; their work area is in the workspace. */
+size_t ensf_sqg_workspace_bytes(const ensf_sqg_params *p, int batch);
+ensf_status ensf_sqg_create(const ensf_sqg_params *p, int batch, void *workspace, size_t ws_bytes,
+                            ensf_sqg **out);
+/* Advances theta [batch][2][n][n] FP32 (device; level 0 = bottom) by nsteps
+ * RK4 steps, in place, on `stream`. */
+ensf_status ensf_sqg_run(ensf_sqg *s, float *theta, int nsteps, void *stream);
+ensf_status ensf_sqg_destroy(ensf_sqg *s);
+
+/* ---- Learned forecast surrogate: a conv U-Net trained in BF16 -------------
+ * x_{t+Delta} = x_t + net(x_t) on the two-level SQG state [B][2][H][W] (FP32
+ * NCHW at the interface).  net: encoder 2->w0->w1->w2->w3 (two 3x3 convs per
+ * level, circular padding, SiLU, 2x2 mean pooling), decoder with nearest x2
+ * upsampling and skip concatenation back to w0, 1x1 head to 2 channels.  The
+ * convolutions run as BF16 GEMMs on the tensor cores (FP32 accumulation);
+ * FP32 master weights, AdamW.  Stands in for the paper's ViT (Sec. III-B).
+ * Flat parameter order: per conv W [Cout][3][3][Cin] then b [Cout] (encoder,
+ * middle, decoder), then head W [2][w0], b [2]. */
+typedef struct {
+    int in_ch;        /* 2 */
+    int out_ch;       /* 2 */
+    int widths[4];    /* channel widths per level, multiples of 8            */
+    int height, width;/* multiples of 8, >= 16                                */
+    int max_batch;
+} ensf_unet_config;
+
+typedef struct ensf_unet ensf_unet;
+
+int64_t ensf_unet_param_count(const ensf_unet_config *cfg);
+size_t ensf_unet_workspace_bytes(const ensf_unet_config *cfg);
+ensf_status ensf_unet_create(const ensf_unet_config *cfg, void *workspace, size_t ws_bytes, ensf_unet **out);
+/* Load / read the flat FP32 parameter vector (device); loading resets AdamW. */
+ensf_status ensf_unet_set_params(ensf_unet *u, const float *params, void *stream);
+ensf_status ensf_unet_get_params(ensf_unet *u, float *params, void *stream);
+/* y [B][2][H][W] = surrogate forecast of x [B][2][H][W] (device FP32). */
+ensf_status ensf_unet_forward(ensf_unet *u, const float *x, int batch, float *y, void *stream);
+/* Mean-squared-error loss against target and its gradient w.r.t. the flat
+ * parameters (device FP32 [param_count]; grads or loss may be NULL). */
+ensf_status ensf_unet_gradients(ensf_unet *u, const float *x, const float *target, int batch, float *grads,
+                                double *loss, void *stream);
+/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8) on that loss; loss (device) may be NULL. */
+ensf_status ensf_unet_train_step(ensf_unet *u, const float *x, const float *target, int batch, float lr,
+                                 float weight_decay, double *loss, void *stream);
+ensf_status ensf_unet_destroy(ensf_unet *u);
 
 /* Wait for `stream` and return the handle's recorded device error, clearing it. */
 ensf_status ensf_status_sync(ensf_handle *h, void *stream);

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libensf.so")
-SOURCES = ["ensf_api.cu", "ensf_simt.cu", "ensf_tc.cu", "ensf_static.cu"]
+SOURCES = ["ensf_api.cu", "ensf_simt.cu", "ensf_tc.cu", "ensf_static.cu", "ensf_sqg.cu", "ensf_unet.cu"]
 HEADERS = ["ensf_device.cuh", "ensf_internal.h", "ensf_tc.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -66,7 +66,9 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         for f in futs:
             f.result()
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+    subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs,
+                           "-L" + cuda_lib, "-lcufft", "-Xlinker", "-rpath", "-Xlinker", cuda_lib])
     os.replace(tmp, LIB)
     return LIB
 

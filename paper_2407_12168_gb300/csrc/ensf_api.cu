@@ -649,6 +649,13 @@ ensf_status ensf_row_norms(const float *x, int n, int64_t d, double *out, void *
     return ENSF_OK;
 }
 
+ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, float factor, void *stream) {
+    if (!prior || !z || n < 2 || d < 1 || !(factor >= 0.0f && factor <= 1.0f))
+        return fail(ENSF_EINVAL, "ensf_relax_spread: bad arguments");
+    ENSF_CUDA(ensf::launch_relax_spread(prior, z, n, d, factor, static_cast<cudaStream_t>(stream)));
+    return ENSF_OK;
+}
+
 size_t ensf_stats_scratch_bytes(int64_t d) {
     return d < 1 ? 0 : sizeof(double) * (size_t)ensf::stats_blocks(d);
 }

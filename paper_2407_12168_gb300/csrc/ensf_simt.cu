@@ -360,7 +360,36 @@ __global__ void k_stats_rmse(const double *__restrict__ block_sq, int blocks, in
     if (threadIdx.x == 0) *rmse = sqrt(red[0] / (double)d);
 }
 
+// Relaxation of the analysis spread to the prior (forecast) spread, per
+// state variable c: with means m_f, m_a and standard deviations s_f, s_a over
+// the n members,  z_i <- m_a + (z_i - m_a) ((1 - a) + a s_f / s_a).
+__global__ void k_relax_spread(const float *__restrict__ prior, float *__restrict__ z, int n, int64_t d, float a) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d) return;
+    double sf = 0.0, sf2 = 0.0, sa = 0.0, sa2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double xf = prior[(int64_t)i * d + c], xa = z[(int64_t)i * d + c];
+        sf += xf;
+        sf2 += xf * xf;
+        sa += xa;
+        sa2 += xa * xa;
+    }
+    const double mf = sf / n, ma = sa / n;
+    const double vf = fmax(sf2 / n - mf * mf, 0.0), va = fmax(sa2 / n - ma * ma, 0.0);
+    const double ratio = va > 0.0 ? sqrt(vf / va) : 1.0;
+    const double f = (1.0 - a) + a * ratio;
+    for (int i = 0; i < n; ++i) {
+        const int64_t o = (int64_t)i * d + c;
+        z[o] = (float)(ma + (z[o] - ma) * f);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, cudaStream_t s) {
+    k_relax_spread<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(prior, z, n, d, a);
+    return cudaGetLastError();
+}
 
 // ===========================================================================
 cudaError_t launch_init_particles(float *z, int n, int64_t d, const float *noise_buf,

@@ -1,0 +1,789 @@
+// ensf_unet.cu -- the learned forecast surrogate: a small convolutional U-Net
+// x_{t+Delta} = x_t + net(x_t) over the two-level SQG state, trained and run
+// in BF16 with FP32 accumulation on this library's own kernels.
+//
+// Architecture (widths c1..c4): enc1 conv(2->c1), conv(c1->c1); 2x2 mean
+// pool; enc2 (c1->c2, c2->c2); pool; enc3 (c2->c3, c3->c3); pool; mid
+// (c3->c4, c4->c4); x2 nearest upsample + concat [up, skip] then two convs per
+// decoder level back to c3, c2, c1; 1x1 head c1->2, no activation; residual
+// output.  conv = 3x3 with circular padding (the SQG domain is periodic) +
+// bias + SiLU.  Loss: mean squared error.  Optimiser: AdamW on FP32 master
+// weights; BF16 copies feed the tensor cores.
+//
+// Every 3x3 convolution is a BF16 GEMM on the tcgen05 kernel of ensf_tc.cu
+// (C[M][N] = A[M][K] B[N][K]^T, FP32 accumulation, split-K partials):
+//   forward        col [P][Kp]  x  W  [Cout][Kp]   -> [P][Cout]
+//   data gradient  dZ  [P][Cout] x W^T [Kp][Cout]  -> dcol [P][Kp] -> col2im
+//   weight grad.   dZ^T [Cout][P] x col^T [Kp][P]   -> dW [Cout][Kp]
+// with P = batch * H * W pixels, Kp = 9 Cin rounded up to 8 (zero padded).
+// Layouts: activations NHWC (pixel-major), weights [Cout][3][3][Cin].
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ensf.h"
+#include "ensf_internal.h"
+#include "ensf_tc.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int kLevels = 3;
+constexpr int kConvs = 14;
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + __expf(-z)); }
+
+unsigned nb(int64_t count, int t = 256) { return (unsigned)((count + t - 1) / t); }
+
+// ------------------------------------------------------------- kernels
+__global__ void k_nchw_to_nhwc(const float *__restrict__ x, int B, int C, int H, int W, float *__restrict__ f32,
+                               bf16 *__restrict__ b16) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // NHWC index
+    const int64_t total = (int64_t)B * H * W * C;
+    if (i >= total) return;
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int xx = (int)(p % W), yy = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    const float v = x[(((int64_t)b * C + c) * H + yy) * W + xx];
+    if (f32) f32[i] = v;
+    if (b16) b16[i] = __float2bfloat16_rn(v);
+}
+
+// col[p][k], k = (dy*3 + dx)*C + c, circular neighbours; zero for k >= 9C.
+__global__ void k_im2col(const bf16 *__restrict__ x, int B, int H, int W, int C, int Kp, bf16 *__restrict__ col) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)B * H * W * Kp;
+    if (i >= total) return;
+    const int k = (int)(i % Kp);
+    const int64_t p = i / Kp;
+    bf16 v = __float2bfloat16_rn(0.f);
+    if (k < 9 * C) {
+        const int c = k % C, tap = k / C, dy = tap / 3, dx = tap % 3;
+        const int xx = (int)(p % W), yy = (int)((p / W) % H);
+        const int64_t b = p / ((int64_t)W * H);
+        const int sy = (yy + dy - 1 + H) % H, sx = (xx + dx - 1 + W) % W;
+        v = x[((b * H + sy) * W + sx) * C + c];
+    }
+    col[i] = v;
+}
+
+// Adjoint of k_im2col: dx[b][y][x][c] (+)= sum over taps of dcol at the pixel
+// that read (y, x) through that tap.
+__global__ void k_col2im(const float *__restrict__ dcol, int B, int H, int W, int C, int Kp, float *__restrict__ dx,
+                         int accumulate) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)B * H * W * C;
+    if (i >= total) return;
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const int64_t b = p / ((int64_t)W * H);
+    float acc = 0.f;
+    for (int dy = 0; dy < 3; ++dy)
+        for (int dxx = 0; dxx < 3; ++dxx) {
+            const int oy = (yy - dy + 1 + H) % H, ox = (xx - dxx + 1 + W) % W;
+            acc += dcol[((b * H + oy) * W + ox) * Kp + (dy * 3 + dxx) * C + c];
+        }
+    dx[i] = accumulate ? dx[i] + acc : acc;
+}
+
+__global__ void k_reduce_splits(const float *__restrict__ part, int S, int64_t count, float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float acc = 0.f;
+    for (int s = 0; s < S; ++s) acc += part[(int64_t)s * count + i];
+    out[i] = acc;
+}
+
+__global__ void k_bias_silu(const float *__restrict__ c, const float *__restrict__ bias, int64_t P, int Co,
+                            float *__restrict__ z, bf16 *__restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * Co) return;
+    const float zz = c[i] + bias[i % Co];
+    z[i] = zz;
+    y[i] = __float2bfloat16_rn(zz * sigmoidf_(zz));
+}
+
+// dZ = dY * silu'(z): FP32 (bias sums) and BF16 (GEMM operand) copies.
+__global__ void k_silu_back(const float *__restrict__ dy, const float *__restrict__ z, int64_t count,
+                            float *__restrict__ dz32, bf16 *__restrict__ dz16) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float s = sigmoidf_(z[i]);
+    const float g = dy[i] * s * (1.f + z[i] * (1.f - s));
+    dz32[i] = g;
+    dz16[i] = __float2bfloat16_rn(g);
+}
+
+// Column sums of in [P][C] in two fixed-order stages: partial[blk][c] over
+// row chunks, then out[c] (+)= sum over blocks.
+__global__ void k_colsum_partial(const float *__restrict__ in, int64_t P, int C, int64_t rows_per_blk,
+                                 float *__restrict__ partial) {
+    const int c = threadIdx.x + blockIdx.y * blockDim.x;
+    if (c >= C) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+    const int64_t r1 = r0 + rows_per_blk < P ? r0 + rows_per_blk : P;
+    float acc = 0.f;
+    for (int64_t r = r0; r < r1; ++r) acc += in[r * C + c];
+    partial[(int64_t)blockIdx.x * C + c] = acc;
+}
+
+__global__ void k_colsum_final(const float *__restrict__ partial, int blocks, int C, float *__restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float acc = 0.f;
+    for (int b = 0; b < blocks; ++b) acc += partial[(int64_t)b * C + c];
+    out[c] = acc;
+}
+
+__global__ void k_transpose_bf16(const bf16 *__restrict__ in, int64_t R, int C, bf16 *__restrict__ out) {
+    __shared__ bf16 tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int c0 = blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t r = r0 + k;
+        const int c = c0 + threadIdx.x;
+        tile[k][threadIdx.x] = (r < R && c < C) ? in[r * C + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < C && r < R) out[(int64_t)c * R + r] = tile[threadIdx.x][k];
+    }
+}
+
+__global__ void k_pool_fwd(const bf16 *__restrict__ x, int B, int H, int W, int C, bf16 *__restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = H / 2, w = W / 2;
+    if (i >= (int64_t)B * h * w * C) return;
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int xx = (int)(p % w), yy = (int)((p / w) % h);
+    const int64_t b = p / ((int64_t)w * h);
+    float s = 0.f;
+    for (int a = 0; a < 2; ++a)
+        for (int e = 0; e < 2; ++e) s += __bfloat162float(x[((b * H + 2 * yy + a) * W + 2 * xx + e) * C + c]);
+    y[i] = __float2bfloat16_rn(0.25f * s);
+}
+
+__global__ void k_pool_bwd(const float *__restrict__ dy, int B, int H, int W, int C, float *__restrict__ dx,
+                           int accumulate) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over the fine grid
+    if (i >= (int64_t)B * H * W * C) return;
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const int64_t b = p / ((int64_t)W * H);
+    const float g = 0.25f * dy[((b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c];
+    dx[i] = accumulate ? dx[i] + g : g;
+}
+
+// out[b][y][x] = [low upsampled (Cl channels), skip (Cs channels)]
+__global__ void k_up_concat_fwd(const bf16 *__restrict__ low, const bf16 *__restrict__ skip, int B, int H, int W,
+                                int Cl, int Cs, bf16 *__restrict__ out) {
+    const int Ct = Cl + Cs;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * H * W * Ct) return;
+    const int c = (int)(i % Ct);
+    const int64_t p = i / Ct;
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const int64_t b = p / ((int64_t)W * H);
+    out[i] = c < Cl ? low[((b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * Cl + c] : skip[p * Cs + (c - Cl)];
+}
+
+// Gradient of k_up_concat_fwd: dlow (coarse, sum of 4) and dskip (+=).
+__global__ void k_up_bwd(const float *__restrict__ dout, int B, int H, int W, int Cl, int Cs,
+                         float *__restrict__ dlow) {
+    const int Ct = Cl + Cs;
+    const int h = H / 2, w = W / 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * h * w * Cl) return;
+    const int c = (int)(i % Cl);
+    const int64_t p = i / Cl;
+    const int xx = (int)(p % w), yy = (int)((p / w) % h);
+    const int64_t b = p / ((int64_t)w * h);
+    float s = 0.f;
+    for (int a = 0; a < 2; ++a)
+        for (int e = 0; e < 2; ++e) s += dout[((b * H + 2 * yy + a) * W + 2 * xx + e) * Ct + c];
+    dlow[i] = s;
+}
+
+__global__ void k_skip_bwd(const float *__restrict__ dout, int64_t P, int Cl, int Cs, float *__restrict__ dskip) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * Cs) return;
+    const int64_t p = i / Cs;
+    const int c = (int)(i % Cs);
+    dskip[i] += dout[p * (Cl + Cs) + Cl + c];
+}
+
+// Head: out_nchw[b][o][y][x] = x_in + sum_c d1[p][c] Wh[o][c] + bh[o].
+__global__ void k_head_fwd(const bf16 *__restrict__ d1, const float *__restrict__ xin, const float *__restrict__ Wh,
+                           const float *__restrict__ bh, int B, int H, int W, int C, int O, float *__restrict__ out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)B * H * W) return;
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const int64_t b = p / ((int64_t)W * H);
+    for (int o = 0; o < O; ++o) {
+        float acc = bh[o] + xin[p * O + o];
+        for (int c = 0; c < C; ++c) acc += __bfloat162float(d1[p * C + c]) * Wh[o * C + c];
+        out[((b * O + o) * H + yy) * W + xx] = acc;
+    }
+}
+
+// Loss gradient at the output (NHWC dout [P][O]) and per-pixel squared error.
+__global__ void k_mse_grad(const float *__restrict__ out, const float *__restrict__ tgt, int B, int O, int H, int W,
+                           float *__restrict__ dout, float *__restrict__ sq) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // NCHW index
+    const int64_t total = (int64_t)B * O * H * W;
+    if (i >= total) return;
+    const int xx = (int)(i % W), yy = (int)((i / W) % H), o = (int)((i / ((int64_t)W * H)) % O);
+    const int64_t b = i / ((int64_t)W * H * O);
+    const float d = out[i] - tgt[i];
+    sq[i] = d * d;
+    dout[((b * H + yy) * W + xx) * O + o] = 2.f * d / (float)total;
+}
+
+// dd1[p][c] = sum_o dout[p][o] Wh[o][c]
+__global__ void k_head_dx(const float *__restrict__ dout, const float *__restrict__ Wh, int64_t P, int C, int O,
+                          float *__restrict__ dd1) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * C) return;
+    const int64_t p = i / C;
+    const int c = (int)(i % C);
+    float acc = 0.f;
+    for (int o = 0; o < O; ++o) acc += dout[p * O + o] * Wh[o * C + c];
+    dd1[i] = acc;
+}
+
+// per-block partial sums of dout[p][o] * d1[p][c] (o-major, then dout[p][o]) for the head gradients
+__global__ void k_head_dw_partial(const float *__restrict__ dout, const bf16 *__restrict__ d1, int64_t P, int C, int O,
+                                  int64_t rows_per_blk, float *__restrict__ partial) {
+    const int j = threadIdx.x + blockIdx.y * blockDim.x;  // 0 .. O*C + O - 1
+    const int nj = O * C + O;
+    if (j >= nj) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+    const int64_t r1 = r0 + rows_per_blk < P ? r0 + rows_per_blk : P;
+    float acc = 0.f;
+    if (j < O * C) {
+        const int o = j / C, c = j % C;
+        for (int64_t r = r0; r < r1; ++r) acc += dout[r * O + o] * __bfloat162float(d1[r * C + c]);
+    } else {
+        const int o = j - O * C;
+        for (int64_t r = r0; r < r1; ++r) acc += dout[r * O + o];
+    }
+    partial[(int64_t)blockIdx.x * nj + j] = acc;
+}
+
+__global__ void k_sum_partial_f64(const float *__restrict__ v, int64_t count, double *__restrict__ out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += 256) acc += (double)v[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] / (double)count;
+}
+
+// master W [Co][9Ci] -> Wb [Co][Kp] (zero padded) and Wt [Kp][Co]
+__global__ void k_repack(const float *__restrict__ w, int Co, int K9, int Kp, bf16 *__restrict__ wb,
+                         bf16 *__restrict__ wt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)Co * Kp) return;
+    const int o = (int)(i / Kp), k = (int)(i % Kp);
+    const bf16 v = __float2bfloat16_rn(k < K9 ? w[(int64_t)o * K9 + k] : 0.f);
+    wb[i] = v;
+    wt[(int64_t)k * Co + o] = v;
+}
+
+__global__ void k_unpad_grad(const float *__restrict__ c, int Co, int K9, int Kp, float *__restrict__ g) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)Co * K9) return;
+    g[i] = c[(i / K9) * Kp + i % K9];
+}
+
+__global__ void k_adamw(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                        float *__restrict__ v, int64_t count, float lr, float b1, float b2, float eps, float wd,
+                        float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
+}
+
+}  // namespace
+
+// ================================================================ host
+struct ensf_unet {
+    ensf_unet_config cfg;
+    ensf::TcContext *tc = nullptr;
+    int sms = 0;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t nparams = 0;
+    int64_t step = 0;
+    struct Conv {
+        int ci, co, kp, res;  // res: resolution level 0..3
+        int64_t w_off, b_off; // offsets in the flat parameter vector
+        bf16 *wb, *wt;        // BF16 weights [co][kp] and [kp][co]
+        float *z;             // pre-activation [P][co]
+        bf16 *y;              // activation [P][co]
+        const bf16 *in;       // input activation [P][ci]
+    } conv[kConvs];
+    int64_t head_w_off, head_b_off;
+    float *params, *grads, *adam_m, *adam_v;
+    float *xin32;              // input NHWC FP32 [P0][2]
+    bf16 *xin16;               // input NHWC BF16
+    bf16 *pool[kLevels];       // pooled activations at levels 1..3
+    bf16 *cat[kLevels];        // decoder concat buffers (levels 2, 1, 0)
+    float *out;                // prediction NCHW
+    float *dout, *sq;          // loss gradient NHWC [P0][2], squared errors NCHW
+    double *loss;              // device scalar
+    int *err;                  // device error word of the GEMM launches (ENSF_ETIMEOUT on an expired wait)
+    // scratch
+    bf16 *col, *colT, *dz16, *dzT;
+    float *gemm_c, *partial, *dz32, *ga, *gb, *colsum_part;
+    float *gskip[kLevels];     // gradients of the encoder outputs (skips), levels 0..2
+    int64_t partial_cap = 0;
+};
+
+namespace {
+
+struct Arena {
+    char *base;
+    size_t off = 0;
+    template <class T> T *take(int64_t count) {
+        size_t o = off;
+        off = (off + sizeof(T) * (size_t)count + 255) / 256 * 256;
+        return base ? reinterpret_cast<T *>(base + o) : nullptr;
+    }
+};
+
+bool unet_cfg_ok(const ensf_unet_config *c) {
+    if (!c || c->in_ch != 2 || c->out_ch != 2 || c->max_batch < 1) return false;
+    if (c->height < 16 || c->width < 16 || c->height % 8 || c->width % 8) return false;
+    for (int w : {c->widths[0], c->widths[1], c->widths[2], c->widths[3]})
+        if (w < 8 || w % 8 || w > 1024) return false;
+    return true;
+}
+
+int64_t round8(int64_t v) { return (v + 7) / 8 * 8; }
+
+// Lays out every buffer; with a null base only measures.
+size_t unet_layout(ensf_unet *u, const ensf_unet_config *c, char *base) {
+    Arena a{base};
+    const int w1 = c->widths[0], w2 = c->widths[1], w3 = c->widths[2], w4 = c->widths[3];
+    const int cin_[kConvs] = {2, w1, w1, w2, w2, w3, w3, w4, w4 + w3, w3, w3 + w2, w2, w2 + w1, w1};
+    const int cout_[kConvs] = {w1, w1, w2, w2, w3, w3, w4, w4, w3, w3, w2, w2, w1, w1};
+    const int res_[kConvs] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0};
+    const int64_t P0 = (int64_t)c->max_batch * c->height * c->width;
+    auto P = [&](int r) { return P0 >> (2 * r); };
+    int64_t off = 0, max_colk = 0, max_c = 0, max_chan = 0;
+    for (int l = 0; l < kConvs; ++l) {
+        ensf_unet::Conv &cv = u->conv[l];
+        cv.ci = cin_[l];
+        cv.co = cout_[l];
+        cv.kp = (int)round8(9 * cv.ci);
+        cv.res = res_[l];
+        cv.w_off = off;
+        off += 9 * (int64_t)cv.ci * cv.co;
+        cv.b_off = off;
+        off += cv.co;
+        max_colk = std::max<int64_t>(max_colk, P(cv.res) * cv.kp);
+        max_c = std::max<int64_t>(max_c, std::max<int64_t>(P(cv.res) * cv.co, P(cv.res) * cv.kp));
+        max_chan = std::max<int64_t>(max_chan, P(cv.res) * std::max(cv.ci, cv.co));
+    }
+    u->head_w_off = off;
+    off += 2 * (int64_t)w1;
+    u->head_b_off = off;
+    off += 2;
+    u->nparams = off;
+    u->params = a.take<float>(off);
+    u->grads = a.take<float>(off);
+    u->adam_m = a.take<float>(off);
+    u->adam_v = a.take<float>(off);
+    for (int l = 0; l < kConvs; ++l) {
+        ensf_unet::Conv &cv = u->conv[l];
+        cv.wb = a.take<bf16>((int64_t)cv.co * cv.kp);
+        cv.wt = a.take<bf16>((int64_t)cv.co * cv.kp);
+        cv.z = a.take<float>(P(cv.res) * cv.co);
+        cv.y = a.take<bf16>(P(cv.res) * cv.co);
+    }
+    u->xin32 = a.take<float>(P0 * 2);
+    u->xin16 = a.take<bf16>(P0 * 2);
+    u->pool[0] = a.take<bf16>(P(1) * w1);
+    u->pool[1] = a.take<bf16>(P(2) * w2);
+    u->pool[2] = a.take<bf16>(P(3) * w3);
+    u->cat[0] = a.take<bf16>(P(2) * (w4 + w3));
+    u->cat[1] = a.take<bf16>(P(1) * (w3 + w2));
+    u->cat[2] = a.take<bf16>(P(0) * (w2 + w1));
+    u->out = a.take<float>(P0 * 2);
+    u->dout = a.take<float>(P0 * 2);
+    u->sq = a.take<float>(P0 * 2);
+    u->loss = a.take<double>(1);
+    u->err = a.take<int>(4);
+    u->col = a.take<bf16>(max_colk);
+    u->colT = a.take<bf16>(max_colk);
+    u->dz16 = a.take<bf16>(max_chan);
+    u->dzT = a.take<bf16>(max_chan);
+    u->gemm_c = a.take<float>(max_c);
+    u->dz32 = a.take<float>(max_chan);
+    u->ga = a.take<float>(max_chan);
+    u->gb = a.take<float>(max_chan);
+    u->gskip[0] = a.take<float>(P(0) * w1);
+    u->gskip[1] = a.take<float>(P(1) * w2);
+    u->gskip[2] = a.take<float>(P(2) * w3);
+    u->colsum_part = a.take<float>((int64_t)1024 * std::max(1024, 2 * w1 + 2));
+    u->partial_cap = std::max<int64_t>(max_c, (int64_t)64 << 20);
+    u->partial = a.take<float>(u->partial_cap);
+    // inputs of the convolutions
+    if (base) {
+        u->conv[0].in = u->xin16;
+        for (int l = 1; l < kConvs; ++l) u->conv[l].in = u->conv[l - 1].y;
+        u->conv[2].in = u->pool[0];
+        u->conv[4].in = u->pool[1];
+        u->conv[6].in = u->pool[2];
+        u->conv[8].in = u->cat[0];
+        u->conv[10].in = u->cat[1];
+        u->conv[12].in = u->cat[2];
+    }
+    return a.off;
+}
+
+ensf_status unet_fail(ensf_status s, const char *m) {
+    ensf::set_last_error(m);
+    return s;
+}
+
+#define UNET_CUDA(call)                                                       \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return unet_fail(ENSF_ECUDA, #call);           \
+    } while (0)
+#define UNET_LAUNCH()                                                         \
+    do {                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                  \
+        if (e_ != cudaSuccess) return unet_fail(ENSF_ECUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+// C[M][N] (FP32) = A[M][K] B[N][K]^T on the tcgen05 GEMM (split-K partials summed in order).
+ensf_status gemm(ensf_unet *u, const bf16 *A, const bf16 *B, int64_t M, int64_t N, int64_t K, float *C,
+                 cudaStream_t s) {
+    ensf::TcGramArgs g;
+    g.zb_hi = A;
+    g.zb_lo = nullptr;
+    g.xb_hi = B;
+    g.xb_lo = nullptr;
+    g.n = (int)M;
+    g.n_x = (int)N;
+    g.d = K;
+    g.split3 = false;
+    g.partial = u->partial;
+    g.partial_cap = u->partial_cap;
+    g.err = u->err;
+    g.noise = nullptr;
+    g.seed = 0;
+    g.offset = 0;
+    g.noise_k = 0;
+    int splits = 0, ldp = 0;
+    int64_t ps = 0;
+    cudaError_t e = ensf::launch_gram_tc(u->tc, g, u->sms, &splits, &ps, &ldp, s);
+    if (e != cudaSuccess) return unet_fail(ENSF_ECUDA, "unet gemm launch");
+    k_reduce_splits<<<nb(M * N), 256, 0, s>>>(u->partial, splits, M * N, C);
+    UNET_LAUNCH();
+    return ENSF_OK;
+}
+
+ensf_status colsum(ensf_unet *u, const float *in, int64_t P, int C, float *out, cudaStream_t s) {
+    const int blocks = (int)std::min<int64_t>(1024, (P + 255) / 256);
+    const int64_t rows = (P + blocks - 1) / blocks;
+    dim3 grid(blocks, (C + 127) / 128);
+    k_colsum_partial<<<grid, 128, 0, s>>>(in, P, C, rows, u->colsum_part);
+    k_colsum_final<<<nb(C, 128), 128, 0, s>>>(u->colsum_part, blocks, C, out);
+    UNET_LAUNCH();
+    return ENSF_OK;
+}
+
+ensf_status forward(ensf_unet *u, const float *x_nchw, int B, cudaStream_t s) {
+    const int H = u->cfg.height, W = u->cfg.width;
+    const int w1 = u->cfg.widths[0], w2 = u->cfg.widths[1], w3 = u->cfg.widths[2], w4 = u->cfg.widths[3];
+    const int64_t P0 = (int64_t)B * H * W;
+    k_nchw_to_nhwc<<<nb(P0 * 2), 256, 0, s>>>(x_nchw, B, 2, H, W, u->xin32, u->xin16);
+    UNET_LAUNCH();
+    auto conv = [&](int l) -> ensf_status {
+        ensf_unet::Conv &cv = u->conv[l];
+        const int h = H >> cv.res, w = W >> cv.res;
+        const int64_t P = (int64_t)B * h * w;
+        k_im2col<<<nb(P * cv.kp), 256, 0, s>>>(cv.in, B, h, w, cv.ci, cv.kp, u->col);
+        UNET_LAUNCH();
+        ensf_status st = gemm(u, u->col, cv.wb, P, cv.co, cv.kp, u->gemm_c, s);
+        if (st != ENSF_OK) return st;
+        k_bias_silu<<<nb(P * cv.co), 256, 0, s>>>(u->gemm_c, u->params + cv.b_off, P, cv.co, cv.z, cv.y);
+        UNET_LAUNCH();
+        return ENSF_OK;
+    };
+    auto pool = [&](const bf16 *x, int res, int C, bf16 *y) -> ensf_status {
+        k_pool_fwd<<<nb((int64_t)B * (H >> (res + 1)) * (W >> (res + 1)) * C), 256, 0, s>>>(x, B, H >> res, W >> res,
+                                                                                            C, y);
+        UNET_LAUNCH();
+        return ENSF_OK;
+    };
+    auto upcat = [&](const bf16 *low, const bf16 *skip, int res, int Cl, int Cs, bf16 *out) -> ensf_status {
+        k_up_concat_fwd<<<nb((int64_t)B * (H >> res) * (W >> res) * (Cl + Cs)), 256, 0, s>>>(
+            low, skip, B, H >> res, W >> res, Cl, Cs, out);
+        UNET_LAUNCH();
+        return ENSF_OK;
+    };
+    ensf_status st;
+#define STEP(x)                 \
+    if ((st = (x)) != ENSF_OK) \
+        return st;
+    STEP(conv(0)) STEP(conv(1)) STEP(pool(u->conv[1].y, 0, w1, u->pool[0]))
+    STEP(conv(2)) STEP(conv(3)) STEP(pool(u->conv[3].y, 1, w2, u->pool[1]))
+    STEP(conv(4)) STEP(conv(5)) STEP(pool(u->conv[5].y, 2, w3, u->pool[2]))
+    STEP(conv(6)) STEP(conv(7)) STEP(upcat(u->conv[7].y, u->conv[5].y, 2, w4, w3, u->cat[0]))
+    STEP(conv(8)) STEP(conv(9)) STEP(upcat(u->conv[9].y, u->conv[3].y, 1, w3, w2, u->cat[1]))
+    STEP(conv(10)) STEP(conv(11)) STEP(upcat(u->conv[11].y, u->conv[1].y, 0, w2, w1, u->cat[2]))
+    STEP(conv(12)) STEP(conv(13))
+#undef STEP
+    k_head_fwd<<<nb(P0), 256, 0, s>>>(u->conv[13].y, u->xin32, u->params + u->head_w_off, u->params + u->head_b_off, B,
+                                      H, W, w1, 2, u->out);
+    UNET_LAUNCH();
+    return ENSF_OK;
+}
+
+// Backward pass of one convolution: dy [P][co] -> gradients of W, b and (+)= dx [P][ci].
+ensf_status conv_back(ensf_unet *u, int l, int B, const float *dy, float *dx, int accumulate, cudaStream_t s) {
+    ensf_unet::Conv &cv = u->conv[l];
+    const int h = u->cfg.height >> cv.res, w = u->cfg.width >> cv.res;
+    const int64_t P = (int64_t)B * h * w;
+    k_silu_back<<<nb(P * cv.co), 256, 0, s>>>(dy, cv.z, P * cv.co, u->dz32, u->dz16);
+    UNET_LAUNCH();
+    ensf_status st = colsum(u, u->dz32, P, cv.co, u->grads + cv.b_off, s);
+    if (st != ENSF_OK) return st;
+    // weight gradient: dZ^T [co][P] x col^T [kp][P]
+    k_im2col<<<nb(P * cv.kp), 256, 0, s>>>(cv.in, B, h, w, cv.ci, cv.kp, u->col);
+    UNET_LAUNCH();
+    k_transpose_bf16<<<dim3((cv.kp + 31) / 32, (unsigned)((P + 31) / 32)), dim3(32, 8), 0, s>>>(u->col, P, cv.kp,
+                                                                                              u->colT);
+    k_transpose_bf16<<<dim3((cv.co + 31) / 32, (unsigned)((P + 31) / 32)), dim3(32, 8), 0, s>>>(u->dz16, P, cv.co,
+                                                                                              u->dzT);
+    UNET_LAUNCH();
+    st = gemm(u, u->dzT, u->colT, cv.co, cv.kp, P, u->gemm_c, s);
+    if (st != ENSF_OK) return st;
+    k_unpad_grad<<<nb((int64_t)cv.co * 9 * cv.ci), 256, 0, s>>>(u->gemm_c, cv.co, 9 * cv.ci, cv.kp,
+                                                               u->grads + cv.w_off);
+    UNET_LAUNCH();
+    if (!dx) return ENSF_OK;
+    // data gradient: dZ [P][co] x W^T [kp][co] -> dcol [P][kp] -> col2im
+    st = gemm(u, u->dz16, cv.wt, P, cv.kp, cv.co, u->gemm_c, s);
+    if (st != ENSF_OK) return st;
+    k_col2im<<<nb(P * cv.ci), 256, 0, s>>>(u->gemm_c, B, h, w, cv.ci, cv.kp, dx, accumulate);
+    UNET_LAUNCH();
+    return ENSF_OK;
+}
+
+ensf_status backward(ensf_unet *u, const float *target, int B, cudaStream_t s) {
+    const int H = u->cfg.height, W = u->cfg.width;
+    const int w1 = u->cfg.widths[0], w2 = u->cfg.widths[1], w3 = u->cfg.widths[2], w4 = u->cfg.widths[3];
+    const int64_t P0 = (int64_t)B * H * W;
+    auto P = [&](int r) { return P0 >> (2 * r); };
+    k_mse_grad<<<nb(P0 * 2), 256, 0, s>>>(u->out, target, B, 2, H, W, u->dout, u->sq);
+    k_sum_partial_f64<<<1, 256, 0, s>>>(u->sq, P0 * 2, u->loss);
+    UNET_LAUNCH();
+    // head
+    {
+        const int nj = 2 * w1 + 2;
+        const int blocks = (int)std::min<int64_t>(1024, (P0 + 255) / 256);
+        const int64_t rows = (P0 + blocks - 1) / blocks;
+        k_head_dw_partial<<<dim3(blocks, (nj + 127) / 128), 128, 0, s>>>(u->dout, u->conv[13].y, P0, w1, 2, rows,
+                                                                         u->colsum_part);
+        k_colsum_final<<<nb(nj, 128), 128, 0, s>>>(u->colsum_part, blocks, nj, u->grads + u->head_w_off);
+        k_head_dx<<<nb(P0 * w1), 256, 0, s>>>(u->dout, u->params + u->head_w_off, P0, w1, 2, u->ga);
+        UNET_LAUNCH();
+    }
+    ensf_status st;
+#define STEP(x)                 \
+    if ((st = (x)) != ENSF_OK) \
+        return st;
+    // decoder level 0: convs 13, 12 (input = cat[2] = [up(d2) w2, e1 w1])
+    STEP(conv_back(u, 13, B, u->ga, u->gb, 0, s))
+    STEP(conv_back(u, 12, B, u->gb, u->ga, 0, s))   // ga = d cat[2] [P0][w2+w1]
+    UNET_CUDA(cudaMemsetAsync(u->gskip[0], 0, sizeof(float) * P(0) * w1, s));
+    k_skip_bwd<<<nb(P(0) * w1), 256, 0, s>>>(u->ga, P(0), w2, w1, u->gskip[0]);
+    k_up_bwd<<<nb(P(1) * w2), 256, 0, s>>>(u->ga, B, H, W, w2, w1, u->gb);  // gb = d d2 [P1][w2]
+    UNET_LAUNCH();
+    // decoder level 1: convs 11, 10 (input = cat[1] = [up(d3) w3, e2 w2])
+    STEP(conv_back(u, 11, B, u->gb, u->ga, 0, s))
+    STEP(conv_back(u, 10, B, u->ga, u->gb, 0, s))   // gb = d cat[1] [P1][w3+w2]
+    UNET_CUDA(cudaMemsetAsync(u->gskip[1], 0, sizeof(float) * P(1) * w2, s));
+    k_skip_bwd<<<nb(P(1) * w2), 256, 0, s>>>(u->gb, P(1), w3, w2, u->gskip[1]);
+    k_up_bwd<<<nb(P(2) * w3), 256, 0, s>>>(u->gb, B, H >> 1, W >> 1, w3, w2, u->ga);  // ga = d d3 [P2][w3]
+    UNET_LAUNCH();
+    // decoder level 2: convs 9, 8 (input = cat[0] = [up(m) w4, e3 w3])
+    STEP(conv_back(u, 9, B, u->ga, u->gb, 0, s))
+    STEP(conv_back(u, 8, B, u->gb, u->ga, 0, s))    // ga = d cat[0] [P2][w4+w3]
+    UNET_CUDA(cudaMemsetAsync(u->gskip[2], 0, sizeof(float) * P(2) * w3, s));
+    k_skip_bwd<<<nb(P(2) * w3), 256, 0, s>>>(u->ga, P(2), w4, w3, u->gskip[2]);
+    k_up_bwd<<<nb(P(3) * w4), 256, 0, s>>>(u->ga, B, H >> 2, W >> 2, w4, w3, u->gb);  // gb = d m [P3][w4]
+    UNET_LAUNCH();
+    // middle: convs 7, 6; then back through the pool into e3
+    STEP(conv_back(u, 7, B, u->gb, u->ga, 0, s))
+    STEP(conv_back(u, 6, B, u->ga, u->gb, 0, s))    // gb = d pool[2] [P3][w3]
+    k_pool_bwd<<<nb(P(2) * w3), 256, 0, s>>>(u->gb, B, H >> 2, W >> 2, w3, u->gskip[2], 1);
+    UNET_LAUNCH();
+    STEP(conv_back(u, 5, B, u->gskip[2], u->ga, 0, s))
+    STEP(conv_back(u, 4, B, u->ga, u->gb, 0, s))    // gb = d pool[1] [P2][w2]
+    k_pool_bwd<<<nb(P(1) * w2), 256, 0, s>>>(u->gb, B, H >> 1, W >> 1, w2, u->gskip[1], 1);
+    UNET_LAUNCH();
+    STEP(conv_back(u, 3, B, u->gskip[1], u->ga, 0, s))
+    STEP(conv_back(u, 2, B, u->ga, u->gb, 0, s))    // gb = d pool[0] [P1][w1]
+    k_pool_bwd<<<nb(P(0) * w1), 256, 0, s>>>(u->gb, B, H, W, w1, u->gskip[0], 1);
+    UNET_LAUNCH();
+    STEP(conv_back(u, 1, B, u->gskip[0], u->ga, 0, s))
+    STEP(conv_back(u, 0, B, u->ga, nullptr, 0, s))
+#undef STEP
+    return ENSF_OK;
+}
+
+ensf_status repack(ensf_unet *u, cudaStream_t s) {
+    for (int l = 0; l < kConvs; ++l) {
+        ensf_unet::Conv &cv = u->conv[l];
+        k_repack<<<nb((int64_t)cv.co * cv.kp), 256, 0, s>>>(u->params + cv.w_off, cv.co, 9 * cv.ci, cv.kp, cv.wb,
+                                                            cv.wt);
+    }
+    UNET_LAUNCH();
+    return ENSF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t ensf_unet_param_count(const ensf_unet_config *cfg) {
+    if (!unet_cfg_ok(cfg)) return 0;
+    ensf_unet tmp;
+    unet_layout(&tmp, cfg, nullptr);
+    return tmp.nparams;
+}
+
+size_t ensf_unet_workspace_bytes(const ensf_unet_config *cfg) {
+    if (!unet_cfg_ok(cfg)) return 0;
+    ensf_unet tmp;
+    return unet_layout(&tmp, cfg, nullptr);
+}
+
+ensf_status ensf_unet_create(const ensf_unet_config *cfg, void *workspace, size_t ws_bytes, ensf_unet **out) {
+    if (!out) return unet_fail(ENSF_EINVAL, "ensf_unet_create: out is NULL");
+    *out = nullptr;
+    if (!unet_cfg_ok(cfg)) return unet_fail(ENSF_EINVAL, "ensf_unet_create: invalid configuration");
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return unet_fail(ENSF_EINVAL, "ensf_unet_create: workspace must be 256-byte aligned");
+    ensf_unet *u = new (std::nothrow) ensf_unet;
+    if (!u) return unet_fail(ENSF_ENOMEM, "ensf_unet_create: host allocation failed");
+    u->cfg = *cfg;
+    const size_t need = unet_layout(u, cfg, static_cast<char *>(workspace));
+    if (ws_bytes < need) {
+        delete u;
+        return unet_fail(ENSF_ENOMEM, "ensf_unet_create: workspace too small");
+    }
+    u->ws = static_cast<char *>(workspace);
+    u->ws_bytes = ws_bytes;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        delete u;
+        return unet_fail(ENSF_ECUDA, "ensf_unet_create: device query failed");
+    }
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        delete u;
+        return unet_fail(ENSF_EUNSUPPORTED, "ensf_unet_create: needs an sm_103 device");
+    }
+    u->sms = prop.multiProcessorCount;
+    if (ensf::tc_context_create(&u->tc) != cudaSuccess) {
+        delete u;
+        return unet_fail(ENSF_ECUDA, "ensf_unet_create: tensor-map encoder unavailable");
+    }
+    if (cudaMemset(u->adam_m, 0, sizeof(float) * u->nparams) != cudaSuccess ||
+        cudaMemset(u->adam_v, 0, sizeof(float) * u->nparams) != cudaSuccess ||
+        cudaMemset(u->loss, 0, sizeof(double)) != cudaSuccess || cudaMemset(u->err, 0, 4 * sizeof(int)) != cudaSuccess) {
+        ensf::tc_context_destroy(u->tc);
+        delete u;
+        return unet_fail(ENSF_ECUDA, "ensf_unet_create: cudaMemset failed");
+    }
+    *out = u;
+    return ENSF_OK;
+}
+
+ensf_status ensf_unet_set_params(ensf_unet *u, const float *params, void *stream) {
+    if (!u || !params) return unet_fail(ENSF_EINVAL, "ensf_unet_set_params: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    UNET_CUDA(cudaMemcpyAsync(u->params, params, sizeof(float) * u->nparams, cudaMemcpyDeviceToDevice, s));
+    UNET_CUDA(cudaMemsetAsync(u->adam_m, 0, sizeof(float) * u->nparams, s));
+    UNET_CUDA(cudaMemsetAsync(u->adam_v, 0, sizeof(float) * u->nparams, s));
+    u->step = 0;
+    return repack(u, s);
+}
+
+ensf_status ensf_unet_get_params(ensf_unet *u, float *params, void *stream) {
+    if (!u || !params) return unet_fail(ENSF_EINVAL, "ensf_unet_get_params: bad arguments");
+    UNET_CUDA(cudaMemcpyAsync(params, u->params, sizeof(float) * u->nparams, cudaMemcpyDeviceToDevice,
+                              static_cast<cudaStream_t>(stream)));
+    return ENSF_OK;
+}
+
+ensf_status ensf_unet_forward(ensf_unet *u, const float *x, int batch, float *y, void *stream) {
+    if (!u || !x || !y || batch < 1 || batch > u->cfg.max_batch)
+        return unet_fail(ENSF_EINVAL, "ensf_unet_forward: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ensf_status st = forward(u, x, batch, s);
+    if (st != ENSF_OK) return st;
+    UNET_CUDA(cudaMemcpyAsync(y, u->out, sizeof(float) * (size_t)batch * 2 * u->cfg.height * u->cfg.width,
+                              cudaMemcpyDeviceToDevice, s));
+    return ENSF_OK;
+}
+
+ensf_status ensf_unet_gradients(ensf_unet *u, const float *x, const float *target, int batch, float *grads,
+                                double *loss, void *stream) {
+    if (!u || !x || !target || batch < 1 || batch > u->cfg.max_batch)
+        return unet_fail(ENSF_EINVAL, "ensf_unet_gradients: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ensf_status st = forward(u, x, batch, s);
+    if (st == ENSF_OK) st = backward(u, target, batch, s);
+    if (st != ENSF_OK) return st;
+    if (grads)
+        UNET_CUDA(cudaMemcpyAsync(grads, u->grads, sizeof(float) * u->nparams, cudaMemcpyDeviceToDevice, s));
+    if (loss) UNET_CUDA(cudaMemcpyAsync(loss, u->loss, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return ENSF_OK;
+}
+
+ensf_status ensf_unet_train_step(ensf_unet *u, const float *x, const float *target, int batch, float lr,
+                                 float weight_decay, double *loss, void *stream) {
+    ensf_status st = ensf_unet_gradients(u, x, target, batch, nullptr, loss, stream);
+    if (st != ENSF_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    u->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - (float)std::pow(b1, (double)u->step), c2 = 1.f - (float)std::pow(b2, (double)u->step);
+    k_adamw<<<nb(u->nparams), 256, 0, s>>>(u->params, u->grads, u->adam_m, u->adam_v, u->nparams, lr, b1, b2, 1e-8f,
+                                          weight_decay, c1, c2);
+    UNET_LAUNCH();
+    return repack(u, s);
+}
+
+ensf_status ensf_unet_destroy(ensf_unet *u) {
+    if (!u) return ENSF_EINVAL;
+    ensf::tc_context_destroy(u->tc);
+    delete u;
+    return ENSF_OK;
+}
+
+}  // extern "C"

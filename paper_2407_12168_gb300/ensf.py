@@ -50,6 +50,17 @@ class EnsfTuning(ctypes.Structure):
                 ("gram_ms", ctypes.c_float), ("wx_tile_n", ctypes.c_int), ("wx_ms", ctypes.c_float)]
 
 
+class EnsfSqgParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("L", ctypes.c_double), ("H", ctypes.c_double), ("N_over_f", ctypes.c_double),
+                ("shear", ctypes.c_double), ("dt", ctypes.c_double), ("tau_diss", ctypes.c_double),
+                ("diffusion", ctypes.c_int), ("tau_relax", ctypes.c_double)]
+
+
+class EnsfUnetConfig(ctypes.Structure):
+    _fields_ = [("in_ch", ctypes.c_int), ("out_ch", ctypes.c_int), ("widths", ctypes.c_int * 4),
+                ("height", ctypes.c_int), ("width", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
 class EnsfError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: status {status}: {message}")
@@ -84,6 +95,8 @@ _SIGNATURES = [
                                           ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_row_norms", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                       ctypes.c_void_p]),
+    ("ensf_relax_spread", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                         ctypes.c_float, ctypes.c_void_p]),
     ("ensf_stats_scratch_bytes", ctypes.c_size_t, [ctypes.c_int64]),
     ("ensf_ensemble_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -91,6 +104,24 @@ _SIGNATURES = [
     ("ensf_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ensf_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EnsfProfileEntry), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
+    ("ensf_sqg_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(EnsfSqgParams), ctypes.c_int]),
+    ("ensf_sqg_create", ctypes.c_int, [ctypes.POINTER(EnsfSqgParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    ("ensf_sqg_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("ensf_sqg_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("ensf_unet_param_count", ctypes.c_int64, [ctypes.POINTER(EnsfUnetConfig)]),
+    ("ensf_unet_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(EnsfUnetConfig)]),
+    ("ensf_unet_create", ctypes.c_int, [ctypes.POINTER(EnsfUnetConfig), ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    ("ensf_unet_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_unet_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_unet_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    ("ensf_unet_gradients", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_unet_train_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_float, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_unet_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("ensf_status_sync", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("ensf_last_error", ctypes.c_char_p, []),
@@ -304,6 +335,109 @@ def weights_static(z, prior, t: float, eps: float, out=None, stream=None):
     return w
 
 
+class SQG:
+    """GPU two-level SQG integrator over a batch of members (theta [B][2][n][n])."""
+
+    def __init__(self, batch: int, n: int = 128, L: float = 20.0, H: float = 1.0, N_over_f: float = 1.0,
+                 shear: float = 1.0, dt: float = 0.025, tau_diss: float = 0.1, diffusion: bool = True,
+                 tau_relax: float = 0.0):
+        torch = _torch()
+        lib = load()
+        self.params = EnsfSqgParams(int(n), float(L), float(H), float(N_over_f), float(shear), float(dt),
+                                    float(tau_diss), 1 if diffusion else 0, float(tau_relax))
+        nbytes = lib.ensf_sqg_workspace_bytes(ctypes.byref(self.params), int(batch))
+        if nbytes == 0:
+            raise ValueError("invalid SQG parameters")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        _check(lib.ensf_sqg_create(ctypes.byref(self.params), int(batch), ctypes.c_void_p(base), nbytes,
+                                   ctypes.byref(h)), "ensf_sqg_create")
+        self._h = h
+        self.batch, self.n = int(batch), int(n)
+
+    def run(self, theta, nsteps: int, stream=None):
+        """Advance theta [batch][2][n][n] (CUDA float32, in place) by nsteps RK4 steps."""
+        torch = _torch()
+        _dev(theta, torch.float32, "theta")
+        if tuple(theta.shape) != (self.batch, 2, self.n, self.n):
+            raise ValueError(f"theta must be {(self.batch, 2, self.n, self.n)}")
+        _check(load().ensf_sqg_run(self._h, theta.data_ptr(), int(nsteps), _stream_ptr(stream)), "ensf_sqg_run")
+        return theta
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None and self._h.value:
+                load().ensf_sqg_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+class UNet:
+    """The BF16 conv U-Net forecast surrogate (x_{t+Delta} = x_t + net(x_t))."""
+
+    def __init__(self, widths=(32, 64, 128, 256), height: int = 128, width: int = 128, max_batch: int = 16):
+        torch = _torch()
+        lib = load()
+        self.cfg = EnsfUnetConfig(2, 2, (ctypes.c_int * 4)(*[int(w) for w in widths]), int(height), int(width),
+                                  int(max_batch))
+        self.nparams = int(lib.ensf_unet_param_count(ctypes.byref(self.cfg)))
+        nbytes = lib.ensf_unet_workspace_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0 or self.nparams == 0:
+            raise ValueError("invalid U-Net configuration")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        _check(lib.ensf_unet_create(ctypes.byref(self.cfg), ctypes.c_void_p(base), nbytes, ctypes.byref(h)),
+               "ensf_unet_create")
+        self._h = h
+        self.loss_buf = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def set_params(self, params, stream=None):
+        torch = _torch()
+        _dev(params, torch.float32, "params")
+        if params.numel() != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters")
+        _check(load().ensf_unet_set_params(self._h, params.data_ptr(), _stream_ptr(stream)), "ensf_unet_set_params")
+
+    def get_params(self, stream=None):
+        torch = _torch()
+        out = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        _check(load().ensf_unet_get_params(self._h, out.data_ptr(), _stream_ptr(stream)), "ensf_unet_get_params")
+        return out
+
+    def forward(self, x, stream=None):
+        torch = _torch()
+        _dev(x, torch.float32, "x")
+        y = torch.empty_like(x)
+        _check(load().ensf_unet_forward(self._h, x.data_ptr(), x.shape[0], y.data_ptr(), _stream_ptr(stream)),
+               "ensf_unet_forward")
+        return y
+
+    def gradients(self, x, target, stream=None):
+        torch = _torch()
+        g = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        _check(load().ensf_unet_gradients(self._h, x.data_ptr(), target.data_ptr(), x.shape[0], g.data_ptr(),
+                                          self.loss_buf.data_ptr(), _stream_ptr(stream)), "ensf_unet_gradients")
+        return g, self.loss_buf
+
+    def train_step(self, x, target, lr: float, weight_decay: float = 0.0, stream=None):
+        """One AdamW step; returns the device loss scalar (before the step)."""
+        _check(load().ensf_unet_train_step(self._h, x.data_ptr(), target.data_ptr(), x.shape[0], float(lr),
+                                           float(weight_decay), self.loss_buf.data_ptr(), _stream_ptr(stream)),
+               "ensf_unet_train_step")
+        return self.loss_buf
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None and self._h.value:
+                load().ensf_unet_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
 def philox_normal(seed: int, offset: int, k0: int, count: int, n: int, d: int, stream=None):
     torch = _torch()
     out = torch.empty((count, n, d), dtype=torch.float32, device="cuda")
@@ -319,6 +453,17 @@ def row_norms(x, stream=None):
     _check(load().ensf_row_norms(x.data_ptr(), x.shape[0], x.shape[1], out.data_ptr(), _stream_ptr(stream)),
            "ensf_row_norms")
     return out
+
+
+def relax_spread(prior, z, factor: float = 1.0, stream=None):
+    """Rescale the analysis anomalies of z [n][d] toward the prior spread (in place)."""
+    torch = _torch()
+    _dev(prior, torch.float32, "prior")
+    _dev(z, torch.float32, "z")
+    n, d = z.shape
+    _check(load().ensf_relax_spread(prior.data_ptr(), z.data_ptr(), n, d, float(factor), _stream_ptr(stream)),
+           "ensf_relax_spread")
+    return z
 
 
 def ensemble_stats(z, truth: Optional[object] = None, stream=None):
