@@ -355,7 +355,7 @@ def run_ours(args):
     y = torch.from_numpy(p.y).to(dev)
     mask = torch.from_numpy(p.mask).to(dev) if p.mask is not None else None
     out = torch.empty_like(prior)
-    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, graph=args.graph)
+    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, graph=args.graph, inline_noise=args.inline_noise)
     stream = torch.cuda.current_stream()
     tuning = None
     if gram != "fp32" or wx != "fp32":
@@ -476,6 +476,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", action="store_true", help="replay each analysis as one captured CUDA graph")
+    ap.add_argument("--inline-noise", action="store_true",
+                    help="tensor-core W X evaluates the noise in its epilogue (no pre-generated slice)")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     args = ap.parse_args(argv)

@@ -65,6 +65,8 @@ typedef enum {
 } ensf_precision;
 
 #define ENSF_FLAG_CHECK_FINITE 1u  /* scan the final particles for NaN/Inf */
+#define ENSF_FLAG_INLINE_NOISE 4u  /* tensor-core W X: evaluate the Philox noise inside its epilogue
+                                      instead of reading a slice pre-generated during the Gram */
 #define ENSF_FLAG_CUDA_GRAPH 2u    /* ensf_analysis captures its whole launch sequence (all K
                                       Euler-Maruyama steps) into one CUDA graph and launches that;
                                       the instantiated graph is kept in the handle and updated in
@@ -210,12 +212,14 @@ size_t ensf_stats_scratch_bytes(int64_t d);
 ensf_status ensf_ensemble_stats(const float *z, int n, int64_t d, const float *truth,
                                 double *mean, double *rmse, void *scratch, void *stream);
 
-/* Spread relaxation used when cycling (Sec. IV-A: the analysis variance is
- * relaxed to the prior (forecast) values): per state variable, the analysis
- * anomalies z [n][d] about their mean are rescaled by (1 - factor) + factor *
- * s_prior / s_analysis, s = ensemble standard deviation over the n members
- * (FP64 accumulation); factor in [0, 1], 1 restores the forecast spread. */
-ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, float factor, void *stream);
+/* Relaxation to the prior used when cycling (Sec. IV-A: the analysis spread
+ * is relaxed to the prior (forecast) values), per state variable over the n
+ * members (FP64 accumulation), in place on the analysis z [n][d]:
+ *   mode 0 (spread):        anomalies rescaled by (1 - factor) + factor s_prior / s_analysis;
+ *   mode 1 (perturbations): anomalies (1 - factor) z' + factor x'_prior.
+ * factor in [0, 1]; 1 restores the forecast spread (mode 0) or perturbations (mode 1). */
+ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, float factor, int mode,
+                              void *stream);
 
 /* Launch accounting of a handle.  Every kernel launch is counted by kind
  * ("row_norms", "init_particles", "split_bf16", "gram", "softmax_rows",

@@ -410,7 +410,10 @@ ensf::TcWxArgs wx_args(ensf_handle *h, int n, int64_t d, const float *y, const u
     a.zb_lo = (is_tc(h->cfg.gram) && L.zb_lo) ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
     a.y = y;
     a.mask = obs_mask;
-    a.noise = noise->buf ? noise->buf + (size_t)(k + 1) * n * d : h->at<float>(L.noise);
+    a.noise = noise->buf ? noise->buf + (size_t)(k + 1) * n * d
+                         : ((h->cfg.flags & ENSF_FLAG_INLINE_NOISE) ? nullptr : h->at<float>(L.noise));
+    a.seed = noise->seed;
+    a.offset = noise->offset;
     a.centre = h->at<float>(L.xbar);
     a.alpha_next = alpha_next;
     a.coef = c;
@@ -436,7 +439,7 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
     // slice: with a tensor-core Gram its idle epilogue warps write xi[k+1]
     // while the MMAs of step k run; otherwise a separate launch does.
     float *nslice = tc_wx ? h->at<float>(L.noise) : nullptr;
-    const bool pregen = tc_wx && !noise->buf;
+    const bool pregen = tc_wx && !noise->buf && !(h->cfg.flags & ENSF_FLAG_INLINE_NOISE);
     for (int k = 0; k < K; ++k) {
         ensf::StepCoef c = step_coef(k, K, eps, sigma_obs, obs_op);
         NoiseRequest nr;
@@ -531,7 +534,7 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
     if (st != ENSF_OK) return st;
     ensf::StepCoef c = step_coef(K / 2, K, eps, sigma_obs, obs_op);
     NoiseRequest nr;
-    const bool pregen = tc_wx && !noise->buf;
+    const bool pregen = tc_wx && !noise->buf && !(h->cfg.flags & ENSF_FLAG_INLINE_NOISE);
     if (pregen && tc_gram) {
         nr.slice = h->at<float>(h->L.noise);
         nr.seed = noise->seed;
@@ -649,10 +652,10 @@ ensf_status ensf_row_norms(const float *x, int n, int64_t d, double *out, void *
     return ENSF_OK;
 }
 
-ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, float factor, void *stream) {
-    if (!prior || !z || n < 2 || d < 1 || !(factor >= 0.0f && factor <= 1.0f))
+ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, float factor, int mode, void *stream) {
+    if (!prior || !z || n < 2 || d < 1 || !(factor >= 0.0f && factor <= 1.0f) || (mode != 0 && mode != 1))
         return fail(ENSF_EINVAL, "ensf_relax_spread: bad arguments");
-    ENSF_CUDA(ensf::launch_relax_spread(prior, z, n, d, factor, static_cast<cudaStream_t>(stream)));
+    ENSF_CUDA(ensf::launch_relax_spread(prior, z, n, d, factor, mode, static_cast<cudaStream_t>(stream)));
     return ENSF_OK;
 }
 

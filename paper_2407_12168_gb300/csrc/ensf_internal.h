@@ -54,7 +54,7 @@ cudaError_t launch_ensemble_stats(const float *z, int n, int64_t d, const float 
                                   double *mean, double *rmse, double *scratch, cudaStream_t s);
 int stats_blocks(int64_t d);
 
-cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, cudaStream_t s);
+cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, int mode, cudaStream_t s);
 
 // Host-side message returned by ensf_last_error() on this thread.
 void set_last_error(const char *msg);

@@ -363,7 +363,9 @@ __global__ void k_stats_rmse(const double *__restrict__ block_sq, int blocks, in
 // Relaxation of the analysis spread to the prior (forecast) spread, per
 // state variable c: with means m_f, m_a and standard deviations s_f, s_a over
 // the n members,  z_i <- m_a + (z_i - m_a) ((1 - a) + a s_f / s_a).
-__global__ void k_relax_spread(const float *__restrict__ prior, float *__restrict__ z, int n, int64_t d, float a) {
+// mode 1 relaxes the perturbations instead:  z_i <- m_a + (1 - a)(z_i - m_a) + a (x_i - m_f).
+__global__ void k_relax_spread(const float *__restrict__ prior, float *__restrict__ z, int n, int64_t d, float a,
+                               int mode) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= d) return;
     double sf = 0.0, sf2 = 0.0, sa = 0.0, sa2 = 0.0;
@@ -380,14 +382,17 @@ __global__ void k_relax_spread(const float *__restrict__ prior, float *__restric
     const double f = (1.0 - a) + a * ratio;
     for (int i = 0; i < n; ++i) {
         const int64_t o = (int64_t)i * d + c;
-        z[o] = (float)(ma + (z[o] - ma) * f);
+        if (mode == 1)
+            z[o] = (float)(ma + (1.0 - a) * (z[o] - ma) + a * (prior[o] - mf));
+        else
+            z[o] = (float)(ma + (z[o] - ma) * f);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, cudaStream_t s) {
-    k_relax_spread<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(prior, z, n, d, a);
+cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, int mode, cudaStream_t s) {
+    k_relax_spread<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(prior, z, n, d, a, mode);
     return cudaGetLastError();
 }
 

@@ -440,7 +440,9 @@ struct WxParams {
     __nv_bfloat16 *zb_hi, *zb_lo;
     const float *y;
     const uint8_t *mask;
-    const float *noise;  // xi[k+1] slice [n][d]
+    const float *noise;  // xi[k+1] slice [n][d] (pre-generated form)
+    uint64_t seed;       // Philox stream (in-kernel form)
+    uint32_t offset;
     const float *centre; // Gram centre m [d] or NULL
     float alpha_next;    // z_hi/z_lo carry z - alpha_next m for the next Gram
     StepCoef coef;
@@ -451,7 +453,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, bool INLINE_NOISE>
 __global__ void __launch_bounds__(kWxThreads, 1)
 k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CUtensorMap xt_lo,
            const __grid_constant__ CUtensorMap w_hi, const __grid_constant__ CUtensorMap w_lo, WxParams p) {
@@ -586,7 +588,18 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
                 for (int e = 0; e < 16; ++e) {
                     if (e < cnt) {
                         zv[e] = p.z[base + e * p.d];
-                        xi[e] = p.noise[base + e * p.d];
+                        if (!INLINE_NOISE) xi[e] = p.noise[base + e * p.d];
+                    }
+                }
+                if (INLINE_NOISE) {
+                    // xi[k+1][i0 .. i0+15][c]: four Philox blocks of four particles each
+#pragma unroll
+                    for (int e4 = 0; e4 < 4; ++e4) {
+                        const float4 v = noise4(p.seed, p.offset, cf.k + 1, c, (i0 >> 2) + e4);
+                        xi[e4 * 4 + 0] = v.x;
+                        xi[e4 * 4 + 1] = v.y;
+                        xi[e4 * 4 + 2] = v.z;
+                        xi[e4 * 4 + 3] = v.w;
                     }
                 }
 #pragma unroll
@@ -913,10 +926,10 @@ cudaError_t run_gram(const CUtensorMap (&maps)[4], const GramParams &p, dim3 gri
     return cudaGetLastError();
 }
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, bool INLINE_NOISE>
 cudaError_t run_wx(const CUtensorMap (&maps)[4], WxParams p, int sms, cudaStream_t s) {
     using P = WxPlan<BN, STAGES, SPLIT>;
-    auto kern = k_wx_em_tc<BN, STAGES, SPLIT>;
+    auto kern = k_wx_em_tc<BN, STAGES, SPLIT, INLINE_NOISE>;
     cudaError_t e = set_smem(kern, P::kBytes);
     if (e != cudaSuccess) return e;
     p.n_tiles = (p.n + BN - 1) / BN;
@@ -1042,19 +1055,21 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     p.y = a.y;
     p.mask = a.mask;
     p.noise = a.noise;
+    p.seed = a.seed;
+    p.offset = a.offset;
     p.centre = a.centre;
     p.alpha_next = a.alpha_next;
     p.coef = a.coef;
     p.err = a.err;
-    if (!p.noise) return cudaErrorInvalidValue;
+    const bool inl = a.noise == nullptr;  // no slice: Philox in the epilogue
     if (split) {
-        if (BN == 256) return run_wx<256, 2, true>(maps, p, sms, s);
-        if (BN == 128) return run_wx<128, 3, true>(maps, p, sms, s);
-        return run_wx<64, 4, true>(maps, p, sms, s);
+        if (BN == 256) return inl ? run_wx<256, 2, true, true>(maps, p, sms, s) : run_wx<256, 2, true, false>(maps, p, sms, s);
+        if (BN == 128) return inl ? run_wx<128, 3, true, true>(maps, p, sms, s) : run_wx<128, 3, true, false>(maps, p, sms, s);
+        return inl ? run_wx<64, 4, true, true>(maps, p, sms, s) : run_wx<64, 4, true, false>(maps, p, sms, s);
     }
-    if (BN == 256) return run_wx<256, 4, false>(maps, p, sms, s);
-    if (BN == 128) return run_wx<128, 6, false>(maps, p, sms, s);
-    return run_wx<64, 8, false>(maps, p, sms, s);
+    if (BN == 256) return inl ? run_wx<256, 4, false, true>(maps, p, sms, s) : run_wx<256, 4, false, false>(maps, p, sms, s);
+    if (BN == 128) return inl ? run_wx<128, 6, false, true>(maps, p, sms, s) : run_wx<128, 6, false, false>(maps, p, sms, s);
+    return inl ? run_wx<64, 8, false, true>(maps, p, sms, s) : run_wx<64, 8, false, false>(maps, p, sms, s);
 }
 
 cudaError_t tc_encode_map(TcContext *ctx, void *out128, const void *base, int64_t cols, int64_t rows, int64_t pitch,

@@ -58,7 +58,9 @@ struct TcWxArgs {
     __nv_bfloat16 *zb_hi, *zb_lo;        // split copies of the updated particles (NULL: skip)
     const float *y;
     const uint8_t *mask;
-    const float *noise;                  // xi[k+1] as a [n][d] slice (pre-generated)
+    const float *noise;                  // xi[k+1] as a [n][d] slice (pre-generated), or NULL:
+    uint64_t seed;                       //   Philox stream (seed, offset) evaluated in the epilogue
+    uint32_t offset;
     const float *centre;                 // [d] Gram centre m (NULL: none); z_hi/z_lo split z - alpha_next m
     float alpha_next;                    // alpha of the next step's Gram
     StepCoef coef;

@@ -21,6 +21,7 @@ OBS_IDENTITY, OBS_ARCTAN = 0, 1
 PREC_FP32, PREC_SPLIT_BF16X3, PREC_BF16 = 0, 1, 2
 FLAG_CHECK_FINITE = 1
 FLAG_CUDA_GRAPH = 2
+FLAG_INLINE_NOISE = 4
 
 PRECISIONS = {"fp32": PREC_FP32, "split": PREC_SPLIT_BF16X3, "bf16": PREC_BF16}
 
@@ -96,7 +97,7 @@ _SIGNATURES = [
     ("ensf_row_norms", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     ("ensf_relax_spread", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
-                                         ctypes.c_float, ctypes.c_void_p]),
+                                         ctypes.c_float, ctypes.c_int, ctypes.c_void_p]),
     ("ensf_stats_scratch_bytes", ctypes.c_size_t, [ctypes.c_int64]),
     ("ensf_ensemble_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -187,11 +188,12 @@ class Filter:
     cores) or ``"bf16"`` (one BF16 product on tensor cores)."""
 
     def __init__(self, max_n: int, max_d: int, gram: str = "fp32", wx: str = "fp32",
-                 check_finite: bool = False, graph: bool = False):
+                 check_finite: bool = False, graph: bool = False, inline_noise: bool = False):
         torch = _torch()
         lib = load()
         self.cfg = EnsfConfig(int(max_n), int(max_d), PRECISIONS[gram], PRECISIONS[wx],
-                              (FLAG_CHECK_FINITE if check_finite else 0) | (FLAG_CUDA_GRAPH if graph else 0))
+                              (FLAG_CHECK_FINITE if check_finite else 0) | (FLAG_CUDA_GRAPH if graph else 0)
+                              | (FLAG_INLINE_NOISE if inline_noise else 0))
         nbytes = lib.ensf_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise ValueError("invalid EnSF configuration")
@@ -455,13 +457,16 @@ def row_norms(x, stream=None):
     return out
 
 
-def relax_spread(prior, z, factor: float = 1.0, stream=None):
-    """Rescale the analysis anomalies of z [n][d] toward the prior spread (in place)."""
+def relax_spread(prior, z, factor: float = 1.0, mode: str = "spread", stream=None):
+    """Relax the analysis z [n][d] toward the prior, in place: ``mode`` "spread"
+    rescales the anomalies to the prior spread, "perturbations" blends them
+    with the prior anomalies."""
     torch = _torch()
     _dev(prior, torch.float32, "prior")
     _dev(z, torch.float32, "z")
     n, d = z.shape
-    _check(load().ensf_relax_spread(prior.data_ptr(), z.data_ptr(), n, d, float(factor), _stream_ptr(stream)),
+    _check(load().ensf_relax_spread(prior.data_ptr(), z.data_ptr(), n, d, float(factor),
+                                    {"spread": 0, "perturbations": 1}[mode], _stream_ptr(stream)),
            "ensf_relax_spread")
     return z
 

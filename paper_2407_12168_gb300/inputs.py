@@ -146,6 +146,23 @@ def noise_buffer(seed: int, K: int, n: int, d: int) -> np.ndarray:
     return rng(seed, _TAG_NOISE).standard_normal((K + 1, n, d), dtype=np.float32)
 
 
+def unet_init_params(widths, seed: int, in_ch: int = 2, out_ch: int = 2) -> np.ndarray:
+    """Seeded initial parameters of the U-Net surrogate (flat order of the
+    library): He-uniform convolution weights, zero biases, a small head."""
+    g = rng(seed, _TAG_SHAPES, 99)
+    c1, c2, c3, c4 = widths
+    convs = [(in_ch, c1), (c1, c1), (c1, c2), (c2, c2), (c2, c3), (c3, c3), (c3, c4), (c4, c4),
+             (c4 + c3, c3), (c3, c3), (c3 + c2, c2), (c2, c2), (c2 + c1, c1), (c1, c1)]
+    parts = []
+    for ci, co in convs:
+        bound = np.sqrt(6.0 / (9 * ci))
+        parts.append(g.uniform(-bound, bound, 9 * ci * co))
+        parts.append(np.zeros(co))
+    parts.append(g.uniform(-0.01, 0.01, c1 * out_ch))
+    parts.append(np.zeros(out_ch))
+    return np.concatenate(parts).astype(np.float32)
+
+
 WORKLOADS = {
     "plain-64": plain_64,
     "sparse-arctan-128": sparse_arctan_128,

@@ -295,3 +295,16 @@ def test_batched_graph_matches_eager():
         stream.synchronize()
         for x, y in zip(a, b):
             np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+def test_inline_noise_is_bitwise_the_pregenerated_noise():
+    """ENSF_FLAG_INLINE_NOISE evaluates the same counter-based draws inside the
+    W X epilogue: the analysis is bitwise the pre-generated-slice one."""
+    p = inputs.small_case(seed=31, n=130, grid=32, layers=2, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    outs = []
+    for inline in (False, True):
+        f = ensf.Filter(p.n, p.d, gram="split", wx="bf16", inline_noise=inline)
+        outs.append(_gpu_analysis(p, "split", "bf16", filt=f))
+    np.testing.assert_array_equal(outs[0], outs[1])
