@@ -209,6 +209,11 @@ void ensf_oracle_prior_score(const float *X, int n, int64_t d, const double *z, 
  *         full analysis; fewer only to time a bounded sample)
  *   out   [nrows][d] final particles;  traj optional [k_stop+1][nrows][d]
  *         with the particles before step 0 and after every step.
+ *   perm, J mini-batch prior score (Eq. 15-16 with J < N): perm is a
+ *         permutation of the n members; Euler-Maruyama step k uses the J
+ *         members perm[w J .. w J + J - 1], w = k mod (n / J), for every
+ *         particle, with the weights normalised over those J.  perm = NULL
+ *         (or J = n with the identity) is the full ensemble.
  *   logit_perturb, perturb_seed
  *         0 for the analysis itself.  A test of how well a result is
  *         determined by its inputs sets logit_perturb > 0: every log-kernel
@@ -226,13 +231,18 @@ void ensf_oracle_prior_score(const float *X, int n, int64_t d, const double *z, 
 int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const uint8_t *mask,
                          double sigma_obs, int K, double eps, int obs_op, const float *noise,
                          uint64_t seed, uint32_t offset, const int *rows, int nrows, int k_stop,
-                         double logit_perturb, uint64_t perturb_seed, double *out, double *traj,
-                         double *diag)
+                         const int *perm, int J, double logit_perturb, uint64_t perturb_seed, double *out,
+                         double *traj, double *diag)
 {
     if (n < 1 || d < 1 || K < 1 || !(eps > 0.0 && eps < 1.0) || !(sigma_obs > 0.0))
         return -1;
     if (!rows) nrows = n;
     if (nrows < 1 || k_stop < 0 || k_stop > K) return -1;
+    if (!perm) J = n;
+    if (J < 1 || J > n || n % J != 0) return -1;
+    if (perm)
+        for (int j = 0; j < n; ++j)
+            if (perm[j] < 0 || perm[j] >= n) return -1;
     for (int r = 0; r < nrows; ++r) {
         int i = rows ? rows[r] : r;
         if (i < 0 || i >= n) return -1;
@@ -267,10 +277,14 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
         ensf_oracle_schedule(t, eps, sch);
         double alpha = sch[0], beta2 = sch[1], b = sch[2], sigma2 = sch[3], h = sch[4];
 
+        /* the members of this step: the whole ensemble, or the mini-batch window */
+        const int w0 = perm ? (k % (n / J)) * J : 0;
+        const int nm = perm ? J : n;
+#define MEMBER(jj) (perm ? perm[w0 + (jj)] : (jj))
         /* log-kernels -|z_i - alpha x_j|^2 / (2 beta^2), direct form (Eq. 12) */
 #pragma omp parallel for schedule(static)
-        for (int j = 0; j < n; ++j) {
-            const float *xj = X + (size_t)j * (size_t)d;
+        for (int j = 0; j < nm; ++j) {
+            const float *xj = X + (size_t)MEMBER(j) * (size_t)d;
             for (int r = 0; r < nrows; ++r) {
                 const double *z = out + (size_t)r * (size_t)d;
                 double dist2 = 0.0;
@@ -290,13 +304,13 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
             }
             for (int r = 0; r < nrows; ++r) {
                 int i = rows ? rows[r] : r;
-                for (int j = 0; j < n; ++j) {
-                    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)i, (uint32_t)k, 0x51EDu};
+                for (int j = 0; j < nm; ++j) {
+                    uint32_t ctr[4] = {(uint32_t)MEMBER(j), (uint32_t)i, (uint32_t)k, 0x51EDu};
                     uint32_t key[2] = {(uint32_t)perturb_seed, (uint32_t)(perturb_seed >> 32)};
                     uint32_t bits[4];
                     ensf_oracle_philox4x32_10(ctr, key, bits);
                     double sign = (bits[0] & 1u) ? 1.0 : -1.0;
-                    l[(size_t)r * n + j] += sign * logit_perturb * alpha * znorm[r] * xnorm[j] / beta2;
+                    l[(size_t)r * n + j] += sign * logit_perturb * alpha * znorm[r] * xnorm[MEMBER(j)] / beta2;
                 }
             }
         }
@@ -304,27 +318,27 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
         for (int r = 0; r < nrows; ++r) {
             double *lr = l + (size_t)r * n, *wr = w + (size_t)r * n;
             double lmax = lr[0];
-            for (int j = 1; j < n; ++j)
+            for (int j = 1; j < nm; ++j)
                 if (lr[j] > lmax) lmax = lr[j];
             if (diag) {
                 double second = -HUGE_VAL;
                 int top = 0;
-                for (int j = 1; j < n; ++j)
+                for (int j = 1; j < nm; ++j)
                     if (lr[j] > lr[top]) top = j;
-                for (int j = 0; j < n; ++j)
+                for (int j = 0; j < nm; ++j)
                     if (j != top && lr[j] > second) second = lr[j];
                 const double *z = out + (size_t)r * (size_t)d;
                 double zn = 0.0;
                 for (int64_t c = 0; c < d; ++c) zn += z[c] * z[c];
-                diag[((size_t)k * nrows + r) * 2 + 0] = (n > 1) ? lmax - second : HUGE_VAL;
+                diag[((size_t)k * nrows + r) * 2 + 0] = (nm > 1) ? lmax - second : HUGE_VAL;
                 diag[((size_t)k * nrows + r) * 2 + 1] = alpha * sqrt(zn) * xmax / beta2;
             }
             double total = 0.0;
-            for (int j = 0; j < n; ++j) {
+            for (int j = 0; j < nm; ++j) {
                 wr[j] = exp(lr[j] - lmax);
                 total += wr[j];
             }
-            for (int j = 0; j < n; ++j)
+            for (int j = 0; j < nm; ++j)
                 wr[j] /= total;
         }
         for (int r = 0; r < nrows; ++r) {
@@ -336,8 +350,8 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
             for (int64_t c = 0; c < d; ++c) {
                 /* prior score, Eq. 15 */
                 double s_prior = 0.0;
-                for (int j = 0; j < n; ++j)
-                    s_prior += -(z[c] - alpha * (double)X[(size_t)j * (size_t)d + c]) / beta2 * wr[j];
+                for (int j = 0; j < nm; ++j)
+                    s_prior += -(z[c] - alpha * (double)X[(size_t)MEMBER(j) * (size_t)d + c]) / beta2 * wr[j];
                 /* posterior score, Eq. 17 */
                 double s = s_prior + h * g[c];
                 double xi = noise ? (double)noise[((size_t)(k + 1) * n + i) * (size_t)d + c]
@@ -349,6 +363,7 @@ int ensf_oracle_analysis(const float *X, int n, int64_t d, const float *y, const
         if (traj)
             memcpy(traj + (size_t)(k + 1) * nrows * (size_t)d, out,
                    sizeof(double) * (size_t)nrows * (size_t)d);
+#undef MEMBER
     }
     free(w);
     free(l);

@@ -73,8 +73,8 @@ def _load():
         lib.ensf_oracle_analysis.argtypes = [fp, ctypes.c_int, ctypes.c_int64, fp, u8p,
                                              ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_int, fp, ctypes.c_uint64, ctypes.c_uint32,
-                                             ip, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                             ctypes.c_uint64, dp, dp, dp]
+                                             ip, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_uint64, dp, dp, dp]
         lib.ensf_oracle_analysis.restype = ctypes.c_int
         lib.ensf_oracle_mean_rmse.argtypes = [dp, ctypes.c_int, ctypes.c_int64, fp, dp]
         lib.ensf_oracle_mean_rmse.restype = ctypes.c_double
@@ -164,7 +164,7 @@ def prior_score(X, z, alpha: float, beta2: float) -> np.ndarray:
 def analysis(X, y, mask, sigma_obs: float, K: int, eps: float, obs_op: int = OBS_IDENTITY,
              noise_buf=None, seed: int = 0, offset: int = 0, rows=None, k_stop=None,
              return_traj: bool = False, return_diag: bool = False, logit_perturb: float = 0.0,
-             perturb_seed: int = 0):
+             perturb_seed: int = 0, perm=None, J=None):
     """Run the EnSF analysis (Eq. 7 discretised by Euler-Maruyama with the
     score of Eq. 17) for the particle rows ``rows`` (default: all).
 
@@ -172,7 +172,9 @@ def analysis(X, y, mask, sigma_obs: float, K: int, eps: float, obs_op: int = OBS
     trajectory [k_stop+1][len(rows)][d]; with ``return_diag`` also
     [k_stop][len(rows)][2] = (top-two log-kernel gap, log-kernel error scale)
     per step and row.  ``logit_perturb`` > 0 (tests of conditioning only)
-    adds +/- logit_perturb * alpha |z_i| |x_j| / beta^2 to every log-kernel."""
+    adds +/- logit_perturb * alpha |z_i| |x_j| / beta^2 to every log-kernel.
+    ``perm``, ``J``: mini-batch prior score over the window k mod (n/J) of J
+    members of the permutation (Eq. 15-16 with J < N)."""
     X = _f32(X)
     n, d = X.shape
     y = _f32(y)
@@ -186,10 +188,13 @@ def analysis(X, y, mask, sigma_obs: float, K: int, eps: float, obs_op: int = OBS
     out = np.zeros((nrows, d))
     traj = np.zeros((ks + 1, nrows, d)) if return_traj else None
     diag = np.zeros((ks, nrows, 2)) if return_diag else None
+    pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    jj = n if J is None else int(J)
     rc = _load().ensf_oracle_analysis(
         _ptr(X, ctypes.c_float), n, d, _ptr(y, ctypes.c_float), _ptr(m, ctypes.c_uint8),
         float(sigma_obs), int(K), float(eps), int(obs_op), _ptr(nb, ctypes.c_float),
-        int(seed), int(offset), _ptr(r, ctypes.c_int), nrows, ks, float(logit_perturb), int(perturb_seed),
+        int(seed), int(offset), _ptr(r, ctypes.c_int), nrows, ks, _ptr(pm, ctypes.c_int), jj,
+        float(logit_perturb), int(perturb_seed),
         _ptr(out, ctypes.c_double), _ptr(traj, ctypes.c_double), _ptr(diag, ctypes.c_double))
     if rc != 0:
         raise ValueError("ensf_oracle_analysis rejected its arguments")

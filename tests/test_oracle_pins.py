@@ -362,3 +362,37 @@ def test_mean_rmse_definition():
     mean, rmse = o.mean_rmse(Z, truth)
     np.testing.assert_allclose(mean, Z.mean(axis=0), rtol=1e-14)
     assert rmse == pytest.approx(np.sqrt(np.mean((Z.mean(axis=0) - truth) ** 2)), rel=1e-13)
+
+
+def test_minibatch_with_all_members_is_the_full_analysis():
+    """J = N with any permutation uses every member at every step: the result
+    equals the full-ensemble analysis (summation order aside)."""
+    p = inputs.small_case(seed=8, n=6, grid=8, K=5, obs_op=1, obs_frac=0.5, sigma_obs=0.5)
+    perm = np.random.default_rng(0).permutation(p.n)
+    a = o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed)
+    b = o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed, perm=perm, J=p.n)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_minibatch_uses_only_its_window():
+    """J = 1: each step's prior score is the single-member closed form of the
+    window's member, so the trajectory follows the point-mass recursion with
+    that member; checked against a member-by-member recomputation with N = 1."""
+    g = np.random.default_rng(3)
+    n, d, K = 4, 8, 4
+    X = g.standard_normal((n, d)).astype(np.float32)
+    nb = g.standard_normal((K + 1, n, d)).astype(np.float32)
+    perm = np.array([2, 0, 3, 1])
+    y = np.zeros(d, np.float32)
+    mask = np.zeros(d, np.uint8)
+    full = o.analysis(X, y, mask, 1.0, K, 0.05, noise_buf=nb, perm=perm, J=1, return_traj=True)[1]
+    for i in range(n):
+        z = nb[0, i].astype(np.float64)
+        for k in range(K):
+            xj = X[perm[k % n]].astype(np.float64)
+            s = o.schedule(1.0 - k / K, 0.05)
+            score = -(z - s["alpha"] * xj) / s["beta2"]
+            z = z - (1.0 / K) * (s["b"] * z - s["sigma2"] * score) + np.sqrt(s["sigma2"] / K) * nb[k + 1, i]
+            np.testing.assert_allclose(full[k + 1, i], z, rtol=1e-12, atol=1e-12)
+    with pytest.raises(ValueError):
+        o.analysis(X, y, mask, 1.0, K, 0.05, noise_buf=nb, perm=perm, J=3)
