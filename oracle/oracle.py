@@ -211,3 +211,28 @@ def mean_rmse(Z, truth):
     rmse = _load().ensf_oracle_mean_rmse(_ptr(Z, ctypes.c_double), n, d,
                                          _ptr(truth, ctypes.c_float), _ptr(mean, ctypes.c_double))
     return mean, float(rmse)
+
+
+def model_error(state, coef, seed: int, cycle: int) -> np.ndarray:
+    """Imperfect-model error of the twin experiment (Sec. IV-A): additive
+    Gaussian errors, uncorrelated in space (diagonal covariance) and white in
+    time, made of several stochastic processes, each realised or not in a
+    given forecast interval.  The caller folds each process's realisation
+    (drawn as an input), amplitude and the model's mean value into coef[p];
+    the result is
+
+        state[b][j] + sum_p coef[p] * xi_p[b][j],
+
+    xi_p[b][j] = noise(seed, offset = cycle, k = p, particle b, element j),
+    the standard normal of the same counter-based stream as the analysis
+    noise, in FP64."""
+    x = np.array(state, dtype=np.float64, copy=True)
+    if x.ndim == 1:
+        x = x[None, :]
+    B, d = x.shape
+    for p, c in enumerate(coef):
+        if c != 0.0:
+            for b in range(B):
+                x[b] += float(c) * noise(seed, cycle, p, b, d)
+    return x
+

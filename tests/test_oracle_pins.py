@@ -396,3 +396,28 @@ def test_minibatch_uses_only_its_window():
             np.testing.assert_allclose(full[k + 1, i], z, rtol=1e-12, atol=1e-12)
     with pytest.raises(ValueError):
         o.analysis(X, y, mask, 1.0, K, 0.05, noise_buf=nb, perm=perm, J=3)
+
+
+def test_model_error_statistics():
+    """Sec. IV-A model error: the processes are independent standard normals
+    scaled by coef, uncorrelated in space, across members and across cycles.
+    With two processes on, the error variance is the sum of the squares (a
+    shared stream would give the square of the sum); a zero coefficient
+    adds nothing."""
+    d = 200_000
+    base = np.zeros((2, d))
+    coef = [0.2, 0.0, 0.4, 0.0]
+    e = o.model_error(base, coef, seed=9, cycle=3)
+    var = 0.2 ** 2 + 0.4 ** 2
+    for b in range(2):
+        assert abs(e[b].mean()) < 5 * np.sqrt(var / d)
+        assert abs(e[b].var() / var - 1.0) < 5 * np.sqrt(2.0 / d)
+        assert abs(np.corrcoef(e[b][:-1], e[b][1:])[0, 1]) < 5 / np.sqrt(d)
+    assert abs(np.corrcoef(e[0], e[1])[0, 1]) < 5 / np.sqrt(d)
+    e2 = o.model_error(base, coef, seed=9, cycle=4)
+    assert abs(np.corrcoef(e[0], e2[0])[0, 1]) < 5 / np.sqrt(d)
+    p0 = o.model_error(base[:1], [1.0, 0, 0, 0], seed=9, cycle=3)[0]
+    p2 = o.model_error(base[:1], [0, 0, 1.0, 0], seed=9, cycle=3)[0]
+    assert abs(np.corrcoef(p0, p2)[0, 1]) < 5 / np.sqrt(d)
+    np.testing.assert_allclose(o.model_error(base, [0.0] * 4, seed=9, cycle=3), base)
+    np.testing.assert_allclose(e[0], 0.2 * p0 + 0.4 * p2, rtol=1e-12, atol=1e-12)
