@@ -236,3 +236,25 @@ def model_error(state, coef, seed: int, cycle: int) -> np.ndarray:
                 x[b] += float(c) * noise(seed, cycle, p, b, d)
     return x
 
+
+def relax_spread(prior, z, factor: float, mode: str = "spread") -> np.ndarray:
+    """Relaxation of the analysis ensemble toward the forecast ensemble after
+    each cycled analysis (Sec. IV-A: the analysis spread is relaxed to the
+    prior values), per state variable over the n members, in FP64.
+
+    "spread" (relaxation to prior spread, Whitaker and Hamill 2012): the
+    analysis anomalies z_i - mean(z) are scaled by (1 - a) + a s_f / s_a, s_f and
+    s_a the forecast and analysis standard deviations (factor 1 where s_a = 0).
+    "perturbations" (relaxation to prior perturbations, Zhang et al. 2004):
+    the anomalies become (1 - a)(z_i - mean(z)) + a (x_i - mean(x)).
+    The analysis mean is kept in both."""
+    x = np.asarray(prior, dtype=np.float64)
+    za = np.asarray(z, dtype=np.float64)
+    ma, mf = za.mean(axis=0), x.mean(axis=0)
+    da, df = za - ma, x - mf
+    if mode == "perturbations":
+        return ma + (1.0 - factor) * da + factor * df
+    sa, sf = np.sqrt((da ** 2).mean(axis=0)), np.sqrt((df ** 2).mean(axis=0))
+    ratio = np.divide(sf, sa, out=np.ones_like(sa), where=sa > 0)
+    return ma + da * ((1.0 - factor) + factor * ratio)
+

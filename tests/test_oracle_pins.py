@@ -421,3 +421,31 @@ def test_model_error_statistics():
     assert abs(np.corrcoef(p0, p2)[0, 1]) < 5 / np.sqrt(d)
     np.testing.assert_allclose(o.model_error(base, [0.0] * 4, seed=9, cycle=3), base)
     np.testing.assert_allclose(e[0], 0.2 * p0 + 0.4 * p2, rtol=1e-12, atol=1e-12)
+
+
+def test_relax_spread_properties():
+    """Relaxation to the prior (Sec. IV-A): factor 0 is the identity; RTPS
+    keeps the analysis mean and moves each variable's spread linearly from
+    the analysis to the forecast spread, so factor 1 restores the forecast
+    spread exactly; RTPP with factor 1 restores the forecast anomalies."""
+    g = np.random.default_rng(4)
+    n, d = 12, 300
+    prior = g.standard_normal((n, d)) * g.uniform(0.5, 2.0, d) + 3.0
+    z = g.standard_normal((n, d)) * g.uniform(0.05, 0.3, d) - 1.0
+    sd = lambda a: a.std(axis=0)
+    for mode in ("spread", "perturbations"):
+        np.testing.assert_allclose(o.relax_spread(prior, z, 0.0, mode), z, rtol=1e-13, atol=1e-13)
+        for a in (0.3, 1.0):
+            r = o.relax_spread(prior, z, a, mode)
+            np.testing.assert_allclose(r.mean(axis=0), z.mean(axis=0), rtol=1e-12, atol=1e-12)
+    for a in (0.3, 0.7, 1.0):
+        r = o.relax_spread(prior, z, a, "spread")
+        np.testing.assert_allclose(sd(r), (1 - a) * sd(z) + a * sd(prior), rtol=1e-12)
+        # the shape of each variable's anomalies is the analysis one
+        np.testing.assert_allclose(np.corrcoef(r[:, 7], z[:, 7])[0, 1], 1.0, rtol=1e-12)
+    r = o.relax_spread(prior, z, 1.0, "perturbations")
+    np.testing.assert_allclose(r - r.mean(axis=0), prior - prior.mean(axis=0), rtol=1e-12, atol=1e-12)
+    # a variable with no analysis spread is left alone by RTPS
+    z2 = z.copy()
+    z2[:, 0] = 0.25
+    np.testing.assert_allclose(o.relax_spread(prior, z2, 1.0, "spread")[:, 0], 0.25)
