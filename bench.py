@@ -134,23 +134,26 @@ def make_problem(workload: str, rank: int):
     return fn(seed={"plain-64": 1, "sparse-arctan-128": 2, "large-512": 4, "medium-192": 5}[workload] + 1000 * rank)
 
 
-def cpu_baseline(p, budget_s: float = 15.0):
+def cpu_baseline(p, budget_s: float = 15.0, J: int = 0):
     """The FP64 oracle as it stands on the host cores, on a bounded sample of
     the workload: `rows` particle rows through the first `k_stop` of the K
-    Euler-Maruyama steps (rows are independent, every step costs the same)."""
+    Euler-Maruyama steps (rows are independent, every step costs the same).
+    With J, the oracle's mini-batch form over an identity permutation (the
+    cost of a step does not depend on which members the window holds)."""
     from oracle import oracle as o
+    mb = dict(perm=np.arange(p.n), J=J) if J else {}
     t0 = time.perf_counter()
-    o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed, rows=[0], k_stop=1)
+    o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed, rows=[0], k_stop=1, **mb)
     per = max(time.perf_counter() - t0, 1e-4)
     k_stop = int(max(1, min(p.K, budget_s / per)))
     rows = int(max(1, min(p.n, budget_s / (per * k_stop))))
     t0 = time.perf_counter()
     o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed,
-               rows=list(range(rows)), k_stop=k_stop)
+               rows=list(range(rows)), k_stop=k_stop, **mb)
     dt = time.perf_counter() - t0
     return {"value": rows * k_stop / dt, "unit": UNIT, "cores": o.num_threads(), "kind": "oracle",
             "sample": f"{rows} particle row(s) x {k_stop} of {p.K} Euler-Maruyama steps of {p.name} "
-                      f"(N={p.n}, d={p.d}), {dt:.1f} s"}
+                      f"(N={p.n}, d={p.d}{f', J={J}' if J else ''}), {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -205,10 +208,12 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
     launches, timed, tot_ms = rec
     avg_ms = tot_ms / timed
     n, d = p.n, p.d
+    nx = args.minibatch or n          # members in the prior-score sum of one step
     prec = gram if kernel == "gram" else wx
-    flops = 2.0 * n * n * d
+    flops = 2.0 * n * nx * d
     if kernel == "wx_em" and prec != "fp32":
-        nbytes = (8 + 4 + 2 * (2 if prec == "split" else 1) + (4 if gram != "fp32" else 0)) * n * d + 5 * d
+        nbytes = ((8 + 4 + (4 if gram != "fp32" else 0)) * n * d + 2 * (2 if prec == "split" else 1) * nx * d
+                  + 5 * d)
         peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
         achieved = nbytes / (avg_ms / 1e3) / 1e9
         return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -363,8 +368,32 @@ def run_ours(args):
     small = p.n * p.d * 4 <= 256 << 20
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if small else None
 
+    J = args.minibatch
+    if J:
+        if gram == "fp32":
+            raise SystemExit("--minibatch needs a tensor-core path (split-bf16 or split)")
+        # one seeded member permutation per analysis, drawn on the host and
+        # made resident before any timed region
+        perms = {}
+
+        def perm_for(k_seed):
+            if k_seed not in perms:
+                g = np.random.default_rng([p.seed, 7, k_seed])
+                perms[k_seed] = torch.from_numpy(g.permutation(p.n).astype(np.int32)).to(dev)
+            return perms[k_seed]
+        for k_seed in list(range(args.warmup)) + [100 + s_ for s_ in range(args.steps)] + \
+                [200 + s_ for s_ in range(3)]:
+            perm_for(k_seed)
+
+    def analyse(pr, yy, mm, k_seed):
+        if J:
+            f.analysis_minibatch(pr, yy, mm, p.sigma_obs, p.K, p.eps, perm_for(k_seed), J, p.obs_op,
+                                 seed=p.seed + k_seed, out=out)
+        else:
+            f.analysis(pr, yy, mm, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed + k_seed, out=out)
+
     def one(k_seed):
-        f.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed + k_seed, out=out)
+        analyse(prior, y, mask, k_seed)
 
     for w in range(args.warmup):
         one(w)
@@ -418,13 +447,17 @@ def run_ours(args):
         d_y.copy_(h_y, non_blocking=True)
         if d_mask is not None:
             d_mask.copy_(h_mask, non_blocking=True)
-        f.analysis(d_prior, d_y, d_mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed + 200 + s_, out=out)
+        analyse(d_prior, d_y, d_mask, 200 + s_)
         h_out.copy_(out, non_blocking=True)
         ee[s_][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = float(sum(a.elapsed_time(b) for a, b in ee)) / e2e_steps
     h2d = p.prior.nbytes + p.y.nbytes + (p.mask.nbytes if p.mask is not None else 0)
     d2h = p.n * p.d * 4
+    # accuracy of the last end-to-end analysis (ensemble-mean RMSE against the truth)
+    post = h_out.numpy().astype(np.float64)
+    accuracy = {"analysis_rmse": float(np.sqrt(np.mean((post.mean(axis=0) - p.truth) ** 2))),
+                "prior_rmse": float(np.sqrt(np.mean((p.prior.astype(np.float64).mean(axis=0) - p.truth) ** 2)))}
 
     # ---- max over ranks ----
     t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
@@ -453,13 +486,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"split-bf16": "bf16x3+bf16 (fp32 acc)", "split": "bf16x3 (fp32 acc)",
                                           "fp32": "f32"}[args.path],
-            "data": "synthetic", "config": _config(p, args.path, world), "roofline": roof,
+            "data": "synthetic", "config": dict(_config(p, args.path, world), minibatch_J=J or p.n),
+            "roofline": roof, "accuracy": accuracy,
             "roofline_other": other,
             "kernels": {k: {"launches": v[0], "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches, "clocks": clk.summary(), "tuning": tuning, "cuda_graph": args.graph}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget_s)
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget_s, J or 0)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -478,6 +512,8 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true", help="replay each analysis as one captured CUDA graph")
     ap.add_argument("--inline-noise", action="store_true",
                     help="tensor-core W X evaluates the noise in its epilogue (no pre-generated slice)")
+    ap.add_argument("--minibatch", type=int, default=0, metavar="J",
+                    help="mini-batch prior score over J members per Euler-Maruyama step (tensor-core paths)")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     args = ap.parse_args(argv)

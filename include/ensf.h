@@ -171,6 +171,17 @@ size_t ensf_batch_workspace_bytes(const ensf_config *cfg, const ensf_instance *i
 ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int count, int K, float eps,
                                   void *workspace, size_t ws_bytes, void *stream);
 
+/* The analysis with the mini-batch prior score of Eq. 15-16 (J < N members
+ * per evaluation): `perm` (device int32 [n]) is a permutation of the forecast
+ * members, drawn by the caller; Euler-Maruyama step k uses the J members
+ * perm[w J .. w J + J - 1], w = k mod (n / J), for every particle, with the
+ * weights normalised over those J.  The Gram and W X cost drop by n / J.
+ * J must divide n and be a multiple of 8 (or equal n).  Tensor-core
+ * precisions only; other arguments as ensf_analysis. */
+ensf_status ensf_analysis_minibatch(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                                    const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
+                                    const ensf_noise *noise, const int *perm, int J, float *out, void *stream);
+
 /* Normalised weights w_ij of Eq. 16 for given particles z [n][d] at pseudo-
  * time t, against the forecast ensemble prior [n_x][d], written to
  * w [n][n_x] FP32.  Uses the handle's Gram precision; this is the Gram +
@@ -220,6 +231,20 @@ ensf_status ensf_ensemble_stats(const float *z, int n, int64_t d, const float *t
  * factor in [0, 1]; 1 restores the forecast spread (mode 0) or perturbations (mode 1). */
 ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, float factor, int mode,
                               void *stream);
+
+/* Imperfect-model error of the twin experiment (Sec. IV-A: additive
+ * Gaussian model errors, uncorrelated in space and white in time, made of
+ * several stochastic processes each realised with its own probability and
+ * amplitude), in place on state [batch][d] (device FP32):
+ *   state[b][j] += sum_{p < nproc} coef[p] * xi_p[b][j],
+ * xi_p[b][j] the standard normal of the analysis noise stream (Philox4x32-10
+ * + Box-Muller) at (seed, offset = cycle, step index p, particle b, element j).
+ * coef: host array of nproc (1..8) floats; the caller folds each process's
+ * realisation in this interval (0 or 1), its amplitude and the model's mean
+ * value into coef[p].  Errors: EINVAL for NULL pointers, batch < 1, d < 1 or
+ * nproc outside 1..8; ECUDA if the launch fails. */
+ensf_status ensf_model_error(float *state, int batch, int64_t d, const float *coef, int nproc, uint64_t seed,
+                             uint32_t cycle, void *stream);
 
 /* Launch accounting of a handle.  Every kernel launch is counted by kind
  * ("row_norms", "init_particles", "split_bf16", "gram", "softmax_rows",

@@ -212,9 +212,10 @@ struct NoiseRequest {
     int k = 0;
 };
 
+// x0: first member row (in the split planes and norms) of a mini-batch window.
 ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *prior, int n_x, int64_t d,
                          const ensf::StepCoef &c, bool want_fp32, cudaStream_t s,
-                         const NoiseRequest &nr = NoiseRequest()) {
+                         const NoiseRequest &nr = NoiseRequest(), int x0 = 0) {
     const Layout &L = h->L;
     float *partial = h->at<float>(L.partial);
     int splits = 0;
@@ -230,8 +231,8 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
         ensf::TcGramArgs a;
         a.zb_hi = h->at<__nv_bfloat16>(L.zb_hi);
         a.zb_lo = L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
-        a.xb_hi = h->at<__nv_bfloat16>(L.xb_hi);
-        a.xb_lo = L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr;
+        a.xb_hi = h->at<__nv_bfloat16>(L.xb_hi) + (size_t)x0 * d;
+        a.xb_lo = L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) + (size_t)x0 * d : nullptr;
         a.n = n;
         a.n_x = n_x;
         a.d = d;
@@ -253,7 +254,7 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
         ldwb = (int)round_up(n_x, 8);
     }
     ENSF_LAUNCH(h, P_SOFTMAX, s,
-                ensf::launch_softmax_rows(partial, splits, part_stride, ldp, n, n_x, h->at<double>(L.norms),
+                ensf::launch_softmax_rows(partial, splits, part_stride, ldp, n, n_x, h->at<double>(L.norms) + x0,
                                           c.alpha_d, c.inv_2beta2_d, want_fp32 ? h->at<float>(L.w) : nullptr,
                                           n_x, wb_hi, wb_lo, ldwb, s));
     return ENSF_OK;
@@ -368,18 +369,20 @@ ensf_status analysis_validate(ensf_handle *h, const float *prior, int n, int64_t
 
 // Everything of one analysis before its first Euler-Maruyama step: centre and
 // norms of the forecast ensemble, the initial particles, the BF16 planes.
+// perm (device, optional): the split planes and norms hold the members in this order.
 ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, int K, float eps, float sigma_obs,
-                          int obs_op, const ensf_noise *noise, float *out, cudaStream_t s) {
+                          int obs_op, const ensf_noise *noise, float *out, cudaStream_t s,
+                          const int *perm = nullptr) {
     const Layout &L = h->L;
     const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
     float *xbar = h->at<float>(L.xbar);
     ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_col_mean(prior, n, d, xbar, s));
-    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, h->at<double>(L.norms), s, xbar));
+    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, h->at<double>(L.norms), s, xbar, perm));
     ENSF_LAUNCH(h, P_INIT, s, ensf::launch_init_particles(out, n, d, noise->buf, noise->seed, noise->offset, s));
     if (tc_gram) {
         ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(prior, n, d, h->at<__nv_bfloat16>(L.xb_hi),
                                                            L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s,
-                                                           xbar, 1.0f));
+                                                           xbar, 1.0f, perm));
         ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, h->at<__nv_bfloat16>(L.zb_hi),
                                                            L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s,
                                                            xbar, step_coef(0, K, eps, sigma_obs, obs_op).alpha));
@@ -388,21 +391,24 @@ ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, 
         ENSF_LAUNCH(h, P_SPLIT, s,
                     ensf::launch_split_bf16_transpose(prior, n, d, h->at<__nv_bfloat16>(L.xt_hi),
                                                       L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) : nullptr,
-                                                      (int)round_up(n, 8), s));
+                                                      (int)round_up(n, 8), s, perm));
     return ENSF_OK;
 }
 
 // Arguments of the tensor-core W X of step k (the noise slice is the handle's
 // pre-generated one unless the caller supplied a buffer).
 ensf::TcWxArgs wx_args(ensf_handle *h, int n, int64_t d, const float *y, const uint8_t *obs_mask,
-                       const ensf_noise *noise, float *out, const ensf::StepCoef &c, float alpha_next, int k) {
+                       const ensf_noise *noise, float *out, const ensf::StepCoef &c, float alpha_next, int k,
+                       int x0 = 0, int J = 0) {
     const Layout &L = h->L;
     ensf::TcWxArgs a;
     a.wb_hi = h->at<__nv_bfloat16>(L.wb_hi);
     a.wb_lo = L.wb_lo ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
-    a.xt_hi = h->at<__nv_bfloat16>(L.xt_hi);
-    a.xt_lo = L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) : nullptr;
+    a.xt_hi = h->at<__nv_bfloat16>(L.xt_hi) + x0;
+    a.xt_lo = L.xt_lo ? h->at<__nv_bfloat16>(L.xt_lo) + x0 : nullptr;
     a.ldw = (int)round_up(n, 8);
+    a.n_x = J > 0 ? J : n;
+    a.ldwb = (int)round_up(a.n_x, 8);
     a.n = n;
     a.d = d;
     a.z = out;
@@ -423,16 +429,18 @@ ensf::TcWxArgs wx_args(ensf_handle *h, int n, int64_t d, const float *y, const u
 
 ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
                              const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
-                             const ensf_noise *noise, float *out, cudaStream_t s) {
+                             const ensf_noise *noise, float *out, cudaStream_t s, const int *perm = nullptr,
+                             int J = 0) {
     const Layout &L = h->L;
     const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
 
     // The Gram runs on centred operands z - alpha m and x_j - m, m = the forecast
     // mean: |z - alpha x_j|^2 is unchanged, the magnitudes entering the expanded
     // logit (and so its rounding error) shrink.
-    ensf_status st0 = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s);
+    ensf_status st0 = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s, perm);
     if (st0 != ENSF_OK) return st0;
     float *xbar = h->at<float>(L.xbar);
+    const int nm = (perm && J > 0) ? J : n;  // members per step (mini-batch window)
     __nv_bfloat16 *zb_hi = tc_gram ? h->at<__nv_bfloat16>(L.zb_hi) : nullptr;
     __nv_bfloat16 *zb_lo = (tc_gram && L.zb_lo) ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
     // The tensor-core W X reads the step's noise as a pre-generated [n][d]
@@ -452,7 +460,8 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
             ENSF_LAUNCH(h, P_NOISE, s,
                         ensf::launch_noise_slice(noise->seed, noise->offset, k + 1, n, d, nslice, 1 << 30, s));
         }
-        ensf_status st = gram_softmax(h, out, n, prior, n, d, c, !tc_wx, s, nr);
+        const int x0 = (nm < n) ? (k % (n / nm)) * nm : 0;
+        ensf_status st = gram_softmax(h, out, n, prior, nm, d, c, !tc_wx, s, nr, x0);
         if (st != ENSF_OK) return st;
         if (!tc_wx) {
             ENSF_LAUNCH(h, P_WXEM, s,
@@ -463,7 +472,7 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
                                                                    step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha));
         } else {
             ensf::TcWxArgs a = wx_args(h, n, d, y, obs_mask, noise, out, c,
-                                       step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha, k);
+                                       step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha, k, x0, nm);
             ENSF_LAUNCH(h, P_WXEM, s, ensf::launch_wx_em_tc(h->tc, a, h->sms, s));
         }
     }
@@ -515,6 +524,21 @@ ensf_status ensf_analysis(ensf_handle *h, const float *prior, int n, int64_t d, 
     }
     ENSF_CUDA(cudaGraphLaunch(h->graph_exec, s));
     return ENSF_OK;
+}
+
+ensf_status ensf_analysis_minibatch(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                                    const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
+                                    const ensf_noise *noise, const int *perm, int J, float *out, void *stream) {
+    ensf_status st = analysis_validate(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, K, eps, noise, out);
+    if (st != ENSF_OK) return st;
+    if (!is_tc(h->cfg.gram) || !is_tc(h->cfg.wx))
+        return fail(ENSF_EUNSUPPORTED, "ensf_analysis_minibatch: needs tensor-core precisions");
+    if (!perm || (reinterpret_cast<uintptr_t>(perm) & 3u))
+        return fail(ENSF_EINVAL, "ensf_analysis_minibatch: perm must be a device int32 array");
+    if (J < 1 || J > n || n % J != 0 || (J != n && J % 8 != 0))
+        return fail(ENSF_EINVAL, "ensf_analysis_minibatch: J must divide n and be a multiple of 8 (or equal n)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return analysis_enqueue(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, K, eps, noise, out, s, perm, J);
 }
 
 ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
@@ -656,6 +680,14 @@ ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, fl
     if (!prior || !z || n < 2 || d < 1 || !(factor >= 0.0f && factor <= 1.0f) || (mode != 0 && mode != 1))
         return fail(ENSF_EINVAL, "ensf_relax_spread: bad arguments");
     ENSF_CUDA(ensf::launch_relax_spread(prior, z, n, d, factor, mode, static_cast<cudaStream_t>(stream)));
+    return ENSF_OK;
+}
+
+ensf_status ensf_model_error(float *state, int batch, int64_t d, const float *coef, int nproc, uint64_t seed,
+                             uint32_t cycle, void *stream) {
+    if (!state || !coef || batch < 1 || d < 1 || nproc < 1 || nproc > 8 || batch > 4 * 65535)
+        return fail(ENSF_EINVAL, "ensf_model_error: bad arguments");
+    ENSF_CUDA(ensf::launch_model_error(state, batch, d, coef, nproc, seed, cycle, static_cast<cudaStream_t>(stream)));
     return ENSF_OK;
 }
 

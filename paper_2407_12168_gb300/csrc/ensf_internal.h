@@ -20,8 +20,9 @@ cudaError_t launch_philox_normal(uint64_t seed, uint32_t offset, int k0, int cou
 cudaError_t launch_noise_slice(uint64_t seed, uint32_t offset, int k, int n, int64_t d, float *out,
                                int max_blocks, cudaStream_t s);
 // out[j] = |x_j - centre|^2 in FP64 (centre may be NULL)
+// (rows: optional row map, row r of the result reads row rows[r] of x)
 cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s,
-                             const float *centre = nullptr);
+                             const float *centre = nullptr, const int *rows = nullptr);
 // m[c] = mean over the n rows of x[.][c]
 cudaError_t launch_col_mean(const float *x, int n, int64_t d, float *m, cudaStream_t s);
 // partial[s][i][j] = sum over slice s of (z[i][c] - alpha m[c]) (x[j][c] - m[c])
@@ -44,16 +45,18 @@ cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, in
 // row-major copy with output row stride ldo
 cudaError_t launch_split_bf16(const float *x, int rows, int64_t cols, __nv_bfloat16 *hi,
                               __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s,
-                              const float *centre = nullptr, float scale = 0.0f);
+                              const float *centre = nullptr, float scale = 0.0f, const int *rowmap = nullptr);
 // Transposed split: xT_hi[c][j] = bf16(x[j][c]), xT_lo likewise (ldo = row stride of xT)
 cudaError_t launch_split_bf16_transpose(const float *x, int rows, int64_t cols,
                                         __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ldo,
-                                        cudaStream_t s);
+                                        cudaStream_t s, const int *rowmap = nullptr);
 cudaError_t launch_check_finite(const float *z, int64_t count, int *err_word, cudaStream_t s);
 cudaError_t launch_ensemble_stats(const float *z, int n, int64_t d, const float *truth,
                                   double *mean, double *rmse, double *scratch, cudaStream_t s);
 int stats_blocks(int64_t d);
 
+cudaError_t launch_model_error(float *state, int batch, int64_t d, const float *coef, int nproc, uint64_t seed,
+                               uint32_t cycle, cudaStream_t s);
 cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, int mode, cudaStream_t s);
 
 // Host-side message returned by ensf_last_error() on this thread.

@@ -23,8 +23,9 @@ __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast
 // float4 loads, the difference rounded to FP32 as the Gram operands are,
 // fixed-order tree reduce.
 __global__ void __launch_bounds__(256) k_row_norms(const float *__restrict__ x, int64_t d,
-                                                   const float *__restrict__ centre, double *__restrict__ out) {
-    const float *row = x + (int64_t)blockIdx.x * d;
+                                                   const float *__restrict__ centre, const int *__restrict__ rows,
+                                                   double *__restrict__ out) {
+    const float *row = x + (int64_t)(rows ? rows[blockIdx.x] : blockIdx.x) * d;
     double acc = 0.0;
     for (int64_t c = (int64_t)threadIdx.x * 4; c < d; c += 256 * 4) {
         float4 v = ld4(row + c);
@@ -265,11 +266,11 @@ k_wx_em_fp32(const float *__restrict__ w, int ldw, const float *__restrict__ x, 
 // x = hi + lo with hi = bf16(x), lo = bf16(x - hi); row-major, out stride ldo.
 __global__ void k_split_bf16(const float *__restrict__ x, int64_t cols, __nv_bfloat16 *__restrict__ hi,
                              __nv_bfloat16 *__restrict__ lo, int64_t ldo, const float *__restrict__ centre,
-                             float scale) {
+                             float scale, const int *__restrict__ rows) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     if (q * 4 >= cols) return;
-    float4 v = ld4(x + (int64_t)r * cols + q * 4);
+    float4 v = ld4(x + (int64_t)(rows ? rows[r] : r) * cols + q * 4);
     if (centre) {  // split x - scale * m
         const float4 m = ld4(centre + q * 4);
         v.x -= scale * m.x; v.y -= scale * m.y; v.z -= scale * m.z; v.w -= scale * m.w;
@@ -288,7 +289,7 @@ __global__ void k_split_bf16(const float *__restrict__ x, int64_t cols, __nv_bfl
 // Transposed split through a 32x32 shared tile: xT[c][j] from x[j][c].
 __global__ void k_split_bf16_t(const float *__restrict__ x, int rows, int64_t cols,
                                __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
-                               int64_t ldo) {
+                               int64_t ldo, const int *__restrict__ rowmap) {
     __shared__ float tile[32][33];
     const int64_t c0 = (int64_t)blockIdx.x * 32;
     const int j0 = blockIdx.y * 32;
@@ -296,7 +297,7 @@ __global__ void k_split_bf16_t(const float *__restrict__ x, int rows, int64_t co
     for (int r = ty; r < 32; r += 8) {
         int j = j0 + r;
         int64_t c = c0 + tx;
-        tile[r][tx] = (j < rows && c < cols) ? x[(int64_t)j * cols + c] : 0.f;
+        tile[r][tx] = (j < rows && c < cols) ? x[(int64_t)(rowmap ? rowmap[j] : j) * cols + c] : 0.f;
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
@@ -391,6 +392,47 @@ __global__ void k_relax_spread(const float *__restrict__ prior, float *__restric
 
 }  // namespace
 
+// Model error of the twin experiment: one thread per (particle quad, column),
+// the four particles of a quad share one Philox block per process (the same
+// counter layout as the analysis noise), grid-stride over the columns.
+struct ModelErrorCoef {
+    float c[8];
+    int n;
+};
+
+__global__ void __launch_bounds__(256) k_model_error(float *__restrict__ state, int batch, int64_t d,
+                                                     ModelErrorCoef coef, uint64_t seed, uint32_t cycle) {
+    const int qd = blockIdx.y;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int p = 0; p < coef.n; ++p) {
+            if (coef.c[p] == 0.0f) continue;
+            const float4 v = noise4(seed, cycle, p, c, qd);
+            acc[0] += coef.c[p] * v.x;
+            acc[1] += coef.c[p] * v.y;
+            acc[2] += coef.c[p] * v.z;
+            acc[3] += coef.c[p] * v.w;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int b = qd * 4 + r;
+            if (b < batch) state[(int64_t)b * d + c] += acc[r];
+        }
+    }
+}
+
+cudaError_t launch_model_error(float *state, int batch, int64_t d, const float *coef, int nproc, uint64_t seed,
+                               uint32_t cycle, cudaStream_t s) {
+    ModelErrorCoef mc{};
+    mc.n = nproc;
+    for (int p = 0; p < nproc; ++p) mc.c[p] = coef[p];
+    int64_t bx = (d + 255) / 256;
+    if (bx > 152 * 8) bx = 152 * 8;
+    dim3 grid((unsigned)bx, (unsigned)((batch + 3) / 4));
+    k_model_error<<<grid, 256, 0, s>>>(state, batch, d, mc, seed, cycle);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, int mode, cudaStream_t s) {
     k_relax_spread<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(prior, z, n, d, a, mode);
     return cudaGetLastError();
@@ -420,8 +462,9 @@ cudaError_t launch_noise_slice(uint64_t seed, uint32_t offset, int k, int n, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s, const float *centre) {
-    k_row_norms<<<n, 256, 0, s>>>(x, d, centre, out);
+cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s, const float *centre,
+                             const int *rows) {
+    k_row_norms<<<n, 256, 0, s>>>(x, d, centre, rows, out);
     return cudaGetLastError();
 }
 
@@ -457,16 +500,17 @@ cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, in
 }
 
 cudaError_t launch_split_bf16(const float *x, int rows, int64_t cols, __nv_bfloat16 *hi,
-                              __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s, const float *centre, float scale) {
+                              __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s, const float *centre, float scale,
+                              const int *rowmap) {
     dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)rows);
-    k_split_bf16<<<grid, 256, 0, s>>>(x, cols, hi, lo, ldo, centre, scale);
+    k_split_bf16<<<grid, 256, 0, s>>>(x, cols, hi, lo, ldo, centre, scale, rowmap);
     return cudaGetLastError();
 }
 
 cudaError_t launch_split_bf16_transpose(const float *x, int rows, int64_t cols, __nv_bfloat16 *hi,
-                                        __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s) {
+                                        __nv_bfloat16 *lo, int64_t ldo, cudaStream_t s, const int *rowmap) {
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-    k_split_bf16_t<<<grid, dim3(32, 8), 0, s>>>(x, rows, cols, hi, lo, ldo);
+    k_split_bf16_t<<<grid, dim3(32, 8), 0, s>>>(x, rows, cols, hi, lo, ldo, rowmap);
     return cudaGetLastError();
 }
 

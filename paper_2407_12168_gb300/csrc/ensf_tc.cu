@@ -1035,14 +1035,15 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
         if (it != ctx->wx_tuned.end()) BN = it->second;
     }
     if (BN != 64 && BN != 128 && BN != 256) return cudaErrorInvalidValue;
-    // A = X^T [d][ldw] (state columns; K = n_x members), B = W [n][ldw] (particles)
-    const int n_x = a.n;
+    // A = X^T [d][ldw] (state columns; K = n_x members), B = W [n][ldwb] (particles)
+    const int n_x = a.n_x > 0 ? a.n_x : a.n;
+    const int ldwb = a.ldwb > 0 ? a.ldwb : a.ldw;
     CUtensorMap maps[4];
     cudaError_t e;
     if ((e = make_map(ctx, &maps[0], a.xt_hi, n_x, a.d, a.ldw, BM)) != cudaSuccess) return e;
     if ((e = make_map(ctx, &maps[1], split ? a.xt_lo : nullptr, n_x, a.d, a.ldw, BM)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[2], a.wb_hi, n_x, a.n, a.ldw, BN)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[3], split ? a.wb_lo : nullptr, n_x, a.n, a.ldw, BN)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[2], a.wb_hi, n_x, a.n, ldwb, BN)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[3], split ? a.wb_lo : nullptr, n_x, a.n, ldwb, BN)) != cudaSuccess) return e;
     WxParams p;
     p.n = a.n;
     p.d = a.d;

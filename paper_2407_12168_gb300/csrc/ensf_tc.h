@@ -51,8 +51,10 @@ struct TcGramArgs {
 struct TcWxArgs {
     const __nv_bfloat16 *wb_hi, *wb_lo;  // weights   [n][ldw]  (lo NULL for plain BF16)
     const __nv_bfloat16 *xt_hi, *xt_lo;  // forecast transposed [d][ldw]
-    int ldw;                             // row pitch (elements) of W and X^T, >= n, multiple of 8
+    int ldw;                             // row pitch (elements) of X^T, >= n_x, multiple of 8
+    int ldwb;                            // row pitch of W (0: same as ldw)
     int n;
+    int n_x;                             // members in the contraction (0: n)
     int64_t d;
     float *z;                            // particles [n][d], updated in place
     __nv_bfloat16 *zb_hi, *zb_lo;        // split copies of the updated particles (NULL: skip)

@@ -77,6 +77,10 @@ _SIGNATURES = [
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
                                      ctypes.c_int, ctypes.c_float, ctypes.POINTER(EnsfNoise),
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_analysis_minibatch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
+                                               ctypes.c_int, ctypes.c_float, ctypes.POINTER(EnsfNoise),
+                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
                                      ctypes.c_float, ctypes.POINTER(EnsfNoise), ctypes.c_void_p,
@@ -98,6 +102,8 @@ _SIGNATURES = [
                                       ctypes.c_void_p]),
     ("ensf_relax_spread", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                                          ctypes.c_float, ctypes.c_int, ctypes.c_void_p]),
+    ("ensf_model_error", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
     ("ensf_stats_scratch_bytes", ctypes.c_size_t, [ctypes.c_int64]),
     ("ensf_ensemble_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -240,6 +246,24 @@ class Filter:
                                   float(sigma_obs), int(K), float(eps), ctypes.byref(nz), out.data_ptr(),
                                   _stream_ptr(stream))
         _check(st, "ensf_analysis")
+        return out
+
+    def analysis_minibatch(self, prior, y, mask, sigma_obs: float, K: int, eps: float, perm, J: int,
+                           obs_op: int = OBS_IDENTITY, seed: int = 0, offset: int = 0, out=None, stream=None):
+        """Analysis with the mini-batch prior score over windows of J members of
+        ``perm`` (device int32 permutation of the members)."""
+        torch = _torch()
+        _dev(prior, torch.float32, "prior")
+        _dev(perm, torch.int32, "perm")
+        n, d = prior.shape
+        if out is None:
+            out = torch.empty_like(prior)
+        nz = EnsfNoise(None, int(seed) & (2 ** 64 - 1), int(offset) & 0xFFFFFFFF)
+        _check(load().ensf_analysis_minibatch(self._h, prior.data_ptr(), n, d, y.data_ptr(),
+                                              mask.data_ptr() if mask is not None else None, int(obs_op),
+                                              float(sigma_obs), int(K), float(eps), ctypes.byref(nz),
+                                              perm.data_ptr(), int(J), out.data_ptr(), _stream_ptr(stream)),
+               "ensf_analysis_minibatch")
         return out
 
     def autotune(self, prior, y, mask, sigma_obs: float, eps: float, obs_op: int = OBS_IDENTITY, seed: int = 0,
@@ -469,6 +493,18 @@ def relax_spread(prior, z, factor: float = 1.0, mode: str = "spread", stream=Non
                                     {"spread": 0, "perturbations": 1}[mode], _stream_ptr(stream)),
            "ensf_relax_spread")
     return z
+
+
+def model_error(state, coef, seed: int, cycle: int, stream=None):
+    """Add the imperfect-model error sum_p coef[p] xi_p to ``state`` [B][d]
+    (or [d]) in place; xi_p the counter-based normals at (seed, cycle, p)."""
+    torch = _torch()
+    _dev(state, torch.float32, "state")
+    B, d = (1, state.shape[0]) if state.dim() == 1 else (state.shape[0], state[0].numel())
+    c = (ctypes.c_float * len(coef))(*[float(v) for v in coef])
+    _check(load().ensf_model_error(state.data_ptr(), B, d, c, len(coef), int(seed) & (2 ** 64 - 1),
+                                   int(cycle) & 0xFFFFFFFF, _stream_ptr(stream)), "ensf_model_error")
+    return state
 
 
 def ensemble_stats(z, truth: Optional[object] = None, stream=None):

@@ -43,22 +43,22 @@ def eps_path(prec: str, d: int) -> float:
     return 2.0 * 2.0 ** -9 / np.sqrt(d)
 
 
-def run_oracle(p, rows=None, noise_buf=None, logit_perturb=0.0, perturb_seed=0):
+def run_oracle(p, rows=None, noise_buf=None, logit_perturb=0.0, perturb_seed=0, perm=None, J=None):
     return o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, noise_buf=noise_buf,
                       seed=p.seed, offset=p.offset, rows=rows, logit_perturb=logit_perturb,
-                      perturb_seed=perturb_seed)
+                      perturb_seed=perturb_seed, perm=perm, J=J)
 
 
 def _rel(a, b):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
 
 
-def conditioning(p, ref, rows=None, noise_buf=None, prec="fp32"):
+def conditioning(p, ref, rows=None, noise_buf=None, prec="fp32", perm=None, J=None):
     """Largest relative change of each oracle member under log-kernel
     perturbations of the size the GPU path's Gram leaves (two sign patterns)."""
     eps = eps_path(prec, p.d)
     return np.maximum.reduce([_rel(run_oracle(p, rows=rows, noise_buf=noise_buf, logit_perturb=eps,
-                                              perturb_seed=s), ref) for s in (1, 2)])
+                                              perturb_seed=s, perm=perm, J=J), ref) for s in (1, 2)])
 
 
 def compare_members(gpu: np.ndarray, ref: np.ndarray, cond: np.ndarray, tol: float):
