@@ -48,6 +48,16 @@ def _dist_env():
         int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings (every rank gets the result);
+    with no process group the values come back unchanged."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -302,13 +312,10 @@ def run_batched(args):
             a = prof.get(k, (0, 0, 0.0))
             prof[k] = (a[0] + v[0], a[1] + v[1], a[2] + v[2])
         f.profile_enable(False)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        if rank != 0:
-            dist.destroy_process_group()
-            return 0
-    ms = float(t[0])
+    ms, = max_over_ranks([ms], dist, dev)
+    if dist and rank != 0:
+        dist.destroy_process_group()
+        return 0
     member_steps = sum(p.n for p in probs) * K
     flops = sum(2.0 * p.n * p.n * p.d for p in probs)
     kern = {k: {"launches": v[0] // args.steps, "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()}
@@ -460,10 +467,7 @@ def run_ours(args):
                 "prior_rmse": float(np.sqrt(np.mean((p.prior.astype(np.float64).mean(axis=0) - p.truth) ** 2)))}
 
     # ---- max over ranks ----
-    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, dev)
     if rank != 0:
         dist.destroy_process_group()
         return 0
