@@ -128,6 +128,7 @@ typedef struct {
     float gram_ms;     /* measured time of one Gram launch with that shape            */
     int wx_tile_n;     /* W X tile width (particles per tile)                         */
     float wx_ms;       /* measured time of one W X launch with that shape            */
+    int gram_k_block;  /* Gram k-block width in elements (64 or 32)                   */
 } ensf_tuning;
 
 /* Autotuner for the tensor-core stages: times the candidate launch shapes of
@@ -140,6 +141,17 @@ typedef struct {
 ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
                           const uint8_t *obs_mask, int obs_op, float sigma_obs, float eps,
                           const ensf_noise *noise, float *out, ensf_tuning *report, void *stream);
+
+/* Records launch shapes for analyses of this (n, d) without timing them,
+ * e.g. a report saved from ensf_autotune in another process.  Uses the
+ * gram_tile_n, gram_stages, gram_splits (0: the cost model), gram_k_block and
+ * wx_tile_n (0: unchanged) fields of `t`.  Valid Gram shapes (tile width,
+ * ring depth, k-block) for the split-BF16x3 Gram: (128, 3, 64), (256, 2, 64),
+ * (128, 6, 32), (256, 4, 32), (256, 3, 32); for the BF16 Gram: (128, 6, 64),
+ * (256, 4, 64), (128, 12, 32), (256, 8, 32).  EINVAL for any other shape, for
+ * n or d outside the handle's limits, or for a handle whose Gram runs on
+ * CUDA cores. */
+ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning *t);
 
 /* One filter of a batched analysis. */
 typedef struct {

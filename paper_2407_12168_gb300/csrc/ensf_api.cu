@@ -622,7 +622,25 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         report->gram_ms = r.gram_ms;
         report->wx_tile_n = r.wx_bn;
         report->wx_ms = r.wx_ms;
+        report->gram_k_block = r.gram_bk;
     }
+    return ENSF_OK;
+}
+
+ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning *t) {
+    if (!h || !t) return fail(ENSF_EINVAL, "ensf_set_tuning: NULL argument");
+    if (n < 1 || n > h->cfg.max_n || d < 8 || d > h->cfg.max_d || d % 8 != 0)
+        return fail(ENSF_EINVAL, "ensf_set_tuning: n or d outside the handle's limits");
+    if (!is_tc(h->cfg.gram)) return fail(ENSF_EINVAL, "ensf_set_tuning: the Gram of this handle runs on CUDA cores");
+    ensf::GramChoice g;
+    g.bn = t->gram_tile_n;
+    g.stages = t->gram_stages;
+    g.splits = t->gram_splits;
+    g.bk = t->gram_k_block;
+    const bool split3 = h->cfg.gram == ENSF_PREC_SPLIT_BF16X3;
+    const bool wx_split = h->cfg.wx == ENSF_PREC_SPLIT_BF16X3;
+    if (ensf::tc_set_tuning(h->tc, n, n, d, split3, g, is_tc(h->cfg.wx) ? t->wx_tile_n : 0, wx_split) != cudaSuccess)
+        return fail(ENSF_EINVAL, "ensf_set_tuning: no kernel for that launch shape");
     return ENSF_OK;
 }
 

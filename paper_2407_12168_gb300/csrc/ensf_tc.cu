@@ -133,6 +133,25 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
+// The same for tiles written with the 64-byte swizzle (32-element k-blocks):
+// rows of 64 bytes, 8-row groups 512 bytes apart, layout 4.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>(1) << 16;
+    d |= static_cast<uint64_t>(512 >> 4) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    d |= static_cast<uint64_t>(4) << 61;
+    return d;
+}
+
+// Descriptor of a K-major tile whose k-block is KB elements wide.
+template <int KB>
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
+    static_assert(KB == 64 || KB == 32, "k-block width");
+    return KB == 64 ? desc_sw128(saddr) : desc_sw64(saddr);
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulator, A and B BF16, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
@@ -188,10 +207,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // ----------------------------------------------------- shared-memory plan
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, int KB = BK>
 struct Plan {
-    static constexpr int kA = BM * BK * 2;  // one A plane of a stage
-    static constexpr int kB = BN * BK * 2;  // one B plane
+    static constexpr int kA = BM * KB * 2;  // one A plane of a stage
+    static constexpr int kB = BN * KB * 2;  // one B plane
     static constexpr int kPlanes = SPLIT ? 2 : 1;
     static constexpr int kStage = (kA + kB) * kPlanes;
     static constexpr int kBarOff = kStage * STAGES;
@@ -243,11 +262,12 @@ __device__ __forceinline__ uint32_t setup(const Ctl &c, int warp) {
     return *c.tmem_slot;
 }
 
-// Producer (one thread): k-blocks kb0 .. kb0+nkb-1 of A rows m0.. and B rows n0..
-template <int BN, int STAGES, bool SPLIT>
+// Producer (one thread): k-blocks kb0 .. kb0+nkb-1 (KB elements wide) of A
+// rows m0.. and B rows n0..
+template <int BN, int STAGES, bool SPLIT, int KB = BK>
 __device__ void produce(const Ctl &c, const CUtensorMap *a_hi, const CUtensorMap *a_lo, const CUtensorMap *b_hi,
                         const CUtensorMap *b_lo, int m0, int n0, int kb0, int nkb, int *err) {
-    using P = Plan<BN, STAGES, SPLIT>;
+    using P = Plan<BN, STAGES, SPLIT, KB>;
     int issued = 0;
     for (int i = 0; i < nkb; ++i) {
         const int s = i % STAGES;
@@ -255,7 +275,7 @@ __device__ void produce(const Ctl &c, const CUtensorMap *a_hi, const CUtensorMap
         if (!mbar_wait(&c.empty[s], ph ^ 1u, c.abort_flag, err)) break;
         const uint32_t st = smem_u32(c.tiles + s * P::kStage);
         mbar_expect_tx(&c.full[s], P::kStage);
-        const int kx = (kb0 + i) * BK;
+        const int kx = (kb0 + i) * KB;
         tma_load_2d(st, a_hi, &c.full[s], kx, m0);
         if (SPLIT) tma_load_2d(st + P::kA, a_lo, &c.full[s], kx, m0);
         tma_load_2d(st + P::kA * P::kPlanes, b_hi, &c.full[s], kx, n0);
@@ -275,9 +295,9 @@ __device__ void produce(const Ctl &c, const CUtensorMap *a_hi, const CUtensorMap
 }
 
 // MMA issuer (one thread): accumulate the tile in TMEM, then signal accum.
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, int KB = BK>
 __device__ void mma_loop(const Ctl &c, uint32_t tmem, int nkb, int *err) {
-    using P = Plan<BN, STAGES, SPLIT>;
+    using P = Plan<BN, STAGES, SPLIT, KB>;
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
     for (int i = 0; i < nkb; ++i) {
         const int s = i % STAGES;
@@ -289,12 +309,13 @@ __device__ void mma_loop(const Ctl &c, uint32_t tmem, int nkb, int *err) {
         const uint32_t b_hi = a_hi + P::kA * P::kPlanes;
         const uint32_t b_lo = b_hi + P::kB;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
+        for (int kk = 0; kk < KB / 16; ++kk) {
             const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes along the swizzled row
-            mma_bf16(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(tmem, desc_kmajor<KB>(a_hi + off), desc_kmajor<KB>(b_hi + off), idesc,
+                     (i > 0 || kk > 0) ? 1u : 0u);
             if (SPLIT) {
-                mma_bf16(tmem, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
-                mma_bf16(tmem, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+                mma_bf16(tmem, desc_kmajor<KB>(a_hi + off), desc_kmajor<KB>(b_lo + off), idesc, 1u);
+                mma_bf16(tmem, desc_kmajor<KB>(a_lo + off), desc_kmajor<KB>(b_hi + off), idesc, 1u);
             }
         }
         mma_commit(&c.empty[s]);
@@ -315,7 +336,7 @@ __device__ __forceinline__ void teardown(uint32_t tmem, int warp) {
 // ------------------------------------------------------------------- Gram
 struct GramParams {
     int n, n_x;
-    int kblocks;       // ceil(d / BK)
+    int kblocks;       // ceil(d / k-block width)
     int kb_per_split;  // k-blocks per split (last split may hold fewer)
     float *partial;    // [splits][n][n_x]
     int *err;
@@ -359,11 +380,11 @@ __device__ __forceinline__ void gram_noise_share(const GramParams &p) {
     }
 }
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, int KB>
 __global__ void __launch_bounds__(kGramThreads, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
           const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
-    using P = Plan<BN, STAGES, SPLIT>;
+    using P = Plan<BN, STAGES, SPLIT, KB>;
     extern __shared__ uint8_t smem_raw[];
     const Ctl c = carve<P>(smem_raw, STAGES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -374,9 +395,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUte
     const uint32_t tmem = setup<BN, STAGES>(c, warp);
 
     if (warp == 0) {
-        if (lane == 0) produce<BN, STAGES, SPLIT>(c, &a_hi, &a_lo, &b_hi, &b_lo, m0, n0, kb0, nkb, p.err);
+        if (lane == 0) produce<BN, STAGES, SPLIT, KB>(c, &a_hi, &a_lo, &b_hi, &b_lo, m0, n0, kb0, nkb, p.err);
     } else if (warp == 1) {
-        if (lane == 0) mma_loop<BN, STAGES, SPLIT>(c, tmem, nkb, p.err);
+        if (lane == 0) mma_loop<BN, STAGES, SPLIT, KB>(c, tmem, nkb, p.err);
     } else {
         if (p.noise) gram_noise_share(p);
         if (warp >= 6) {
@@ -894,19 +915,22 @@ int64_t tc_partial_floats(int max_n, int /*sms*/) {
 namespace {
 
 // 2-D BF16 tensor map: rows x cols (cols contiguous), row pitch `pitch`
-// elements, box = BK columns x box_rows rows, 128-byte swizzle, zero fill.
+// elements, box = box_cols columns x box_rows rows, zero fill; 64-column
+// boxes use the 128-byte swizzle, 32-column boxes the 64-byte swizzle.
 cudaError_t make_map(const TcContext *ctx, CUtensorMap *m, const void *base, int64_t cols, int64_t rows,
-                     int64_t pitch, int box_rows) {
+                     int64_t pitch, int box_rows, int box_cols = BK) {
     if (!base) {  // an unused plane: point at nothing valid but keep the map well formed
         memset(m, 0, sizeof(*m));
         return cudaSuccess;
     }
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch) * 2};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+    if (box_cols != 64 && box_cols != 32) return cudaErrorInvalidValue;
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = ctx->encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -916,10 +940,10 @@ cudaError_t set_smem(K kernel, int bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, int KB = BK>
 cudaError_t run_gram(const CUtensorMap (&maps)[4], const GramParams &p, dim3 grid, cudaStream_t s) {
-    using P = Plan<BN, STAGES, SPLIT>;
-    auto kern = k_gram_tc<BN, STAGES, SPLIT>;
+    using P = Plan<BN, STAGES, SPLIT, KB>;
+    auto kern = k_gram_tc<BN, STAGES, SPLIT, KB>;
     cudaError_t e = set_smem(kern, P::kBytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, kGramThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
@@ -974,17 +998,18 @@ GramChoice default_gram_choice(const TcGramArgs &a) {
 cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const GramChoice &ch, int *splits,
                         int64_t *part_stride, int *ldp, cudaStream_t s) {
     const int BN = ch.bn;
+    const int KB = ch.bk == 32 ? 32 : BK;
     CUtensorMap maps[4];
     cudaError_t e;
-    if ((e = make_map(ctx, &maps[0], a.zb_hi, a.d, a.n, a.d, BM)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[1], a.split3 ? a.zb_lo : nullptr, a.d, a.n, a.d, BM)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[2], a.xb_hi, a.d, a.n_x, a.d, BN)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[3], a.split3 ? a.xb_lo : nullptr, a.d, a.n_x, a.d, BN)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[0], a.zb_hi, a.d, a.n, a.d, BM, KB)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[1], a.split3 ? a.zb_lo : nullptr, a.d, a.n, a.d, BM, KB)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[2], a.xb_hi, a.d, a.n_x, a.d, BN, KB)) != cudaSuccess) return e;
+    if ((e = make_map(ctx, &maps[3], a.split3 ? a.xb_lo : nullptr, a.d, a.n_x, a.d, BN, KB)) != cudaSuccess) return e;
     const int mt = (a.n + BM - 1) / BM, nt = (a.n_x + BN - 1) / BN;
     GramParams p;
     p.n = a.n;
     p.n_x = a.n_x;
-    p.kblocks = static_cast<int>((a.d + BK - 1) / BK);
+    p.kblocks = static_cast<int>((a.d + KB - 1) / KB);
     const int64_t per_split = static_cast<int64_t>(a.n) * a.n_x;
     int S = ch.splits > 0 ? ch.splits : choose_splits(mt * nt, p.kblocks, sms, per_split, a.partial_cap);
     S = std::max(1, std::min<int>(S, static_cast<int>(std::min<int64_t>(p.kblocks, a.partial_cap / per_split))));
@@ -1001,6 +1026,15 @@ cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const Gram
     *part_stride = per_split;
     *ldp = a.n_x;
     dim3 grid(mt, nt, S);
+    if (KB == 32) {  // narrow k-blocks: twice the ring depth for the same bytes in flight
+        if (a.split3) {
+            if (BN == 256) return ch.stages == 3 ? run_gram<256, 3, true, 32>(maps, p, grid, s)
+                                                 : run_gram<256, 4, true, 32>(maps, p, grid, s);
+            return run_gram<128, 6, true, 32>(maps, p, grid, s);
+        }
+        if (BN == 256) return run_gram<256, 8, false, 32>(maps, p, grid, s);
+        return run_gram<128, 12, false, 32>(maps, p, grid, s);
+    }
     if (a.split3) {
         if (BN == 256) return run_gram<256, 2, true>(maps, p, grid, s);
         return run_gram<128, 3, true>(maps, p, grid, s);
@@ -1071,6 +1105,27 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     if (BN == 256) return inl ? run_wx<256, 4, false, true>(maps, p, sms, s) : run_wx<256, 4, false, false>(maps, p, sms, s);
     if (BN == 128) return inl ? run_wx<128, 6, false, true>(maps, p, sms, s) : run_wx<128, 6, false, false>(maps, p, sms, s);
     return inl ? run_wx<64, 8, false, true>(maps, p, sms, s) : run_wx<64, 8, false, false>(maps, p, sms, s);
+}
+
+cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3, const GramChoice &g, int wx_bn,
+                          bool wx_split) {
+    if (!ctx) return cudaErrorInvalidValue;
+    const int bk = g.bk ? g.bk : BK;
+    bool ok;
+    if (split3)
+        ok = (bk == 64 && ((g.bn == 128 && g.stages == 3) || (g.bn == 256 && g.stages == 2))) ||
+             (bk == 32 && ((g.bn == 128 && g.stages == 6) || (g.bn == 256 && (g.stages == 4 || g.stages == 3))));
+    else
+        ok = (bk == 64 && ((g.bn == 128 && g.stages == 6) || (g.bn == 256 && g.stages == 4))) ||
+             (bk == 32 && ((g.bn == 128 && g.stages == 12) || (g.bn == 256 && g.stages == 8)));
+    if (!ok || g.splits < 0 || (wx_bn != 0 && wx_bn != 64 && wx_bn != 128 && wx_bn != 256))
+        return cudaErrorInvalidValue;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    GramChoice c = g;
+    c.bk = bk;
+    ctx->gram_tuned[std::make_tuple(n, n_x, d, split3)] = c;
+    if (wx_bn) ctx->wx_tuned[std::make_tuple(n, d, wx_split)] = wx_bn;
+    return cudaSuccess;
 }
 
 cudaError_t tc_encode_map(TcContext *ctx, void *out128, const void *base, int64_t cols, int64_t rows, int64_t pitch,
@@ -1160,15 +1215,20 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
         const GramChoice base = default_gram_choice(*g);
         GramChoice best = base;
         float best_ms = 1e30f;
-        for (int bn : {128, 256}) {
+        // (tile width, ring depth, k-block width); the split count is searched
+        // around the cost model's choice
+        const int shapes[][3] = {{128, 3, 64}, {256, 2, 64}, {128, 6, 32}, {256, 4, 32}, {256, 3, 32}};
+        for (const auto &sh : shapes) {
+            const int bn = sh[0], kbw = sh[2];
             if (bn == 256 && g->n_x <= 128) continue;
-            const int stages = g->split3 ? (bn == 256 ? 2 : 3) : (bn == 256 ? 4 : 6);
+            const int stages = g->split3 ? sh[1] : (kbw == 32 ? (bn == 256 ? 8 : 12) : (bn == 256 ? 4 : 6));
+            if (!g->split3 && bn == 256 && kbw == 32 && sh[1] == 3) continue;  // one non-split narrow shape per width
             const int mt = (g->n + BM - 1) / BM, nt = (g->n_x + bn - 1) / bn;
-            const int kblocks = static_cast<int>((g->d + BK - 1) / BK);
+            const int kblocks = static_cast<int>((g->d + kbw - 1) / kbw);
             const int s0 = choose_splits(mt * nt, kblocks, sms, static_cast<int64_t>(g->n) * g->n_x, g->partial_cap);
             for (int sp : {s0, std::max(1, s0 / 2), s0 * 2, std::max(1, (s0 * 3) / 4), (s0 * 3) / 2,
                            std::max(1, s0 / 4), std::max(1, s0 / 8)}) {
-                GramChoice ch{bn, stages, sp};
+                GramChoice ch{bn, stages, sp, kbw};
                 int splits = 0, ldp = 0;
                 int64_t ps = 0;
                 float ms = 0.f;
@@ -1193,6 +1253,7 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
             rep->gram_bn = best.bn;
             rep->gram_stages = best.stages;
             rep->gram_splits = best.splits;
+            rep->gram_bk = best.bk ? best.bk : BK;
             rep->gram_ms = best_ms;
         }
     }

@@ -16,10 +16,11 @@ struct GramChoice {
     int bn = 0;      // output tile width (128 or 256 forecast members)
     int stages = 0;  // shared-memory ring depth
     int splits = 0;  // split-K slices over d (0: cost model)
+    int bk = 0;      // k-block width: 64 (128-byte swizzle) or 32 (64-byte swizzle); 0 = 64
 };
 
 struct TcTuneReport {
-    int gram_bn = 0, gram_stages = 0, gram_splits = 0;
+    int gram_bn = 0, gram_stages = 0, gram_splits = 0, gram_bk = 0;
     float gram_ms = 0.f;
     int wx_bn = 0;
     float wx_ms = 0.f;
@@ -123,6 +124,11 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
 // `after_gram(splits, part_stride, ldp)` enqueues whatever consumes the
 // partials (the row softmax), so that a shape is judged by Gram + reduction.
 using AfterGram = cudaError_t (*)(void *ctx, int splits, int64_t part_stride, int ldp, cudaStream_t s);
+// Records a launch shape for (n, n_x, d) as if the autotuner had chosen it
+// (wx_bn 0 leaves W X alone).  cudaErrorInvalidValue for a shape that has no
+// compiled kernel.
+cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3, const GramChoice &g, int wx_bn,
+                          bool wx_split);
 cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, int sms, cudaStream_t s,
                         TcTuneReport *rep, AfterGram after_gram = nullptr, void *after_ctx = nullptr);
 

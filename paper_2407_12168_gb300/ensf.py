@@ -48,7 +48,8 @@ class EnsfProfileEntry(ctypes.Structure):
 
 class EnsfTuning(ctypes.Structure):
     _fields_ = [("gram_tile_n", ctypes.c_int), ("gram_stages", ctypes.c_int), ("gram_splits", ctypes.c_int),
-                ("gram_ms", ctypes.c_float), ("wx_tile_n", ctypes.c_int), ("wx_ms", ctypes.c_float)]
+                ("gram_ms", ctypes.c_float), ("wx_tile_n", ctypes.c_int), ("wx_ms", ctypes.c_float),
+                ("gram_k_block", ctypes.c_int)]
 
 
 class EnsfSqgParams(ctypes.Structure):
@@ -102,6 +103,7 @@ _SIGNATURES = [
                                       ctypes.c_void_p]),
     ("ensf_relax_spread", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                                          ctypes.c_float, ctypes.c_int, ctypes.c_void_p]),
+    ("ensf_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(EnsfTuning)]),
     ("ensf_model_error", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_float),
                                         ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
     ("ensf_stats_scratch_bytes", ctypes.c_size_t, [ctypes.c_int64]),
@@ -265,6 +267,14 @@ class Filter:
                                               perm.data_ptr(), int(J), out.data_ptr(), _stream_ptr(stream)),
                "ensf_analysis_minibatch")
         return out
+
+    def set_tuning(self, n: int, d: int, gram_tile_n: int, gram_stages: int, gram_k_block: int = 64,
+                   gram_splits: int = 0, wx_tile_n: int = 0):
+        """Record tensor-core launch shapes for analyses of this (n, d)
+        without timing them (e.g. a report saved from ``autotune``)."""
+        t = EnsfTuning(gram_tile_n=gram_tile_n, gram_stages=gram_stages, gram_splits=gram_splits,
+                       wx_tile_n=wx_tile_n, gram_k_block=gram_k_block)
+        _check(load().ensf_set_tuning(self._h, int(n), int(d), ctypes.byref(t)), "ensf_set_tuning")
 
     def autotune(self, prior, y, mask, sigma_obs: float, eps: float, obs_op: int = OBS_IDENTITY, seed: int = 0,
                  out=None, stream=None) -> dict:

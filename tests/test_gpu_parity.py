@@ -379,3 +379,62 @@ def test_analysis_large_512_rows_in_the_bench_configuration():
     rel, tie, bad = compare_members(got, ref, cond, tol)
     assert not bad.any(), describe(rel, tie, bad)
     assert tie.sum() <= 1, describe(rel, tie, bad)
+
+
+GRAM_SHAPES = {
+    # Gram precision: (tile width, ring depth, k-block width) of every compiled variant
+    "split": [(256, 2, 64), (128, 3, 64), (128, 6, 32), (256, 4, 32), (256, 3, 32)],
+    "bf16": [(256, 4, 64), (128, 6, 64), (128, 12, 32), (256, 8, 32)],
+}
+
+
+@pytest.mark.parametrize("gram", ["split", "bf16"])
+def test_gram_launch_shapes_agree_bitwise(gram):
+    """Every K = 16 MMA chunk is accumulated in the same order whatever the
+    tile width, ring depth or k-block width, so with the same split
+    boundaries (d = 72 x 64, two splits) every launch shape gives the same
+    bits through the whole analysis."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    p = inputs.small_case(seed=61, n=300, grid=48, layers=2, K=4, obs_op=1, obs_frac=0.5, sigma_obs=0.5)
+    prior, y = torch.from_numpy(p.prior).cuda(), torch.from_numpy(p.y).cuda()
+    mask = torch.from_numpy(p.mask).cuda()
+    outs = []
+    for bn, stages, bk in GRAM_SHAPES[gram]:
+        f = ensf.Filter(p.n, p.d, gram=gram, wx="bf16", check_finite=True)
+        f.set_tuning(p.n, p.d, bn, stages, gram_k_block=bk, gram_splits=2)
+        outs.append(f.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed).cpu().numpy())
+        assert f.status_sync() == 0
+    for (bn, stages, bk), o_ in zip(GRAM_SHAPES[gram][1:], outs[1:]):
+        np.testing.assert_array_equal(o_, outs[0], err_msg=f"shape {(bn, stages, bk)}")
+
+
+@pytest.mark.parametrize("shape", [(128, 6, 32), (256, 4, 32), (256, 3, 32)])
+def test_narrow_kblock_gram_ragged_matches_oracle(shape):
+    """32-wide k-blocks (64-byte swizzle) with a ragged state tail (d = 2888
+    is not a multiple of 32), ragged member tiles (N = 70) and three splits
+    that do not divide the k-blocks evenly, against the oracle."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    gram, wx, tol = PATHS["split"]
+    p = inputs.small_case(seed=62, n=70, grid=38, layers=2, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
+    ref = run_oracle(p)
+    cond = conditioning(p, ref, prec=_cond_prec(gram, wx))
+    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, check_finite=True)
+    bn, stages, bk = shape
+    f.set_tuning(p.n, p.d, bn, stages, gram_k_block=bk, gram_splits=3)
+    got = _gpu_analysis(p, gram, wx, filt=f)
+    rel, tie, bad = compare_members(got, ref, cond, tol)
+    assert not bad.any(), describe(rel, tie, bad)
+    assert tie.sum() <= 2, describe(rel, tie, bad)
+
+
+def test_set_tuning_rejects_shapes_without_a_kernel():
+    from paper_2407_12168_gb300 import ensf
+    f = ensf.Filter(64, 4096, gram="split", wx="bf16")
+    for bn, stages, bk in [(256, 4, 64), (128, 5, 32), (192, 2, 64), (256, 2, 16)]:
+        with pytest.raises(ensf.EnsfError):
+            f.set_tuning(64, 4096, bn, stages, gram_k_block=bk)
+    g = ensf.Filter(64, 4096, gram="fp32", wx="fp32")
+    with pytest.raises(ensf.EnsfError):
+        g.set_tuning(64, 4096, 256, 2)
