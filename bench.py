@@ -233,6 +233,18 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
                 "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback",
                 "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms,
                 "tflops": flops / (avg_ms / 1e3) / 1e12}
+    if kernel == "softmax_rows":
+        # split-K partials read (FP32), weights written (BF16 planes or FP32), FP64 norms read
+        splits = (args.tuning or {}).get("gram_splits") or 1
+        w_bytes = 4 if wx == "fp32" else (4 if wx == "split" else 2)
+        nbytes = (4 * splits + w_bytes) * n * nx + 8 * nx
+        peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
+        achieved = nbytes / (avg_ms / 1e3) / 1e9
+        return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback",
+                "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms,
+                "note": "latency bound at this size (partials mostly L2-resident)"}
     if kernel not in ("gram", "wx_em"):
         return {"kernel": kernel, "bound": None, "avg_launch_ms": avg_ms}
     split_factor = {"split": 3.0, "bf16": 1.0, "fp32": 1.0}[prec]
@@ -374,6 +386,7 @@ def run_ours(args):
     tuning = None
     if gram != "fp32" or wx != "fp32":
         tuning = f.autotune(prior, y, mask, p.sigma_obs, p.eps, p.obs_op, seed=p.seed, out=out)
+    args.tuning = tuning
     small = p.n * p.d * 4 <= 256 << 20
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if small else None
 
@@ -448,6 +461,11 @@ def run_ours(args):
     d_mask = torch.empty_like(mask) if mask is not None else None
     e2e_steps = max(1, min(args.steps, 3))
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    # one untimed pass first: the first device writes into freshly pinned host
+    # pages cost a one-time mapping
+    d_prior.copy_(h_prior, non_blocking=True)
+    h_out.copy_(d_prior, non_blocking=True)
+    torch.cuda.synchronize()
     for s_ in range(e2e_steps):
         if flush is not None:
             flush.zero_()

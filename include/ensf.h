@@ -129,6 +129,8 @@ typedef struct {
     int wx_tile_n;     /* W X tile width (particles per tile)                         */
     float wx_ms;       /* measured time of one W X launch with that shape            */
     int gram_k_block;  /* Gram k-block width in elements (64 or 32)                   */
+    int gram_cta_pair; /* 1: Gram tiles of 256 x 256 on a cluster of two CTAs         */
+    int gram_noise_warps; /* warps of a Gram CTA generating the next step's noise (8 or 4) */
 } ensf_tuning;
 
 /* Autotuner for the tensor-core stages: times the candidate launch shapes of
@@ -147,7 +149,8 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
  * gram_tile_n, gram_stages, gram_splits (0: the cost model), gram_k_block and
  * wx_tile_n (0: unchanged) fields of `t`.  Valid Gram shapes (tile width,
  * ring depth, k-block) for the split-BF16x3 Gram: (128, 3, 64), (256, 2, 64),
- * (128, 6, 32), (256, 4, 32), (256, 3, 32); for the BF16 Gram: (128, 6, 64),
+ * (128, 6, 32), (256, 4, 32), (256, 3, 32), and with gram_cta_pair = 1
+ * (256, 3, 64) when n is a multiple of 256; for the BF16 Gram: (128, 6, 64),
  * (256, 4, 64), (128, 12, 32), (256, 8, 32).  EINVAL for any other shape, for
  * n or d outside the handle's limits, or for a handle whose Gram runs on
  * CUDA cores. */

@@ -623,6 +623,8 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         report->wx_tile_n = r.wx_bn;
         report->wx_ms = r.wx_ms;
         report->gram_k_block = r.gram_bk;
+        report->gram_cta_pair = r.gram_pair;
+        report->gram_noise_warps = r.gram_noise_warps;
     }
     return ENSF_OK;
 }
@@ -637,6 +639,8 @@ ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning 
     g.stages = t->gram_stages;
     g.splits = t->gram_splits;
     g.bk = t->gram_k_block;
+    g.pair = t->gram_cta_pair;
+    g.noise_warps = t->gram_noise_warps;
     const bool split3 = h->cfg.gram == ENSF_PREC_SPLIT_BF16X3;
     const bool wx_split = h->cfg.wx == ENSF_PREC_SPLIT_BF16X3;
     if (ensf::tc_set_tuning(h->tc, n, n, d, split3, g, is_tc(h->cfg.wx) ? t->wx_tile_n : 0, wx_split) != cudaSuccess)

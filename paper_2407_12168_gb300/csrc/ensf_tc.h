@@ -17,10 +17,12 @@ struct GramChoice {
     int stages = 0;  // shared-memory ring depth
     int splits = 0;  // split-K slices over d (0: cost model)
     int bk = 0;      // k-block width: 64 (128-byte swizzle) or 32 (64-byte swizzle); 0 = 64
+    int pair = 0;    // 1: a cluster of two CTAs per 256 x 256 tile (tcgen05 cta_group::2)
+    int noise_warps = 0;  // warps generating the next step's noise: 8 (default) or 4
 };
 
 struct TcTuneReport {
-    int gram_bn = 0, gram_stages = 0, gram_splits = 0, gram_bk = 0;
+    int gram_bn = 0, gram_stages = 0, gram_splits = 0, gram_bk = 0, gram_pair = 0, gram_noise_warps = 0;
     float gram_ms = 0.f;
     int wx_bn = 0;
     float wx_ms = 0.f;

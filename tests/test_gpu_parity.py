@@ -432,9 +432,58 @@ def test_narrow_kblock_gram_ragged_matches_oracle(shape):
 def test_set_tuning_rejects_shapes_without_a_kernel():
     from paper_2407_12168_gb300 import ensf
     f = ensf.Filter(64, 4096, gram="split", wx="bf16")
-    for bn, stages, bk in [(256, 4, 64), (128, 5, 32), (192, 2, 64), (256, 2, 16)]:
+    for bn, stages, bk in [(256, 4, 64), (128, 5, 32), (192, 2, 64), (256, 2, 16), (256, 3, 64)]:
         with pytest.raises(ensf.EnsfError):
             f.set_tuning(64, 4096, bn, stages, gram_k_block=bk)
     g = ensf.Filter(64, 4096, gram="fp32", wx="fp32")
     with pytest.raises(ensf.EnsfError):
         g.set_tuning(64, 4096, 256, 2)
+
+
+def test_pair_gram_matches_single_cta_bitwise():
+    """The CTA-pair Gram (tcgen05 cta_group::2, 256 x 256 tiles) accumulates
+    the K = 16 chunks in the same order as the single-CTA shapes: with the
+    same split boundaries the analyses are bitwise equal (N = 512, two
+    pair tiles per side)."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    p = inputs.small_case(seed=63, n=512, grid=48, layers=2, K=3, obs_op=1, obs_frac=0.5, sigma_obs=0.5)
+    prior, y = torch.from_numpy(p.prior).cuda(), torch.from_numpy(p.y).cuda()
+    mask = torch.from_numpy(p.mask).cuda()
+    outs = []
+    # (pair, tile width, ring depth, warps generating the next step's noise)
+    for pair, bn, stages, nw in [(0, 256, 2, 8), (1, 256, 3, 8), (0, 128, 3, 8), (1, 256, 3, 4), (0, 256, 2, 4)]:
+        f = ensf.Filter(p.n, p.d, gram="split", wx="bf16", check_finite=True)
+        f.set_tuning(p.n, p.d, bn, stages, gram_splits=2, gram_cta_pair=pair, gram_noise_warps=nw)
+        outs.append(f.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed).cpu().numpy())
+        assert f.status_sync() == 0
+    for o_ in outs[1:]:
+        np.testing.assert_array_equal(o_, outs[0])
+
+
+def test_pair_gram_ragged_state_matches_oracle():
+    """One pair tile (N = 256), a ragged state tail (d = 2888 is not a
+    multiple of the 64-wide k-block) and three uneven splits, against the
+    oracle."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    gram, wx, tol = PATHS["split"]
+    p = inputs.small_case(seed=64, n=256, grid=38, layers=2, K=5, obs_op=1, obs_frac=0.5, sigma_obs=0.5)
+    ref = run_oracle(p)
+    cond = conditioning(p, ref, prec=_cond_prec(gram, wx))
+    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, check_finite=True)
+    f.set_tuning(p.n, p.d, 256, 3, gram_splits=3, gram_cta_pair=1)
+    got = _gpu_analysis(p, gram, wx, filt=f)
+    rel, tie, bad = compare_members(got, ref, cond, tol)
+    assert not bad.any(), describe(rel, tie, bad)
+    assert tie.sum() <= max(1, p.n // 50), describe(rel, tie, bad)
+
+
+def test_pair_gram_needs_whole_pair_tiles():
+    from paper_2407_12168_gb300 import ensf
+    f = ensf.Filter(300, 4096, gram="split", wx="bf16")
+    with pytest.raises(ensf.EnsfError):
+        f.set_tuning(300, 4096, 256, 3, gram_cta_pair=1)
+    g = ensf.Filter(512, 4096, gram="bf16", wx="bf16")
+    with pytest.raises(ensf.EnsfError):
+        g.set_tuning(512, 4096, 256, 3, gram_cta_pair=1)
