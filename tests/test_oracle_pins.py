@@ -449,3 +449,96 @@ def test_relax_spread_properties():
     z2 = z.copy()
     z2[:, 0] = 0.25
     np.testing.assert_allclose(o.relax_spread(prior, z2, 1.0, "spread")[:, 0], 0.25)
+
+
+def test_tiny_analysis_against_50_digit_brute_force():
+    """Brute force on tiny inputs (N <= 3, d <= 4, K <= 3): the whole analysis
+    in 50-digit decimal arithmetic, with the drift and diffusion of Eq. 9
+    obtained by differentiating alpha_t and beta_t^2 numerically (not from
+    their closed forms), the Gaussian-kernel weights from the squared
+    distances, the likelihood score of Eq. 5 and the Euler-Maruyama step of
+    Eq. 7; the FP64 oracle agrees to 1e-12."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    g = np.random.default_rng(17)
+    for n, d, K, obs_op in [(1, 2, 2, 0), (2, 3, 3, 1), (3, 4, 3, 0), (3, 4, 1, 1)]:
+        X = g.standard_normal((n, d)).astype(np.float32)
+        y = g.standard_normal(d).astype(np.float32)
+        mask = np.array([1, 0, 1, 1][:d], np.uint8)
+        nb = g.standard_normal((K + 1, n, d)).astype(np.float32)
+        sigma, eps = 0.7, 0.05
+        ref = o.analysis(X, y, mask, sigma, K, eps, obs_op, noise_buf=nb)
+        D = Decimal
+        eps_d, one = D(eps), D(1)
+        alpha = lambda t: one - t * (one - eps_d)
+        beta2 = lambda t: t
+        hstep = D(10) ** -20
+
+        def ln(v):
+            return v.ln()
+
+        def deriv(f, t):
+            return (f(t + hstep) - f(t - hstep)) / (2 * hstep)
+
+        r2 = D(sigma) ** 2
+        for i in range(n):
+            z = [D(float(v)) for v in nb[0, i]]
+            for k in range(K):
+                t = one - D(k) / D(K)
+                a, b2 = alpha(t), beta2(t)
+                b = deriv(lambda s: ln(alpha(s)), t)                 # d log alpha / dt
+                s2 = deriv(beta2, t) - 2 * b * b2                     # d beta^2/dt - 2 b beta^2
+                h = one - t
+                logits = [-sum((z[c] - a * D(float(X[j, c]))) ** 2 for c in range(d)) / (2 * b2)
+                          for j in range(n)]
+                m = max(logits)
+                ws = [(lj - m).exp() for lj in logits]
+                tot = sum(ws)
+                ws = [w / tot for w in ws]
+                dt = one / D(K)
+                nz = []
+                for c in range(d):
+                    sp = -sum(ws[j] * (z[c] - a * D(float(X[j, c]))) for j in range(n)) / b2
+                    if mask[c]:
+                        if obs_op == 1:
+                            # arctan by its Taylor series after two argument halvings
+                            # (atan v = 2 atan(v / (1 + sqrt(1 + v^2))))
+                            v = z[c]
+                            for _ in range(2):
+                                v = v / (one + (one + v * v).sqrt())
+                            acc, term, j = D(0), v, 0
+                            while abs(term) > D(10) ** -45:
+                                acc += term / (2 * j + 1)
+                                term = -term * v * v
+                                j += 1
+                            hz = 4 * acc
+                            dh = one / (one + z[c] * z[c])
+                        else:
+                            hz, dh = z[c], one
+                        gl = dh * (D(float(y[c])) - hz) / r2
+                    else:
+                        gl = D(0)
+                    sc = sp + h * gl
+                    nz.append(z[c] - dt * (b * z[c] - s2 * sc) + (s2 * dt).sqrt() * D(float(nb[k + 1, i, c])))
+                z = nz
+            got = np.array([float(v) for v in z])
+            np.testing.assert_allclose(ref[i], got, rtol=1e-12, atol=1e-12, err_msg=f"n={n} d={d} K={K} op={obs_op}")
+
+
+def test_random_field_spectrum_and_variance():
+    """The synthetic truth: isotropic power spectrum |k|^-3 (log-log slope of
+    the shell-averaged spectrum -3 +- 0.05 over the resolved band) and unit
+    variance per layer."""
+    f = inputs.gaussian_random_field(2, 256, 3.0, np.random.default_rng(5))
+    assert f.shape == (2, 256, 256)
+    np.testing.assert_allclose(f.std(axis=(1, 2)), 1.0, rtol=1e-12)
+    np.testing.assert_allclose(f.mean(axis=(1, 2)), 0.0, atol=1e-12)
+    slopes = []
+    for layer in f:
+        P = np.abs(np.fft.fft2(layer)) ** 2
+        k = np.fft.fftfreq(256) * 256
+        kk = np.sqrt(k[:, None] ** 2 + k[None, :] ** 2)
+        shells = np.arange(4, 64)
+        spec = np.array([P[(kk >= s - 0.5) & (kk < s + 0.5)].mean() for s in shells])
+        slopes.append(np.polyfit(np.log(shells), np.log(spec), 1)[0])
+    assert abs(np.mean(slopes) + 3.0) < 0.05, slopes

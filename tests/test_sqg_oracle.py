@@ -95,3 +95,16 @@ def test_relaxation_decay_rate():
     out = sq.run(theta, 250, p)
     ratio = np.abs(out[0]).max() / np.abs(theta[0]).max()
     assert ratio == pytest.approx(np.exp(-250 * p.dt / p.tau_relax), rel=1e-6)
+
+
+def test_spectral_transform_matches_naive_dft():
+    """The oracle's grid <-> spectral transforms against a naive DFT on 8 x 8."""
+    g = np.random.default_rng(3)
+    th = g.standard_normal((2, 8, 8))
+    spec = sq.to_spectral(th)
+    j = np.arange(8)
+    W = np.exp(-2j * np.pi * np.outer(j, j) / 8)
+    for lev in range(2):
+        naive = W @ th[lev] @ W.T          # sum over y, x of theta e^{-2 pi i (k_y y + k_x x)/8}
+        np.testing.assert_allclose(spec[lev], naive[:, :5], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(sq.to_grid(spec, 8), th, rtol=1e-12, atol=1e-12)
