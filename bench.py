@@ -440,18 +440,6 @@ def run_ours(args):
     if f.status_sync() != 0:
         raise RuntimeError("device error during the benchmark")
 
-    # ---- per-kernel timing: the same steps again, every launch bracketed by
-    # CUDA events on its stream (kept out of the timed region above, whose
-    # small kernels the extra events would slow down) ----
-    f.profile_enable(True)
-    for s_ in range(args.steps):
-        if flush is not None:
-            flush.zero_()
-        one(100 + s_)
-    torch.cuda.synchronize()
-    prof = f.profile_read()
-    f.profile_enable(False)
-
     # ---- end to end: host buffers, copies inside the timed region ----
     h_prior = torch.from_numpy(p.prior).pin_memory()
     h_y = torch.from_numpy(p.y).pin_memory()
@@ -466,21 +454,35 @@ def run_ours(args):
     d_prior.copy_(h_prior, non_blocking=True)
     h_out.copy_(d_prior, non_blocking=True)
     torch.cuda.synchronize()
-    for s_ in range(e2e_steps):
-        if flush is not None:
-            flush.zero_()
-        ee[s_][0].record(stream)
-        d_prior.copy_(h_prior, non_blocking=True)
-        d_y.copy_(h_y, non_blocking=True)
-        if d_mask is not None:
-            d_mask.copy_(h_mask, non_blocking=True)
-        analyse(d_prior, d_y, d_mask, 200 + s_)
-        h_out.copy_(out, non_blocking=True)
-        ee[s_][1].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = float(sum(a.elapsed_time(b) for a, b in ee)) / e2e_steps
+    with ClockSampler(local_rank) as e2e_clk:
+        for s_ in range(e2e_steps):
+            if flush is not None:
+                flush.zero_()
+            ee[s_][0].record(stream)
+            d_prior.copy_(h_prior, non_blocking=True)
+            d_y.copy_(h_y, non_blocking=True)
+            if d_mask is not None:
+                d_mask.copy_(h_mask, non_blocking=True)
+            analyse(d_prior, d_y, d_mask, 200 + s_)
+            h_out.copy_(out, non_blocking=True)
+            ee[s_][1].record(stream)
+        torch.cuda.synchronize()
+    e2e_each = [a.elapsed_time(b) for a, b in ee]
+    e2e_ms = float(sum(e2e_each)) / e2e_steps
     h2d = p.prior.nbytes + p.y.nbytes + (p.mask.nbytes if p.mask is not None else 0)
     d2h = p.n * p.d * 4
+    # ---- per-kernel timing: the same steps again, every launch bracketed by
+    # CUDA events on its stream (kept out of the timed region above, whose
+    # small kernels the extra events would slow down) ----
+    f.profile_enable(True)
+    for s_ in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        one(100 + s_)
+    torch.cuda.synchronize()
+    prof = f.profile_read()
+    f.profile_enable(False)
+
     # ---- accuracy: one more analysis with the workload's own seed (and the
     # identity permutation for the mini-batch form), ensemble-mean RMSE
     # against the truth, beside the FP64 oracle's when the CPU baseline's
@@ -530,7 +532,8 @@ def run_ours(args):
             "roofline": roof, "accuracy": accuracy,
             "roofline_other": other,
             "kernels": {k: {"launches": v[0], "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "clocks": e2e_clk.summary(), "ms_per_step": [round(v, 2) for v in e2e_each]},
             "gpu_launches": gpu_launches, "clocks": clk.summary(), "tuning": tuning, "cuda_graph": args.graph}
     if not args.no_cpu_baseline:
         line["cpu_baseline"], oracle_out = cpu_baseline(p, args.cpu_budget_s, J or 0)

@@ -131,6 +131,8 @@ typedef struct {
     int gram_k_block;  /* Gram k-block width in elements (64 or 32)                   */
     int gram_cta_pair; /* 1: Gram tiles of 256 x 256 on a cluster of two CTAs         */
     int gram_noise_warps; /* warps of a Gram CTA generating the next step's noise (8 or 4) */
+    int gram_fp32_particles; /* 1 (pair tiles only): the Gram reads the FP32 particles and splits
+                                them itself, so the W X step writes no BF16 particle planes */
 } ensf_tuning;
 
 /* Autotuner for the tensor-core stages: times the candidate launch shapes of
@@ -150,7 +152,8 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
  * wx_tile_n (0: unchanged) fields of `t`.  Valid Gram shapes (tile width,
  * ring depth, k-block) for the split-BF16x3 Gram: (128, 3, 64), (256, 2, 64),
  * (128, 6, 32), (256, 4, 32), (256, 3, 32), and with gram_cta_pair = 1
- * (256, 3, 64) when n is a multiple of 256; for the BF16 Gram: (128, 6, 64),
+ * (256, 3, 64) when n is a multiple of 256 (optionally with
+ * gram_fp32_particles = 1); for the BF16 Gram: (128, 6, 64),
  * (256, 4, 64), (128, 12, 32), (256, 8, 32).  EINVAL for any other shape, for
  * n or d outside the handle's limits, or for a handle whose Gram runs on
  * CUDA cores. */

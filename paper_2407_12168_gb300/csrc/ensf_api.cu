@@ -244,6 +244,9 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
         a.seed = nr.seed;
         a.offset = nr.offset;
         a.noise_k = nr.k;
+        a.z32 = z;
+        a.centre = h->at<float>(L.xbar);
+        a.alpha = c.alpha;
         ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_tc(h->tc, a, h->sms, &splits, &part_stride, &ldp, s));
     }
     __nv_bfloat16 *wb_hi = nullptr, *wb_lo = nullptr;
@@ -372,7 +375,7 @@ ensf_status analysis_validate(ensf_handle *h, const float *prior, int n, int64_t
 // perm (device, optional): the split planes and norms hold the members in this order.
 ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, int K, float eps, float sigma_obs,
                           int obs_op, const ensf_noise *noise, float *out, cudaStream_t s,
-                          const int *perm = nullptr) {
+                          const int *perm = nullptr, bool skip_z_split = false) {
     const Layout &L = h->L;
     const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
     float *xbar = h->at<float>(L.xbar);
@@ -383,9 +386,11 @@ ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, 
         ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(prior, n, d, h->at<__nv_bfloat16>(L.xb_hi),
                                                            L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s,
                                                            xbar, 1.0f, perm));
-        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, h->at<__nv_bfloat16>(L.zb_hi),
-                                                           L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s,
-                                                           xbar, step_coef(0, K, eps, sigma_obs, obs_op).alpha));
+        if (!skip_z_split)  // (the FP32-operand Gram splits the particles itself)
+            ENSF_LAUNCH(h, P_SPLIT, s,
+                        ensf::launch_split_bf16(out, n, d, h->at<__nv_bfloat16>(L.zb_hi),
+                                                L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s, xbar,
+                                                step_coef(0, K, eps, sigma_obs, obs_op).alpha));
     }
     if (tc_wx)
         ENSF_LAUNCH(h, P_SPLIT, s,
@@ -437,10 +442,13 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
     // The Gram runs on centred operands z - alpha m and x_j - m, m = the forecast
     // mean: |z - alpha x_j|^2 is unchanged, the magnitudes entering the expanded
     // logit (and so its rounding error) shrink.
-    ensf_status st0 = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s, perm);
+    const int nm = (perm && J > 0) ? J : n;  // members per step (mini-batch window)
+    // the tuned Gram may read the FP32 particles and split them itself; then
+    // nobody needs the BF16 particle planes
+    const bool gram_f32 = tc_gram && ensf::tc_gram_reads_fp32(h->tc, n, nm, d, h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
+    ensf_status st0 = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s, perm, gram_f32);
     if (st0 != ENSF_OK) return st0;
     float *xbar = h->at<float>(L.xbar);
-    const int nm = (perm && J > 0) ? J : n;  // members per step (mini-batch window)
     __nv_bfloat16 *zb_hi = tc_gram ? h->at<__nv_bfloat16>(L.zb_hi) : nullptr;
     __nv_bfloat16 *zb_lo = (tc_gram && L.zb_lo) ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
     // The tensor-core W X reads the step's noise as a pre-generated [n][d]
@@ -467,12 +475,13 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
             ENSF_LAUNCH(h, P_WXEM, s,
                         ensf::launch_wx_em_fp32(h->at<float>(L.w), n, prior, n, n, d, out, y, obs_mask, noise->buf,
                                                 noise->seed, noise->offset, c, s));
-            if (tc_gram)
+            if (tc_gram && !gram_f32)
                 ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, zb_hi, zb_lo, d, s, xbar,
                                                                    step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha));
         } else {
             ensf::TcWxArgs a = wx_args(h, n, d, y, obs_mask, noise, out, c,
                                        step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha, k, x0, nm);
+            if (gram_f32) a.zb_hi = a.zb_lo = nullptr;
             ENSF_LAUNCH(h, P_WXEM, s, ensf::launch_wx_em_tc(h->tc, a, h->sms, s));
         }
     }
@@ -585,6 +594,9 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         ga.seed = nr.seed;
         ga.offset = nr.offset;
         ga.noise_k = nr.k;
+        ga.z32 = out;
+        ga.centre = h->at<float>(L.xbar);
+        ga.alpha = c.alpha;
     }
     ensf::TcWxArgs wa;
     if (tc_wx) {
@@ -625,6 +637,7 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         report->gram_k_block = r.gram_bk;
         report->gram_cta_pair = r.gram_pair;
         report->gram_noise_warps = r.gram_noise_warps;
+        report->gram_fp32_particles = r.gram_a_fp32;
     }
     return ENSF_OK;
 }
@@ -641,6 +654,7 @@ ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning 
     g.bk = t->gram_k_block;
     g.pair = t->gram_cta_pair;
     g.noise_warps = t->gram_noise_warps;
+    g.a_fp32 = t->gram_fp32_particles;
     const bool split3 = h->cfg.gram == ENSF_PREC_SPLIT_BF16X3;
     const bool wx_split = h->cfg.wx == ENSF_PREC_SPLIT_BF16X3;
     if (ensf::tc_set_tuning(h->tc, n, n, d, split3, g, is_tc(h->cfg.wx) ? t->wx_tile_n : 0, wx_split) != cudaSuccess)

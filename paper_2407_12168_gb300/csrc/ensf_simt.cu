@@ -1,5 +1,5 @@
 // ensf_simt.cu -- CUDA-core kernels of the EnSF analysis step:
-//   * FP64 squared row norms |x_j|^2 (used in the expanded logit)
+//   * squared row norms |x_j - m|^2 to FP64 accuracy (the expanded logit)
 //   * the counter-based Gaussian noise stream (Philox4x32-10 + Box-Muller)
 //   * the plain FP32 path: Gram Z X^T, row softmax, W X with the fused
 //     Euler-Maruyama epilogue
@@ -19,24 +19,46 @@ constexpr int kTileK = 16;   // reduction depth per shared-memory stage
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
 // ---------------------------------------------------------------------------
-// |x_j - m|^2 in FP64 (m = the centre vector, or 0): one block per row,
-// float4 loads, the difference rounded to FP32 as the Gram operands are,
-// fixed-order tree reduce.
+// |x_j - m|^2 to FP64 accuracy (m = the centre vector, or 0): one block per
+// row, float4 loads, the difference rounded to FP32 as the Gram operands are.
+// Each thread keeps a double-float (unevaluated FP32 pair) sum: squares are
+// split exactly into p + e with an FMA (Dekker's product), the running sum
+// is updated with Knuth's error-free two-sum, so the per-thread sums carry
+// about 48 bits at FP32 speed (GB300 issues FP64 at a small fraction of the
+// FP32 rate); the 256 thread sums are combined in FP64 in a fixed order.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+__device__ __forceinline__ void df_add_square(float &hi, float &lo, float v) {
+    const float p = __fmul_rn(v, v);
+    const float e = fmaf(v, v, -p);  // v*v - p exactly
+    df_add(hi, lo, p);
+    lo = __fadd_rn(lo, e);
+}
+
 __global__ void __launch_bounds__(256) k_row_norms(const float *__restrict__ x, int64_t d,
                                                    const float *__restrict__ centre, const int *__restrict__ rows,
                                                    double *__restrict__ out) {
     const float *row = x + (int64_t)(rows ? rows[blockIdx.x] : blockIdx.x) * d;
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     for (int64_t c = (int64_t)threadIdx.x * 4; c < d; c += 256 * 4) {
         float4 v = ld4(row + c);
         if (centre) {
             const float4 m = ld4(centre + c);
             v.x -= m.x; v.y -= m.y; v.z -= m.z; v.w -= m.w;
         }
-        acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+        df_add_square(hi, lo, v.x);
+        df_add_square(hi, lo, v.y);
+        df_add_square(hi, lo, v.z);
+        df_add_square(hi, lo, v.w);
     }
     __shared__ double red[256];
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = (double)hi + (double)lo;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -45,14 +67,24 @@ __global__ void __launch_bounds__(256) k_row_norms(const float *__restrict__ x, 
     if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
-// Column means m[c] = (1/n) sum_j x[j][c], FP64 accumulation, FP32 result.
+// Column means m[c] = (1/n) sum_j x[j][c] in FP32.  m only centres the Gram
+// operands: |(z - alpha m) - alpha (x_j - m)|^2 = |z - alpha x_j|^2 for any m,
+// so its rounding does not enter the result; the sum runs over four
+// interleaved partial sums for memory-level parallelism.
 __global__ void __launch_bounds__(256) k_col_mean(const float *__restrict__ x, int n, int64_t d,
                                                   float *__restrict__ m) {
     const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (c >= d) return;
-    double acc = 0.0;
-    for (int j = 0; j < n; ++j) acc += (double)x[(int64_t)j * d + c];
-    m[c] = (float)(acc / (double)n);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int j = 0;
+    for (; j + 4 <= n; j += 4) {
+        a0 += x[(int64_t)j * d + c];
+        a1 += x[(int64_t)(j + 1) * d + c];
+        a2 += x[(int64_t)(j + 2) * d + c];
+        a3 += x[(int64_t)(j + 3) * d + c];
+    }
+    for (; j < n; ++j) a0 += x[(int64_t)j * d + c];
+    m[c] = ((a0 + a1) + (a2 + a3)) / (float)n;
 }
 
 // ---------------------------------------------------------------------------
@@ -271,9 +303,12 @@ __global__ void k_split_bf16(const float *__restrict__ x, int64_t cols, __nv_bfl
     int r = blockIdx.y;
     if (q * 4 >= cols) return;
     float4 v = ld4(x + (int64_t)(rows ? rows[r] : r) * cols + q * 4);
-    if (centre) {  // split x - scale * m
+    if (centre) {  // split x - scale * m (product and difference each rounded, as in the W X epilogue)
         const float4 m = ld4(centre + q * 4);
-        v.x -= scale * m.x; v.y -= scale * m.y; v.z -= scale * m.z; v.w -= scale * m.w;
+        v.x = __fsub_rn(v.x, __fmul_rn(scale, m.x));
+        v.y = __fsub_rn(v.y, __fmul_rn(scale, m.y));
+        v.z = __fsub_rn(v.z, __fmul_rn(scale, m.z));
+        v.w = __fsub_rn(v.w, __fmul_rn(scale, m.w));
     }
     float vv[4] = {v.x, v.y, v.z, v.w};
     __align__(8) __nv_bfloat16 h[4], l[4];

@@ -86,6 +86,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Bounded wait for the phase with the given parity.  Returns false when the
 // CTA is aborting (another role timed out) or when this wait times out, in
 // which case it raises the abort flag and records ENSF_ETIMEOUT.
@@ -354,6 +358,9 @@ struct GramParams {
     int noise_k;
     int64_t d;
     int noise_warp0;   // first warp that generates noise (2: warps 2-9, 6: warps 6-9)
+    // FP32-operand form: A = z - alpha m split in the kernel (centre m, [d])
+    float alpha;
+    const float *centre;
 };
 
 // This CTA's share of the next step's noise slice, written while the MMAs
@@ -684,6 +691,245 @@ k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__
     }
 }
 
+// ------------------------------------------------ Pair Gram, FP32 particles
+// The same 256 x 256 pair tile, but the particle operand arrives as FP32 z
+// (two 128-byte-swizzled 32-column boxes per k-block) instead of BF16 hi/lo
+// planes: warps 2-5 form a = z - alpha m for their 32 rows, split it into
+// a_hi + a_lo and store both into TMEM with tcgen05.st; the MMAs take A from
+// TMEM (tcgen05.mma ... [a_tmem], b_desc).  The W X kernel then no longer
+// writes Z hi/lo planes (4 bytes per particle element per step less HBM
+// traffic), and shared memory carries only B for the MMAs.  The split is the
+// one the W X epilogue would have written, so results are bitwise those of
+// the plane-fed kernels.
+constexpr int kPairF32Stages = 3;
+
+struct PairF32Plan {
+    static constexpr int kZBox = 128 * 32 * 4;  // one 32-column FP32 box of this CTA's 128 rows
+    static constexpr int kB = 128 * BK * 2;     // this CTA's 128 rows of B, one plane
+    static constexpr int kStage = 2 * kZBox + 2 * kB;
+    static constexpr int kBarOff = kStage * kPairF32Stages;
+    static constexpr int kBytes = kBarOff + 256 + 1024;
+    static_assert(kBytes <= 227 * 1024, "shared memory plan too large");
+};
+constexpr int kPairF32TmemCols = 512;   // accumulator 0-255, A slots 256 + 64 s (hi 32, lo 32)
+
+__device__ __forceinline__ void mma_bf16_pair_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                                 uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    __syncwarp();
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_k, __nv_bfloat16 hi_k) {
+    return static_cast<uint32_t>(__bfloat16_as_ushort(lo_k)) |
+           (static_cast<uint32_t>(__bfloat16_as_ushort(hi_k)) << 16);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGramThreads, 1)
+k_gram_tc_pair_f32(const __grid_constant__ CUtensorMap z32, const __grid_constant__ CUtensorMap unused,
+                   const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
+    using P = PairF32Plan;
+    constexpr int S = kPairF32Stages;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    uint8_t *tiles = smem_raw + pad;
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
+    uint64_t *empty = full + S;
+    uint64_t *aready = empty + S;
+    uint64_t *accum = aready + S;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *skip_own = abort_flag + 1;
+    volatile int *skip_pair = abort_flag + 2;
+    (void)unused;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+    const int m_own = (blockIdx.x >> 1) * kPairTile + static_cast<int>(rank) * 128;
+    const int n0 = blockIdx.y * kPairTile;
+    const int n_own = n0 + static_cast<int>(rank) * 128;
+    const int split = blockIdx.z;
+    const int kb0 = split * p.kb_per_split;
+    int nkb = min(p.kblocks, kb0 + p.kb_per_split) - kb0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&aready[s], leader ? 5 : 4);  // four converting warps (+ the peer's forward)
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        *skip_own = *reinterpret_cast<volatile int *>(p.err) != 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc_pair(tmem_slot, kPairF32TmemCols);
+    tc_fence_before();
+    cluster_sync_all();
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+        uint32_t peer_flag = mapa_shared(smem_u32(const_cast<int *>(skip_own)), rank ^ 1u);
+        int other;
+        asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(other) : "r"(peer_flag) : "memory");
+        *skip_pair = (*skip_own | other) != 0;
+    }
+    __syncthreads();
+    const bool skip = *skip_pair != 0;
+    if (skip) nkb = 0;
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % S;
+                const uint32_t ph = (i / S) & 1;
+                if (!mbar_wait_cl(&empty[s], ph ^ 1u, abort_flag, p.err)) break;
+                const uint32_t st = smem_u32(tiles + s * P::kStage);
+                mbar_expect_tx(&full[s], P::kStage);
+                const int kx = (kb0 + i) * BK;
+                tma_load_2d(st, &z32, &full[s], kx, m_own);
+                tma_load_2d(st + P::kZBox, &z32, &full[s], kx + 32, m_own);
+                tma_load_2d(st + 2 * P::kZBox, &b_hi, &full[s], kx, n_own);
+                tma_load_2d(st + 2 * P::kZBox + P::kB, &b_lo, &full[s], kx, n_own);
+                issued = i + 1;
+            }
+            if (*abort_flag) {
+                const uint64_t t0 = globaltimer();
+                for (int i = issued > S ? issued - S : 0; i < issued; ++i) {
+                    const int s = i % S;
+                    while (!mbar_try_wait(&full[s], (i / S) & 1) && globaltimer() - t0 < kTimeoutNs) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            if (leader) {
+                constexpr uint32_t idesc = idesc_bf16(2 * BM, kPairTile);
+                for (int i = 0; i < nkb; ++i) {
+                    const int s = i % S;
+                    const uint32_t ph = (i / S) & 1;
+                    if (!mbar_wait_cl(&aready[s], ph, abort_flag, p.err)) break;
+                    tc_fence_after();
+                    const uint32_t a_hi = tmem + 256 + 64 * s;
+                    const uint32_t b0 = smem_u32(tiles + s * P::kStage + 2 * P::kZBox);
+                    const uint32_t b1 = b0 + P::kB;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t ta = a_hi + 8 * kk;  // 16 BF16 = 8 columns per K = 16 chunk
+                        const uint32_t off = kk * 32;
+                        mma_bf16_pair_ta(tmem, ta, desc_sw128(b0 + off), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16_pair_ta(tmem, ta, desc_sw128(b1 + off), idesc, 1u);
+                        mma_bf16_pair_ta(tmem, ta + 32, desc_sw128(b0 + off), idesc, 1u);
+                    }
+                    mma_commit_pair(&empty[s]);
+                }
+                mma_commit_pair(accum);
+            } else {
+                // forward this CTA's A-ready signals to the leader
+                for (int i = 0; i < nkb; ++i) {
+                    const int s = i % S;
+                    if (!mbar_wait(&aready[s], (i / S) & 1, abort_flag, p.err)) break;
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&aready[s]), 0));
+                }
+            }
+        }
+    } else if (warp < 6) {
+        const int q = warp & 3;        // TMEM lane quarter of this warp
+        const int r = q * 32 + lane;   // this thread's row within the CTA's 128
+        const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % S;
+            if (!mbar_wait(&full[s], (i / S) & 1, abort_flag, p.err)) break;
+            const uint8_t *zt = tiles + s * P::kStage;
+            const int64_t kx = static_cast<int64_t>(kb0 + i) * BK;
+            uint32_t hw[32], lw[32];
+#pragma unroll
+            for (int box = 0; box < 2; ++box) {
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    // 128-byte swizzle: 16-byte chunk ch of row r sits at chunk ch ^ (r & 7)
+                    const float4 v = *reinterpret_cast<const float4 *>(zt + box * P::kZBox + r * 128 +
+                                                                       ((ch ^ (r & 7)) << 4));
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+                    __nv_bfloat16 h[4], l[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int64_t c = kx + box * 32 + ch * 4 + e;
+                        float a = 0.f;
+                        if (c < p.d) {
+                            const float shift = p.centre ? __fmul_rn(p.alpha, __ldg(p.centre + c)) : 0.f;
+                            a = __fsub_rn(vv[e], shift);
+                        }
+                        h[e] = __float2bfloat16_rn(a);
+                        l[e] = __float2bfloat16_rn(__fsub_rn(a, __bfloat162float(h[e])));
+                    }
+                    const int w = box * 16 + ch * 2;
+                    hw[w] = pack_bf16x2(h[0], h[1]);
+                    hw[w + 1] = pack_bf16x2(h[2], h[3]);
+                    lw[w] = pack_bf16x2(l[0], l[1]);
+                    lw[w + 1] = pack_bf16x2(l[2], l[3]);
+                }
+            }
+            const uint32_t ta = tmem + lane_base + 256 + 64 * s;
+            tmem_st32(ta, hw);
+            tmem_st32(ta + 32, lw);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&aready[s]);
+        }
+        if (nkb > 0) {
+            const int row = m_own + r;
+            const bool ok = mbar_wait_cl(accum, 0, abort_flag, p.err);
+            tc_fence_after();
+            if (ok) {
+                float *dst = p.partial + (static_cast<int64_t>(split) * p.n + row) * p.n_x;
+#pragma unroll 1
+                for (int cc = 0; cc < kPairTile; cc += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + lane_base + cc, v);
+                    const int col0 = n0 + cc;
+                    if (row < p.n && col0 < p.n_x) {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)
+                            if (col0 + e < p.n_x) dst[col0 + e] = v[e];
+                    }
+                }
+            }
+        }
+    } else {
+        if (p.noise && !skip) gram_noise_share(p);
+    }
+    tc_fence_before();
+    cluster_sync_all();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, kPairF32TmemCols);
+    }
+}
+
 // ------------------------------------------------------- W X + EM update
 // Persistent kernel over tiles of U^T = X^T W^T: MMA rows (TMEM lanes) are 128
 // state columns c, MMA columns are BN particles i.  An epilogue thread owns one
@@ -728,9 +974,6 @@ struct WxParams {
     int *err;
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 template <int BN, int STAGES, bool SPLIT, bool INLINE_NOISE>
 __global__ void __launch_bounds__(kWxThreads, 1)
@@ -853,7 +1096,7 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
             const bool cok = c < p.d;
             const float yc = cok ? p.y[c] : 0.f;
             const bool obs = cok && (p.mask == nullptr || p.mask[c] != 0);
-            const float shift = (cok && p.centre) ? p.alpha_next * p.centre[c] : 0.f;
+            const float shift = (cok && p.centre) ? __fmul_rn(p.alpha_next, p.centre[c]) : 0.f;
 #pragma unroll 1
             for (int cc = part * kCols; cc < (part + 1) * kCols; cc += 16) {
                 float u[16];
@@ -889,7 +1132,7 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
                     const int64_t off = base + e * p.d;
                     p.z[off] = zn;
                     if (p.zb_hi) {
-                        const float zc = zn - shift;
+                        const float zc = __fsub_rn(zn, shift);  // rounded as the FP32-operand Gram rounds it
                         const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
                         p.zb_hi[off] = hi;
                         if (p.zb_lo) p.zb_lo[off] = __float2bfloat16_rn(zc - __bfloat162float(hi));
@@ -1088,7 +1331,7 @@ k_wx_em_tc_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__restri
             const bool cok = c < I.d;
             const float yc = cok ? I.y[c] : 0.f;
             const bool obs = cok && (I.mask == nullptr || I.mask[c] != 0);
-            const float shift = cok ? alpha_next * I.centre[c] : 0.f;
+            const float shift = cok ? __fmul_rn(alpha_next, I.centre[c]) : 0.f;
 #pragma unroll 1
             for (int cc = part * kCols; cc < (part + 1) * kCols; cc += 16) {
                 float u[16];
@@ -1120,7 +1363,7 @@ k_wx_em_tc_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__restri
                     const float zn = em_update(cf, zv[e], u[e], g, xi[e]);
                     const int64_t off = base_off + e * I.d;
                     I.z[off] = zn;
-                    const float zc = zn - shift;
+                    const float zc = __fsub_rn(zn, shift);
                     const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
                     I.zb_hi[off] = hi;
                     if (I.zb_lo) I.zb_lo[off] = __float2bfloat16_rn(zc - __bfloat162float(hi));
@@ -1193,6 +1436,20 @@ cudaError_t make_map(const TcContext *ctx, CUtensorMap *m, const void *base, int
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 2-D FP32 tensor map rows x cols (cols contiguous, pitch = cols), box of 32
+// columns (128 bytes) x box_rows rows with the 128-byte swizzle, zero fill.
+cudaError_t make_map_f32(const TcContext *ctx, CUtensorMap *m, const float *base, int64_t cols, int64_t rows,
+                         int box_rows) {
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * 4};
+    cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = ctx->encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <class K>
 cudaError_t set_smem(K kernel, int bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1205,6 +1462,13 @@ cudaError_t run_gram(const CUtensorMap (&maps)[4], const GramParams &p, dim3 gri
     cudaError_t e = set_smem(kern, P::kBytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, kGramThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
+    return cudaGetLastError();
+}
+
+cudaError_t run_gram_pair_f32(const CUtensorMap (&maps)[4], const GramParams &p, dim3 grid, cudaStream_t s) {
+    cudaError_t e = set_smem(k_gram_tc_pair_f32, PairF32Plan::kBytes);
+    if (e != cudaSuccess) return e;
+    k_gram_tc_pair_f32<<<grid, kGramThreads, PairF32Plan::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
     return cudaGetLastError();
 }
 
@@ -1265,13 +1529,20 @@ cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const Gram
     // the pair Gram needs whole 256-row tiles on both sides (no tile of a CTA
     // lies entirely outside the operands)
     const bool pair = ch.pair && a.split3 && a.n % kPairTile == 0 && a.n_x % kPairTile == 0;
+    const bool f32a = pair && ch.a_fp32 && a.z32 != nullptr;
     const int BN = pair ? kPairTile : ch.bn;
     const int KB = pair ? BK : (ch.bk == 32 ? 32 : BK);
     const int box_a = BM, box_b = pair ? 128 : BN;
     CUtensorMap maps[4];
     cudaError_t e;
-    if ((e = make_map(ctx, &maps[0], a.zb_hi, a.d, a.n, a.d, BM, KB)) != cudaSuccess) return e;
-    if ((e = make_map(ctx, &maps[1], a.split3 ? a.zb_lo : nullptr, a.d, a.n, a.d, BM, KB)) != cudaSuccess) return e;
+    if (f32a) {
+        if ((e = make_map_f32(ctx, &maps[0], a.z32, a.d, a.n, BM)) != cudaSuccess) return e;
+        memset(&maps[1], 0, sizeof(maps[1]));
+    } else {
+        if ((e = make_map(ctx, &maps[0], a.zb_hi, a.d, a.n, a.d, BM, KB)) != cudaSuccess) return e;
+        if ((e = make_map(ctx, &maps[1], a.split3 ? a.zb_lo : nullptr, a.d, a.n, a.d, BM, KB)) != cudaSuccess)
+            return e;
+    }
     if ((e = make_map(ctx, &maps[2], a.xb_hi, a.d, a.n_x, a.d, box_b, KB)) != cudaSuccess) return e;
     if ((e = make_map(ctx, &maps[3], a.split3 ? a.xb_lo : nullptr, a.d, a.n_x, a.d, box_b, KB)) != cudaSuccess) return e;
     (void)box_a;
@@ -1293,11 +1564,14 @@ cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const Gram
     p.offset = a.offset;
     p.noise_k = a.noise_k;
     p.d = a.d;
-    p.noise_warp0 = ch.noise_warps == 4 ? 6 : 2;
+    p.noise_warp0 = (ch.noise_warps == 4 || f32a) ? 6 : 2;  // the FP32 form's warps 2-5 split A
+    p.alpha = a.alpha;
+    p.centre = a.centre;
     *splits = S;
     *part_stride = per_split;
     *ldp = a.n_x;
     dim3 grid(mt, nt, S);
+    if (f32a) return run_gram_pair_f32(maps, p, grid, s);
     if (pair) return run_gram_pair(maps, p, grid, s);  // mt = 2 x pair tiles: one CTA per 128 rows
     if (KB == 32) {  // narrow k-blocks: twice the ring depth for the same bytes in flight
         if (a.split3) {
@@ -1398,11 +1672,19 @@ cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3
         return cudaErrorInvalidValue;
     std::lock_guard<std::mutex> lock(ctx->mu);
     if (g.noise_warps != 0 && g.noise_warps != 4 && g.noise_warps != 8) return cudaErrorInvalidValue;
+    if (g.a_fp32 && !g.pair) return cudaErrorInvalidValue;
     GramChoice c = g;
     c.bk = bk;
     ctx->gram_tuned[std::make_tuple(n, n_x, d, split3)] = c;
     if (wx_bn) ctx->wx_tuned[std::make_tuple(n, d, wx_split)] = wx_bn;
     return cudaSuccess;
+}
+
+bool tc_gram_reads_fp32(TcContext *ctx, int n, int n_x, int64_t d, bool split3) {
+    if (!ctx || !split3 || n % kPairTile != 0 || n_x % kPairTile != 0) return false;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->gram_tuned.find(std::make_tuple(n, n_x, d, split3));
+    return it != ctx->gram_tuned.end() && it->second.pair && it->second.a_fp32;
 }
 
 cudaError_t tc_encode_map(TcContext *ctx, void *out128, const void *base, int64_t cols, int64_t rows, int64_t pitch,
@@ -1488,6 +1770,52 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
                         TcTuneReport *rep, AfterGram after_gram, void *after_ctx) {
     if (!ctx) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
+    float wx_saving = 0.f;
+    if (w) {
+        const bool split = w->wb_lo != nullptr && w->xt_lo != nullptr;
+        int best_bn = 0;
+        float best_ms = 1e30f;
+        for (int bn : {64, 128, 256}) {
+            TcWxArgs a = *w;
+            a.force_bn = bn;
+            float ms = 0.f;
+            e = time_launches([&] { return launch_wx_em_tc(ctx, a, sms, s); }, 3, s, &ms);
+            if (e != cudaSuccess) return e;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_bn = bn;
+            }
+        }
+        {
+            std::lock_guard<std::mutex> lock(ctx->mu);
+            ctx->wx_tuned[std::make_tuple(w->n, w->d, split)] = best_bn;
+        }
+        if (rep) {
+            rep->wx_bn = best_bn;
+            rep->wx_ms = best_ms;
+        }
+        // what W X saves when it need not write the BF16 particle planes (the
+        // Gram form that splits the FP32 particles itself)
+        if (w->zb_hi) {
+            TcWxArgs a = *w;  // without the planes
+            a.force_bn = best_bn;
+            a.zb_hi = a.zb_lo = nullptr;
+            TcWxArgs b = *w;  // with them
+            b.force_bn = best_bn;
+            float with = 0.f, without = 0.f;
+            for (int pass = 0; pass < 2; ++pass) {
+                float t1 = 0.f, t2 = 0.f;
+                if ((e = time_launches([&] { return launch_wx_em_tc(ctx, b, sms, s); }, 5, s, &t1)) != cudaSuccess)
+                    return e;
+                if ((e = time_launches([&] { return launch_wx_em_tc(ctx, a, sms, s); }, 5, s, &t2)) != cudaSuccess)
+                    return e;
+                with = pass ? std::min(with, t1) : t1;
+                without = pass ? std::min(without, t2) : t2;
+            }
+            wx_saving = std::max(0.f, with - without);
+        }
+    }
+
     if (g) {
         // One timed launch of the Gram (with the softmax that consumes its partials).
         auto time_choice = [&](const GramChoice &ch, int reps, float *ms, int *splits_out) {
@@ -1510,9 +1838,11 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
             float ms;
         };
         std::vector<Cand> cands;
-        const int shapes[][4] = {{128, 3, 64, 0}, {256, 2, 64, 0}, {256, 3, 64, 1}};
+        // (tile width, ring depth, k-block width, CTA pair, FP32 particle operand)
+        const int shapes[][5] = {{128, 3, 64, 0, 0}, {256, 2, 64, 0, 0}, {256, 3, 64, 1, 0}, {256, 3, 64, 1, 1}};
         for (const auto &sh : shapes) {
-            const int bn = sh[0], kbw = sh[2], pr = sh[3];
+            const int bn = sh[0], kbw = sh[2], pr = sh[3], f32 = sh[4];
+            if (f32 && !(g->z32 && w && w->zb_hi)) continue;
             if (pr && !(g->split3 && g->n % kPairTile == 0 && g->n_x % kPairTile == 0)) continue;
             if (bn == 256 && g->n_x <= 128) continue;
             const int stages = g->split3 ? sh[1] : (bn == 256 ? 4 : 6);
@@ -1522,13 +1852,16 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
             for (int sp : {s0, std::max(1, s0 / 2), s0 * 2, std::max(1, (s0 * 3) / 4), (s0 * 3) / 2,
                            std::max(1, s0 / 4), std::max(1, s0 / 8)}) {
                 GramChoice ch{bn, stages, sp, kbw, pr};
+                ch.a_fp32 = f32;
                 float ms = 0.f;
                 int splits = 0;
                 if ((e = time_choice(ch, 3, &ms, &splits)) != cudaSuccess) return e;
+                if (f32) ms -= wx_saving;  // credited with the W X planes it makes unnecessary
                 ch.splits = splits;
                 bool dup = false;
                 for (const Cand &c : cands)
-                    dup |= c.ch.bn == ch.bn && c.ch.pair == ch.pair && c.ch.splits == ch.splits;
+                    dup |= c.ch.bn == ch.bn && c.ch.pair == ch.pair && c.ch.splits == ch.splits &&
+                           c.ch.a_fp32 == ch.a_fp32;
                 if (!dup) cands.push_back({ch, ms});
             }
         }
@@ -1547,6 +1880,7 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
                 float ms = 0.f;
                 int splits = 0;
                 if ((e = time_choice(c.ch, 10, &ms, &splits)) != cudaSuccess) return e;
+                if (c.ch.a_fp32) ms -= wx_saving;
                 c.ms = std::min(c.ms, ms);
             }
         GramChoice best = default_gram_choice(*g);
@@ -1564,30 +1898,9 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
             rep->gram_splits = best.splits;
             rep->gram_bk = best.bk ? best.bk : BK;
             rep->gram_pair = best.pair;
-            rep->gram_noise_warps = best.noise_warps ? best.noise_warps : 8;
+            rep->gram_noise_warps = best.a_fp32 ? 4 : (best.noise_warps ? best.noise_warps : 8);
+            rep->gram_a_fp32 = best.a_fp32;
             rep->gram_ms = best_ms;
-        }
-    }
-    if (w) {
-        const bool split = w->wb_lo != nullptr && w->xt_lo != nullptr;
-        int best_bn = 0;
-        float best_ms = 1e30f;
-        for (int bn : {64, 128, 256}) {
-            TcWxArgs a = *w;
-            a.force_bn = bn;
-            float ms = 0.f;
-            e = time_launches([&] { return launch_wx_em_tc(ctx, a, sms, s); }, 3, s, &ms);
-            if (e != cudaSuccess) return e;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_bn = bn;
-            }
-        }
-        std::lock_guard<std::mutex> lock(ctx->mu);
-        ctx->wx_tuned[std::make_tuple(w->n, w->d, split)] = best_bn;
-        if (rep) {
-            rep->wx_bn = best_bn;
-            rep->wx_ms = best_ms;
         }
     }
     return cudaSuccess;

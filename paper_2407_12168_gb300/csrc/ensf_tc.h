@@ -19,10 +19,12 @@ struct GramChoice {
     int bk = 0;      // k-block width: 64 (128-byte swizzle) or 32 (64-byte swizzle); 0 = 64
     int pair = 0;    // 1: a cluster of two CTAs per 256 x 256 tile (tcgen05 cta_group::2)
     int noise_warps = 0;  // warps generating the next step's noise: 8 (default) or 4
+    int a_fp32 = 0;       // pair form only: read the FP32 particles and split them in the kernel
 };
 
 struct TcTuneReport {
     int gram_bn = 0, gram_stages = 0, gram_splits = 0, gram_bk = 0, gram_pair = 0, gram_noise_warps = 0;
+    int gram_a_fp32 = 0;
     float gram_ms = 0.f;
     int wx_bn = 0;
     float wx_ms = 0.f;
@@ -49,6 +51,11 @@ struct TcGramArgs {
     uint64_t seed;
     uint32_t offset;
     int noise_k;
+    // the FP32 particles [n][d] and the centre, for the form that splits
+    // z - alpha * centre itself (NULL: only the BF16 planes are available)
+    const float *z32 = nullptr;
+    const float *centre = nullptr;
+    float alpha = 0.f;
 };
 
 struct TcWxArgs {
@@ -131,6 +138,9 @@ using AfterGram = cudaError_t (*)(void *ctx, int splits, int64_t part_stride, in
 // compiled kernel.
 cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3, const GramChoice &g, int wx_bn,
                           bool wx_split);
+// True when the tuned Gram for this shape reads the FP32 particles (the W X
+// epilogue then need not write the BF16 particle planes).
+bool tc_gram_reads_fp32(TcContext *ctx, int n, int n_x, int64_t d, bool split3);
 cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, int sms, cudaStream_t s,
                         TcTuneReport *rep, AfterGram after_gram = nullptr, void *after_ctx = nullptr);
 

@@ -59,6 +59,13 @@ def test_row_norms_fp64():
     x = np.random.default_rng(0).standard_normal((37, 1032)).astype(np.float32)
     got = ensf.row_norms(torch.from_numpy(x).cuda()).cpu().numpy()
     np.testing.assert_allclose(got, np.sum(x.astype(np.float64) ** 2, axis=1), rtol=1e-13)
+    # long rows with a large offset: thousands of terms per thread, where an
+    # FP32 running sum would lose about ten digits
+    # (a plain FP64 running sum over the same 2048 terms per thread is good to
+    # about 1e-13 here as well)
+    x = (30.0 + np.random.default_rng(1).standard_normal((4, 524288))).astype(np.float32)
+    got = ensf.row_norms(torch.from_numpy(x).cuda()).cpu().numpy()
+    np.testing.assert_allclose(got, np.sum(x.astype(np.float64) ** 2, axis=1), rtol=1e-12)
 
 
 def test_ensemble_stats_fp64():
@@ -451,20 +458,25 @@ def test_pair_gram_matches_single_cta_bitwise():
     prior, y = torch.from_numpy(p.prior).cuda(), torch.from_numpy(p.y).cuda()
     mask = torch.from_numpy(p.mask).cuda()
     outs = []
-    # (pair, tile width, ring depth, warps generating the next step's noise)
-    for pair, bn, stages, nw in [(0, 256, 2, 8), (1, 256, 3, 8), (0, 128, 3, 8), (1, 256, 3, 4), (0, 256, 2, 4)]:
+    # (pair, tile width, ring depth, warps generating the next step's noise,
+    #  Gram reading the FP32 particles and splitting them itself)
+    for pair, bn, stages, nw, f32 in [(0, 256, 2, 8, 0), (1, 256, 3, 8, 0), (0, 128, 3, 8, 0), (1, 256, 3, 4, 0),
+                                      (0, 256, 2, 4, 0), (1, 256, 3, 4, 1)]:
         f = ensf.Filter(p.n, p.d, gram="split", wx="bf16", check_finite=True)
-        f.set_tuning(p.n, p.d, bn, stages, gram_splits=2, gram_cta_pair=pair, gram_noise_warps=nw)
+        f.set_tuning(p.n, p.d, bn, stages, gram_splits=2, gram_cta_pair=pair, gram_noise_warps=nw,
+                     gram_fp32_particles=f32)
         outs.append(f.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed).cpu().numpy())
         assert f.status_sync() == 0
     for o_ in outs[1:]:
         np.testing.assert_array_equal(o_, outs[0])
 
 
-def test_pair_gram_ragged_state_matches_oracle():
+@pytest.mark.parametrize("f32", [0, 1])
+def test_pair_gram_ragged_state_matches_oracle(f32):
     """One pair tile (N = 256), a ragged state tail (d = 2888 is not a
     multiple of the 64-wide k-block) and three uneven splits, against the
-    oracle."""
+    oracle; with the particle operand from BF16 planes or split in the
+    kernel from the FP32 particles."""
     torch = _torch()
     from paper_2407_12168_gb300 import ensf
     gram, wx, tol = PATHS["split"]
@@ -472,7 +484,7 @@ def test_pair_gram_ragged_state_matches_oracle():
     ref = run_oracle(p)
     cond = conditioning(p, ref, prec=_cond_prec(gram, wx))
     f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, check_finite=True)
-    f.set_tuning(p.n, p.d, 256, 3, gram_splits=3, gram_cta_pair=1)
+    f.set_tuning(p.n, p.d, 256, 3, gram_splits=3, gram_cta_pair=1, gram_fp32_particles=f32)
     got = _gpu_analysis(p, gram, wx, filt=f)
     rel, tie, bad = compare_members(got, ref, cond, tol)
     assert not bad.any(), describe(rel, tie, bad)
