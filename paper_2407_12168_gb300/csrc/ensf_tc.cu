@@ -375,7 +375,7 @@ __device__ __forceinline__ void gram_noise_share(const GramParams &p) {
     const int64_t c1 = c0 + per < p.d ? c0 + per : p.d;
     const int quads = (p.n + 3) / 4;
     const int et = threadIdx.x - 32 * p.noise_warp0;
-    const int kStride = kGramThreads - 32 * p.noise_warp0;
+    const int kStride = static_cast<int>(blockDim.x) - 32 * p.noise_warp0;
     for (int qd = 0; qd < quads; ++qd) {
         for (int64_t col = c0 + et; col < c1; col += 2 * kStride) {
             const int64_t col2 = col + kStride;
@@ -712,6 +712,11 @@ struct PairF32Plan {
     static_assert(kBytes <= 227 * 1024, "shared memory plan too large");
 };
 constexpr int kPairF32TmemCols = 512;   // accumulator 0-255, A slots 256 + 64 s (hi 32, lo 32)
+// warps: 0 producer, 1 MMA issuer (leader) / forwarder (peer), 2-9 split the
+// particle operand (warp w: TMEM lane quarter w % 4, 32-column box (w - 2) / 4)
+// and then run the epilogue, 10-15 generate the next step's noise
+constexpr int kPairF32Threads = 512;
+constexpr int kPairF32Convert = 8;
 
 __device__ __forceinline__ void mma_bf16_pair_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                                  uint32_t acc) {
@@ -723,17 +728,14 @@ __device__ __forceinline__ void mma_bf16_pair_ta(uint32_t d_tmem, uint32_t a_tme
         : "memory");
 }
 
-// 32 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
     __syncwarp();
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
         "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
-        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
-        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
         : "memory");
 }
 
@@ -742,7 +744,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_k, __nv_bfloat1
            (static_cast<uint32_t>(__bfloat16_as_ushort(hi_k)) << 16);
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGramThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairF32Threads, 1)
 k_gram_tc_pair_f32(const __grid_constant__ CUtensorMap z32, const __grid_constant__ CUtensorMap unused,
                    const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
     using P = PairF32Plan;
@@ -774,7 +776,7 @@ k_gram_tc_pair_f32(const __grid_constant__ CUtensorMap z32, const __grid_constan
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&aready[s], leader ? 5 : 4);  // four converting warps (+ the peer's forward)
+            mbar_init(&aready[s], leader ? kPairF32Convert + 1 : kPairF32Convert);  // (+ the peer's forward)
         }
         mbar_init(accum, 1);
         *abort_flag = 0;
@@ -854,66 +856,69 @@ k_gram_tc_pair_f32(const __grid_constant__ CUtensorMap z32, const __grid_constan
                 }
             }
         }
-    } else if (warp < 6) {
-        const int q = warp & 3;        // TMEM lane quarter of this warp
-        const int r = q * 32 + lane;   // this thread's row within the CTA's 128
+    } else if (warp < 2 + kPairF32Convert) {
+        const int q = warp & 3;             // TMEM lane quarter of this warp
+        const int box = (warp - 2) >> 2;    // which 32-column half of the k-block
+        const int r = q * 32 + lane;        // this thread's row within the CTA's 128
         const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
         for (int i = 0; i < nkb; ++i) {
             const int s = i % S;
             if (!mbar_wait(&full[s], (i / S) & 1, abort_flag, p.err)) break;
-            const uint8_t *zt = tiles + s * P::kStage;
-            const int64_t kx = static_cast<int64_t>(kb0 + i) * BK;
-            uint32_t hw[32], lw[32];
+            // alpha m for the 32 columns of this box: one coalesced load per
+            // warp, handed to every lane by shuffles
+            const int64_t c_lane = static_cast<int64_t>(kb0 + i) * BK + box * 32 + lane;
+            const float shift_lane =
+                (p.centre && c_lane < p.d) ? __fmul_rn(p.alpha, __ldg(p.centre + c_lane)) : 0.f;
+            const bool tail = static_cast<int64_t>(kb0 + i) * BK + box * 32 + 32 > p.d;
+            const uint8_t *zrow = tiles + s * P::kStage + box * P::kZBox + r * 128;
+            float4 v[8];
 #pragma unroll
-            for (int box = 0; box < 2; ++box) {
+            for (int ch = 0; ch < 8; ++ch)  // 128-byte swizzle: chunk ch of row r sits at ch ^ (r & 7)
+                v[ch] = *reinterpret_cast<const float4 *>(zrow + ((ch ^ (r & 7)) << 4));
+            uint32_t hw[16], lw[16];
 #pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    // 128-byte swizzle: 16-byte chunk ch of row r sits at chunk ch ^ (r & 7)
-                    const float4 v = *reinterpret_cast<const float4 *>(zt + box * P::kZBox + r * 128 +
-                                                                       ((ch ^ (r & 7)) << 4));
-                    const float vv[4] = {v.x, v.y, v.z, v.w};
-                    __nv_bfloat16 h[4], l[4];
+            for (int ch = 0; ch < 8; ++ch) {
+                const float vv[4] = {v[ch].x, v[ch].y, v[ch].z, v[ch].w};
+                __nv_bfloat16 h[4], l[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int64_t c = kx + box * 32 + ch * 4 + e;
-                        float a = 0.f;
-                        if (c < p.d) {
-                            const float shift = p.centre ? __fmul_rn(p.alpha, __ldg(p.centre + c)) : 0.f;
-                            a = __fsub_rn(vv[e], shift);
-                        }
-                        h[e] = __float2bfloat16_rn(a);
-                        l[e] = __float2bfloat16_rn(__fsub_rn(a, __bfloat162float(h[e])));
-                    }
-                    const int w = box * 16 + ch * 2;
-                    hw[w] = pack_bf16x2(h[0], h[1]);
-                    hw[w + 1] = pack_bf16x2(h[2], h[3]);
-                    lw[w] = pack_bf16x2(l[0], l[1]);
-                    lw[w + 1] = pack_bf16x2(l[2], l[3]);
+                for (int e = 0; e < 4; ++e) {
+                    const int j = ch * 4 + e;
+                    const float sh = __shfl_sync(0xffffffffu, shift_lane, j);
+                    // past the end of the state the tile holds zeros: keep them
+                    const bool in = !tail || (static_cast<int64_t>(kb0 + i) * BK + box * 32 + j < p.d);
+                    const float a = in ? __fsub_rn(vv[e], sh) : 0.f;
+                    h[e] = __float2bfloat16_rn(a);
+                    l[e] = __float2bfloat16_rn(__fsub_rn(a, __bfloat162float(h[e])));
                 }
+                hw[ch * 2] = pack_bf16x2(h[0], h[1]);
+                hw[ch * 2 + 1] = pack_bf16x2(h[2], h[3]);
+                lw[ch * 2] = pack_bf16x2(l[0], l[1]);
+                lw[ch * 2 + 1] = pack_bf16x2(l[2], l[3]);
             }
-            const uint32_t ta = tmem + lane_base + 256 + 64 * s;
-            tmem_st32(ta, hw);
-            tmem_st32(ta + 32, lw);
+            const uint32_t ta = tmem + lane_base + 256 + 64 * s + 16 * box;
+            tmem_st16(ta, hw);
+            tmem_st16(ta + 32, lw);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&aready[s]);
         }
         if (nkb > 0) {
+            // epilogue: the two warps of a lane quarter take 128 columns each
             const int row = m_own + r;
             const bool ok = mbar_wait_cl(accum, 0, abort_flag, p.err);
             tc_fence_after();
             if (ok) {
                 float *dst = p.partial + (static_cast<int64_t>(split) * p.n + row) * p.n_x;
 #pragma unroll 1
-                for (int cc = 0; cc < kPairTile; cc += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + lane_base + cc, v);
+                for (int cc = box * 128; cc < box * 128 + 128; cc += 32) {
+                    float o[32];
+                    tmem_ld32(tmem + lane_base + cc, o);
                     const int col0 = n0 + cc;
                     if (row < p.n && col0 < p.n_x) {
 #pragma unroll
                         for (int e = 0; e < 32; ++e)
-                            if (col0 + e < p.n_x) dst[col0 + e] = v[e];
+                            if (col0 + e < p.n_x) dst[col0 + e] = o[e];
                     }
                 }
             }
@@ -1468,7 +1473,7 @@ cudaError_t run_gram(const CUtensorMap (&maps)[4], const GramParams &p, dim3 gri
 cudaError_t run_gram_pair_f32(const CUtensorMap (&maps)[4], const GramParams &p, dim3 grid, cudaStream_t s) {
     cudaError_t e = set_smem(k_gram_tc_pair_f32, PairF32Plan::kBytes);
     if (e != cudaSuccess) return e;
-    k_gram_tc_pair_f32<<<grid, kGramThreads, PairF32Plan::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
+    k_gram_tc_pair_f32<<<grid, kPairF32Threads, PairF32Plan::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
     return cudaGetLastError();
 }
 
@@ -1564,7 +1569,8 @@ cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const Gram
     p.offset = a.offset;
     p.noise_k = a.noise_k;
     p.d = a.d;
-    p.noise_warp0 = (ch.noise_warps == 4 || f32a) ? 6 : 2;  // the FP32 form's warps 2-5 split A
+    // the FP32 form's warps 2-9 split A and warps 10-15 generate the noise
+    p.noise_warp0 = f32a ? 2 + kPairF32Convert : (ch.noise_warps == 4 ? 6 : 2);
     p.alpha = a.alpha;
     p.centre = a.centre;
     *splits = S;
