@@ -381,7 +381,8 @@ def run_ours(args):
     y = torch.from_numpy(p.y).to(dev)
     mask = torch.from_numpy(p.mask).to(dev) if p.mask is not None else None
     out = torch.empty_like(prior)
-    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, graph=args.graph, inline_noise=args.inline_noise)
+    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, graph=args.graph, inline_noise=args.inline_noise,
+                    persistent=args.persistent)
     stream = torch.cuda.current_stream()
     tuning = None
     if gram != "fp32" or wx != "fp32":
@@ -454,19 +455,19 @@ def run_ours(args):
     d_prior.copy_(h_prior, non_blocking=True)
     h_out.copy_(d_prior, non_blocking=True)
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as e2e_clk:
-        for s_ in range(e2e_steps):
-            if flush is not None:
-                flush.zero_()
-            ee[s_][0].record(stream)
-            d_prior.copy_(h_prior, non_blocking=True)
-            d_y.copy_(h_y, non_blocking=True)
-            if d_mask is not None:
-                d_mask.copy_(h_mask, non_blocking=True)
-            analyse(d_prior, d_y, d_mask, 200 + s_)
-            h_out.copy_(out, non_blocking=True)
-            ee[s_][1].record(stream)
-        torch.cuda.synchronize()
+    # (no clock sampling in this loop: its driver queries slow the host copies)
+    for s_ in range(e2e_steps):
+        if flush is not None:
+            flush.zero_()
+        ee[s_][0].record(stream)
+        d_prior.copy_(h_prior, non_blocking=True)
+        d_y.copy_(h_y, non_blocking=True)
+        if d_mask is not None:
+            d_mask.copy_(h_mask, non_blocking=True)
+        analyse(d_prior, d_y, d_mask, 200 + s_)
+        h_out.copy_(out, non_blocking=True)
+        ee[s_][1].record(stream)
+    torch.cuda.synchronize()
     e2e_each = [a.elapsed_time(b) for a, b in ee]
     e2e_ms = float(sum(e2e_each)) / e2e_steps
     h2d = p.prior.nbytes + p.y.nbytes + (p.mask.nbytes if p.mask is not None else 0)
@@ -533,8 +534,9 @@ def run_ours(args):
             "roofline_other": other,
             "kernels": {k: {"launches": v[0], "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "clocks": e2e_clk.summary(), "ms_per_step": [round(v, 2) for v in e2e_each]},
-            "gpu_launches": gpu_launches, "clocks": clk.summary(), "tuning": tuning, "cuda_graph": args.graph}
+                    "ms_per_step": [round(v, 2) for v in e2e_each]},
+            "gpu_launches": gpu_launches, "clocks": clk.summary(), "tuning": tuning, "cuda_graph": args.graph,
+            "persistent": args.persistent}
     if not args.no_cpu_baseline:
         line["cpu_baseline"], oracle_out = cpu_baseline(p, args.cpu_budget_s, J or 0)
         if oracle_out is not None:
@@ -558,6 +560,8 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true", help="replay each analysis as one captured CUDA graph")
     ap.add_argument("--inline-noise", action="store_true",
                     help="tensor-core W X evaluates the noise in its epilogue (no pre-generated slice)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="fp32 path, N <= 128: all K steps in one cooperative launch")
     ap.add_argument("--minibatch", type=int, default=0, metavar="J",
                     help="mini-batch prior score over J members per Euler-Maruyama step (tensor-core paths)")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)

@@ -72,6 +72,11 @@ typedef enum {
                                       the instantiated graph is kept in the handle and updated in
                                       place when only scalars or pointers change.  Ignored on the
                                       legacy default stream and inside a caller's own capture. */
+#define ENSF_FLAG_PERSISTENT 8u    /* FP32 precisions and n <= 128: the K Euler-Maruyama steps run in
+                                      one cooperative launch (one block per SM, three bounded grid
+                                      barriers per step) instead of three launches per step; for
+                                      small filters, whose step costs less than a kernel launch.
+                                      Other configurations ignore the flag. */
 
 typedef struct {
     int max_n;        /* largest ensemble size N this handle will run (>= 1)          */
@@ -263,6 +268,18 @@ ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, fl
  * nproc outside 1..8; ECUDA if the launch fails. */
 ensf_status ensf_model_error(float *state, int batch, int64_t d, const float *coef, int nproc, uint64_t seed,
                              uint32_t cycle, void *stream);
+
+/* Failure-detection self-test (no counterpart in the paper): runs the two
+ * kinds of bounded waits of the library against conditions that never occur
+ * and reports how they ended, without faulting or hanging the GPU.
+ *   words[0]: a tensor-core pipeline wait on an mbarrier that nothing completes;
+ *   words[1]: a grid barrier of the persistent small-filter kernel that one
+ *             block leaves without arriving at.
+ * words: device, 4 ints, caller-owned (words[2..3] are the barrier's scratch);
+ * words[0..1] are zeroed, the two kernels run (about two seconds each), and
+ * both should hold ENSF_ETIMEOUT after the stream completes.  The context
+ * stays usable.  EINVAL for NULL; ECUDA if a launch fails. */
+ensf_status ensf_selftest_timeouts(int *words, void *stream);
 
 /* Launch accounting of a handle.  Every kernel launch is counted by kind
  * ("row_norms", "init_particles", "split_bf16", "gram", "softmax_rows",

@@ -81,6 +81,8 @@ Layout make_layout(const ensf_config *c) {
     int64_t simt_cap = (2 * (int64_t)kSizingSMs + tiles_simt) * kSimtTile * kSimtTile;
     int64_t tc_cap = ensf::tc_partial_floats(c->max_n, kSizingSMs);
     L.partial_floats = std::max<int64_t>(std::max<int64_t>(simt_cap, tc_cap), N * N);
+    // the persistent small-filter path wants one partial Gram per block (SM)
+    if (N <= 128) L.partial_floats = std::max<int64_t>(L.partial_floats, (int64_t)kSizingSMs * N * N);
     L.partial = take(sizeof(float) * L.partial_floats);
     if (is_tc(c->gram) || is_tc(c->wx)) {
         const int64_t NP = round_up(N, 8);  // bf16 row pitch multiple of 16 bytes
@@ -438,6 +440,21 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
                              int J = 0) {
     const Layout &L = h->L;
     const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
+    if ((h->cfg.flags & ENSF_FLAG_PERSISTENT) && !tc_gram && !tc_wx && n <= 128 && !perm) {
+        // one cooperative launch for all K steps (small filters)
+        ensf_status st0 = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s);
+        if (st0 != ENSF_OK) return st0;
+        const double so = sigma_obs;
+        ENSF_LAUNCH(h, P_WXEM, s,
+                    ensf::launch_analysis_small(prior, h->at<double>(L.norms), h->at<float>(L.xbar), out, y, obs_mask,
+                                                n, d, K, (double)eps, (float)(1.0 / (so * so)), obs_op, noise->buf,
+                                                noise->seed, noise->offset, h->at<float>(L.partial), L.partial_floats,
+                                                h->at<float>(L.w), reinterpret_cast<unsigned *>(h->err() + 2),
+                                                h->err(), h->sms, s));
+        if (h->cfg.flags & ENSF_FLAG_CHECK_FINITE)
+            ENSF_LAUNCH(h, P_CHECK, s, ensf::launch_check_finite(out, (int64_t)n * d, h->err(), s));
+        return ENSF_OK;
+    }
 
     // The Gram runs on centred operands z - alpha m and x_j - m, m = the forecast
     // mean: |z - alpha x_j|^2 is unchanged, the magnitudes entering the expanded
@@ -716,6 +733,15 @@ ensf_status ensf_relax_spread(const float *prior, float *z, int n, int64_t d, fl
     if (!prior || !z || n < 2 || d < 1 || !(factor >= 0.0f && factor <= 1.0f) || (mode != 0 && mode != 1))
         return fail(ENSF_EINVAL, "ensf_relax_spread: bad arguments");
     ENSF_CUDA(ensf::launch_relax_spread(prior, z, n, d, factor, mode, static_cast<cudaStream_t>(stream)));
+    return ENSF_OK;
+}
+
+ensf_status ensf_selftest_timeouts(int *words, void *stream) {
+    if (!words) return fail(ENSF_EINVAL, "ensf_selftest_timeouts: NULL words");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ENSF_CUDA(cudaMemsetAsync(words, 0, 2 * sizeof(int), s));
+    ENSF_CUDA(ensf::launch_selftest_mbar_wait(words, s));
+    ENSF_CUDA(ensf::launch_selftest_grid_barrier(reinterpret_cast<unsigned *>(words + 2), words + 1, s));
     return ENSF_OK;
 }
 

@@ -88,7 +88,8 @@ __device__ __forceinline__ float em_update(const StepCoef &c, float z, float u, 
 }
 
 
-// One row i of the softmax of Eq. 16 from split-K partial Grams (block of 256
+// One row i of the softmax of Eq. 16 from split-K partial Grams (read through
+// L2 only: they may come from other blocks of the same launch; block of 256
 // threads; lg = n_x doubles of shared memory, red = 256 doubles):
 //   G_ij = sum_s partial[s][i][j]  (fixed order: deterministic),
 //   l_ij = (2 alpha G_ij - alpha^2 |x_j|^2) / (2 beta^2), w_ij = softmax_j(l_ij).
@@ -111,7 +112,7 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
     if (groups == 1) {
         for (int j = tid; j < n_x; j += 256) {
             double g = 0.0;
-            for (int s = 0; s < splits; ++s) g += (double)partial[s * part_stride + (int64_t)i * ldp + j];
+            for (int s = 0; s < splits; ++s) g += (double)__ldcg(partial + s * part_stride + (int64_t)i * ldp + j);
             double l = (2.0 * alpha * g - alpha * alpha * norms[j]) * inv_2beta2;
             lg[j] = l;
             lmax = fmax(lmax, l);
@@ -121,7 +122,7 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
         if (grp < groups) {
             double g = 0.0;
             const int s0 = grp * per, s1 = min(splits, s0 + per);
-            for (int s = s0; s < s1; ++s) g += (double)partial[s * part_stride + (int64_t)i * ldp + j];
+            for (int s = s0; s < s1; ++s) g += (double)__ldcg(partial + s * part_stride + (int64_t)i * ldp + j);
             red[grp * n_x + j] = g;
         }
         __syncthreads();

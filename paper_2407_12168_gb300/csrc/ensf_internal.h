@@ -55,6 +55,14 @@ cudaError_t launch_ensemble_stats(const float *z, int n, int64_t d, const float 
                                   double *mean, double *rmse, double *scratch, cudaStream_t s);
 int stats_blocks(int64_t d);
 
+// The whole analysis of a small filter (n <= 128, FP32) in one cooperative
+// launch; z holds xi_0 on entry.  bar: two zeroed-per-launch words.
+cudaError_t launch_analysis_small(const float *x, const double *norms, const float *centre, float *z, const float *y,
+                                  const uint8_t *mask, int n, int64_t d, int K, double eps, float inv_r, int obs_op,
+                                  const float *noise_buf, uint64_t seed, uint32_t offset, float *partial,
+                                  int64_t partial_floats, float *w, unsigned *bar, int *err, int sms,
+                                  cudaStream_t s);
+cudaError_t launch_selftest_grid_barrier(unsigned *bar, int *err, cudaStream_t s);
 cudaError_t launch_model_error(float *state, int batch, int64_t d, const float *coef, int nproc, uint64_t seed,
                                uint32_t cycle, cudaStream_t s);
 cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, int mode, cudaStream_t s);

@@ -1693,6 +1693,25 @@ bool tc_gram_reads_fp32(TcContext *ctx, int n, int n_x, int64_t d, bool split3) 
     return it != ctx->gram_tuned.end() && it->second.pair && it->second.a_fp32;
 }
 
+namespace {
+// One thread waits on an mbarrier that nothing completes, through the same
+// bounded wait as every pipeline wait of the tensor-core kernels.
+__global__ void k_selftest_mbar_wait(int *err) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0, &abort_flag, err)) return;  // records ENSF_ETIMEOUT after kTimeoutNs
+    atomicExch(err, -1);                                 // unreachable: the phase cannot complete
+}
+}  // namespace
+
+cudaError_t launch_selftest_mbar_wait(int *err, cudaStream_t s) {
+    k_selftest_mbar_wait<<<1, 1, 0, s>>>(err);
+    return cudaGetLastError();
+}
+
 cudaError_t tc_encode_map(TcContext *ctx, void *out128, const void *base, int64_t cols, int64_t rows, int64_t pitch,
                           int box_rows) {
     if (!ctx) return cudaErrorInvalidValue;

@@ -138,6 +138,8 @@ using AfterGram = cudaError_t (*)(void *ctx, int splits, int64_t part_stride, in
 // compiled kernel.
 cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3, const GramChoice &g, int wx_bn,
                           bool wx_split);
+// Failure-detection self-test: a bounded mbarrier wait that must run out.
+cudaError_t launch_selftest_mbar_wait(int *err, cudaStream_t s);
 // True when the tuned Gram for this shape reads the FP32 particles (the W X
 // epilogue then need not write the BF16 particle planes).
 bool tc_gram_reads_fp32(TcContext *ctx, int n, int n_x, int64_t d, bool split3);

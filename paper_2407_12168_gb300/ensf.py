@@ -21,6 +21,7 @@ OBS_IDENTITY, OBS_ARCTAN = 0, 1
 PREC_FP32, PREC_SPLIT_BF16X3, PREC_BF16 = 0, 1, 2
 FLAG_CHECK_FINITE = 1
 FLAG_CUDA_GRAPH = 2
+FLAG_PERSISTENT = 8
 FLAG_INLINE_NOISE = 4
 
 PRECISIONS = {"fp32": PREC_FP32, "split": PREC_SPLIT_BF16X3, "bf16": PREC_BF16}
@@ -104,6 +105,7 @@ _SIGNATURES = [
                                       ctypes.c_void_p]),
     ("ensf_relax_spread", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                                          ctypes.c_float, ctypes.c_int, ctypes.c_void_p]),
+    ("ensf_selftest_timeouts", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(EnsfTuning)]),
     ("ensf_model_error", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_float),
                                         ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
@@ -194,15 +196,18 @@ class Filter:
 
     ``gram`` and ``wx`` choose the arithmetic of the Gram Z X^T and of the
     weighted sum W X: ``"fp32"`` (CUDA cores), ``"split"`` (BF16x3 on tensor
-    cores) or ``"bf16"`` (one BF16 product on tensor cores)."""
+    cores) or ``"bf16"`` (one BF16 product on tensor cores).  ``persistent``:
+    with FP32 precisions and n <= 128, all K steps run in one cooperative
+    launch (small filters)."""
 
     def __init__(self, max_n: int, max_d: int, gram: str = "fp32", wx: str = "fp32",
-                 check_finite: bool = False, graph: bool = False, inline_noise: bool = False):
+                 check_finite: bool = False, graph: bool = False, inline_noise: bool = False,
+                 persistent: bool = False):
         torch = _torch()
         lib = load()
         self.cfg = EnsfConfig(int(max_n), int(max_d), PRECISIONS[gram], PRECISIONS[wx],
                               (FLAG_CHECK_FINITE if check_finite else 0) | (FLAG_CUDA_GRAPH if graph else 0)
-                              | (FLAG_INLINE_NOISE if inline_noise else 0))
+                              | (FLAG_INLINE_NOISE if inline_noise else 0) | (FLAG_PERSISTENT if persistent else 0))
         nbytes = lib.ensf_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise ValueError("invalid EnSF configuration")
@@ -506,6 +511,17 @@ def relax_spread(prior, z, factor: float = 1.0, mode: str = "spread", stream=Non
                                     {"spread": 0, "perturbations": 1}[mode], _stream_ptr(stream)),
            "ensf_relax_spread")
     return z
+
+
+def selftest_timeouts(stream=None):
+    """Run the library's two bounded-wait self-tests (an mbarrier that never
+    completes, a grid barrier that one block skips); returns the two status
+    words, both ETIMEOUT when detection works.  Takes about 4 s."""
+    torch = _torch()
+    words = torch.zeros(4, dtype=torch.int32, device="cuda")
+    _check(load().ensf_selftest_timeouts(words.data_ptr(), _stream_ptr(stream)), "ensf_selftest_timeouts")
+    torch.cuda.synchronize()
+    return [int(v) for v in words[:2].cpu()]
 
 
 def model_error(state, coef, seed: int, cycle: int, stream=None):

@@ -499,3 +499,27 @@ def test_pair_gram_needs_whole_pair_tiles():
     g = ensf.Filter(512, 4096, gram="bf16", wx="bf16")
     with pytest.raises(ensf.EnsfError):
         g.set_tuning(512, 4096, 256, 3, gram_cta_pair=1)
+
+
+@pytest.mark.parametrize("f32", [0, 1])
+def test_pair_gram_in_a_cuda_graph(f32):
+    """The cluster-launched pair Gram (both operand forms) captured in a CUDA
+    graph and replayed gives the eager bits, across a seed change (graph
+    update) and a repeat."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    p0 = inputs.small_case(seed=65, n=512, grid=40, layers=2, K=4, obs_op=1, obs_frac=0.5, sigma_obs=0.5)
+    eager = ensf.Filter(p0.n, p0.d, gram="split", wx="bf16")
+    graph = ensf.Filter(p0.n, p0.d, gram="split", wx="bf16", graph=True)
+    for f in (eager, graph):
+        f.set_tuning(p0.n, p0.d, 256, 3, gram_splits=3, gram_cta_pair=1, gram_fp32_particles=f32)
+    prior, y = torch.from_numpy(p0.prior).cuda(), torch.from_numpy(p0.y).cuda()
+    mask = torch.from_numpy(p0.mask).cuda()
+    stream = torch.cuda.Stream()
+    for seed in (1, 2, 2):
+        with torch.cuda.stream(stream):
+            a = eager.analysis(prior, y, mask, p0.sigma_obs, p0.K, p0.eps, p0.obs_op, seed=seed)
+            b = graph.analysis(prior, y, mask, p0.sigma_obs, p0.K, p0.eps, p0.obs_op, seed=seed)
+        stream.synchronize()
+        assert graph.status_sync() == 0
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
