@@ -385,7 +385,11 @@ def run_ours(args):
                     persistent=args.persistent)
     stream = torch.cuda.current_stream()
     tuning = None
-    if gram != "fp32" or wx != "fp32":
+    if args.set_tuning:
+        # fixed launch shapes (no autotuner launches before the measured ones)
+        tuning = dict(json.loads(args.set_tuning))
+        f.set_tuning(p.n, p.d, **tuning)
+    elif gram != "fp32" or wx != "fp32":
         tuning = f.autotune(prior, y, mask, p.sigma_obs, p.eps, p.obs_op, seed=p.seed, out=out)
     args.tuning = tuning
     small = p.n * p.d * 4 <= 256 << 20
@@ -560,6 +564,9 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true", help="replay each analysis as one captured CUDA graph")
     ap.add_argument("--inline-noise", action="store_true",
                     help="tensor-core W X evaluates the noise in its epilogue (no pre-generated slice)")
+    ap.add_argument("--set-tuning", default=None, metavar="JSON",
+                    help='launch shapes instead of the autotuner, e.g. {"gram_tile_n": 256, "gram_stages": 3, '
+                         '"gram_splits": 4, "gram_cta_pair": 1, "wx_tile_n": 256}')
     ap.add_argument("--persistent", action="store_true",
                     help="fp32 path, N <= 128: all K steps in one cooperative launch")
     ap.add_argument("--minibatch", type=int, default=0, metavar="J",
