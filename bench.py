@@ -37,6 +37,9 @@ PATHS = {
     "split-bf16": ("split", "bf16"),
     "split": ("split", "split"),
     "fp32": ("fp32", "fp32"),
+    "tf32-bf16": ("tf32", "bf16"),   # precision study: TF32 Gram
+    "tf32": ("tf32", "split"),       # precision study: TF32 Gram, split W X (isolates the Gram's error)
+    "bf16": ("bf16", "bf16"),        # precision study: one BF16 product in both contractions
 }
 METRIC = "EnSF member-steps/s (analysis step, K Euler-Maruyama steps per member)"
 UNIT = "member-steps/s"
@@ -247,7 +250,7 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
                 "note": "latency bound at this size (partials mostly L2-resident)"}
     if kernel not in ("gram", "wx_em"):
         return {"kernel": kernel, "bound": None, "avg_launch_ms": avg_ms}
-    split_factor = {"split": 3.0, "bf16": 1.0, "fp32": 1.0}[prec]
+    split_factor = {"split": 3.0, "bf16": 1.0, "fp32": 1.0, "tf32": 1.0}[prec]
     executed = flops * split_factor
     if prec == "fp32":
         bound, peak, src = "alu", FP32_SIMT_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
@@ -257,6 +260,8 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
             peak, src = float(peaks["bf16_tflops_sustained"]), "measured bf16 sustained (MEASURED_PEAKS.json)"
         else:
             peak, src = 1700.0, "fallback bf16 sustained"
+        if prec == "tf32":  # TF32 dense is half the BF16 rate (1.1 of 2.25 PFLOP/s nominal)
+            peak, src = peak * 1.1 / 2.25, src + " x 1.1/2.25 (nominal TF32/BF16 ratio)"
     achieved = flops / (avg_ms / 1e3) / 1e12
     return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": _traffic_record(kernel, p.name, args.path), "peak_source": src,
@@ -502,6 +507,8 @@ def run_ours(args):
     truth_dev = torch.from_numpy(p.truth.astype(np.float32)).to(dev)
     _, gpu_rmse = ensf.ensemble_stats(acc_out, truth_dev)        # FP64 mean and RMSE (step a6)
     _, prior_rmse = ensf.ensemble_stats(prior, truth_dev)
+    # the members themselves, for a per-member comparison with the oracle (small workloads)
+    acc_members = acc_out.cpu().numpy() if p.n * p.d <= (64 << 20) else None
     del acc_out
 
     def _rmse(mean):
@@ -532,7 +539,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"split-bf16": "bf16x3+bf16 (fp32 acc)", "split": "bf16x3 (fp32 acc)",
-                                          "fp32": "f32"}[args.path],
+                                          "fp32": "f32", "tf32-bf16": "tf32+bf16 (fp32 acc)",
+                                          "tf32": "tf32+bf16x3 (fp32 acc)",
+                                          "bf16": "bf16 (fp32 acc)"}[args.path],
             "data": "synthetic", "config": dict(_config(p, args.path, world), minibatch_J=J or p.n),
             "roofline": roof, "accuracy": accuracy,
             "roofline_other": other,
@@ -545,6 +554,11 @@ def run_ours(args):
         line["cpu_baseline"], oracle_out = cpu_baseline(p, args.cpu_budget_s, J or 0)
         if oracle_out is not None:
             accuracy["oracle_rmse"] = _rmse(oracle_out.mean(axis=0))
+            if acc_members is not None:
+                rel = np.linalg.norm(acc_members.astype(np.float64) - oracle_out, axis=1) / \
+                    np.linalg.norm(oracle_out, axis=1)
+                accuracy["member_rel_err"] = {"median": float(np.median(rel)), "p95": float(np.percentile(rel, 95)),
+                                              "max": float(rel.max())}
             accuracy["rmse_rel_diff"] = abs(accuracy["analysis_rmse"] / accuracy["oracle_rmse"] - 1.0)
     print(json.dumps(line))
     if dist:

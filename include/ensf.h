@@ -61,7 +61,9 @@ typedef enum {
     ENSF_PREC_FP32 = 0,        /* CUDA-core FP32 for the Gram Z X^T and for W X */
     ENSF_PREC_SPLIT_BF16X3 = 1 /* tensor cores: each operand split a = a_hi + a_lo in BF16,
                                   products a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulate */,
-    ENSF_PREC_BF16 = 2         /* tensor cores: one BF16 product, FP32 accumulate */
+    ENSF_PREC_BF16 = 2,        /* tensor cores: one BF16 product, FP32 accumulate */
+    ENSF_PREC_TF32 = 3         /* Gram only: tensor cores (kind::tf32) on the FP32 centred operands
+                                  read directly (the MMA uses their TF32 part), FP32 accumulate */
 } ensf_precision;
 
 #define ENSF_FLAG_CHECK_FINITE 1u  /* scan the final particles for NaN/Inf */

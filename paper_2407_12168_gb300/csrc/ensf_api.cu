@@ -42,7 +42,7 @@ constexpr int kSimtTile = 64;
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-bool is_tc(int p) { return p == ENSF_PREC_SPLIT_BF16X3 || p == ENSF_PREC_BF16; }
+bool is_tc(int p) { return p == ENSF_PREC_SPLIT_BF16X3 || p == ENSF_PREC_BF16 || p == ENSF_PREC_TF32; }
 
 // Offsets of every scratch array inside the workspace.
 struct Layout {
@@ -63,8 +63,9 @@ int simt_splits(int n, int n_x, int64_t d, int sms) {
 bool config_ok(const ensf_config *c) {
     if (!c || c->max_n < 1 || c->max_n > 8192 || c->max_d < 8 || c->max_d % 8 != 0) return false;
     for (int p : {c->gram, c->wx})
-        if (p != ENSF_PREC_FP32 && p != ENSF_PREC_SPLIT_BF16X3 && p != ENSF_PREC_BF16) return false;
-    return true;
+        if (p != ENSF_PREC_FP32 && p != ENSF_PREC_SPLIT_BF16X3 && p != ENSF_PREC_BF16 && p != ENSF_PREC_TF32)
+            return false;
+    return c->wx != ENSF_PREC_TF32;  // TF32 is a Gram form
 }
 
 Layout make_layout(const ensf_config *c) {
@@ -86,7 +87,11 @@ Layout make_layout(const ensf_config *c) {
     L.partial = take(sizeof(float) * L.partial_floats);
     if (is_tc(c->gram) || is_tc(c->wx)) {
         const int64_t NP = round_up(N, 8);  // bf16 row pitch multiple of 16 bytes
-        if (is_tc(c->gram)) {
+        if (c->gram == ENSF_PREC_TF32) {
+            // FP32 centred copies x - m and z - alpha m (the TF32 Gram's operands)
+            L.xb_hi = take(4 * N * D);
+            L.zb_hi = take(4 * N * D);
+        } else if (is_tc(c->gram)) {
             L.xb_hi = take(2 * N * D);
             L.zb_hi = take(2 * N * D);
             if (c->gram == ENSF_PREC_SPLIT_BF16X3) {
@@ -249,6 +254,11 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
         a.z32 = z;
         a.centre = h->at<float>(L.xbar);
         a.alpha = c.alpha;
+        if (h->cfg.gram == ENSF_PREC_TF32) {
+            a.tf32 = true;
+            a.zc32 = h->at<float>(L.zb_hi);
+            a.xc32 = h->at<float>(L.xb_hi) + (size_t)x0 * d;
+        }
         ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_tc(h->tc, a, h->sms, &splits, &part_stride, &ldp, s));
     }
     __nv_bfloat16 *wb_hi = nullptr, *wb_lo = nullptr;
@@ -375,6 +385,17 @@ ensf_status analysis_validate(ensf_handle *h, const float *prior, int n, int64_t
 // Everything of one analysis before its first Euler-Maruyama step: centre and
 // norms of the forecast ensemble, the initial particles, the BF16 planes.
 // perm (device, optional): the split planes and norms hold the members in this order.
+// The Gram's copy of src [rows][d] (row r taken from rowmap[r] when given):
+// BF16 hi (and lo) planes of src - scale m, or for the TF32 Gram the FP32
+// src - scale m itself.
+cudaError_t gram_operand(const ensf_handle *h, const float *src, int rows, int64_t d, size_t off_hi, size_t off_lo,
+                         const float *centre, float scale, const int *rowmap, cudaStream_t s) {
+    if (h->cfg.gram == ENSF_PREC_TF32)
+        return ensf::launch_centre_copy(src, rows, d, h->at<float>(off_hi), centre, scale, rowmap, s);
+    return ensf::launch_split_bf16(src, rows, d, h->at<__nv_bfloat16>(off_hi),
+                                   off_lo ? h->at<__nv_bfloat16>(off_lo) : nullptr, d, s, centre, scale, rowmap);
+}
+
 ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, int K, float eps, float sigma_obs,
                           int obs_op, const ensf_noise *noise, float *out, cudaStream_t s,
                           const int *perm = nullptr, bool skip_z_split = false) {
@@ -385,14 +406,11 @@ ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, 
     ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, h->at<double>(L.norms), s, xbar, perm));
     ENSF_LAUNCH(h, P_INIT, s, ensf::launch_init_particles(out, n, d, noise->buf, noise->seed, noise->offset, s));
     if (tc_gram) {
-        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(prior, n, d, h->at<__nv_bfloat16>(L.xb_hi),
-                                                           L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s,
-                                                           xbar, 1.0f, perm));
+        ENSF_LAUNCH(h, P_SPLIT, s, gram_operand(h, prior, n, d, L.xb_hi, L.xb_lo, xbar, 1.0f, perm, s));
         if (!skip_z_split)  // (the FP32-operand Gram splits the particles itself)
             ENSF_LAUNCH(h, P_SPLIT, s,
-                        ensf::launch_split_bf16(out, n, d, h->at<__nv_bfloat16>(L.zb_hi),
-                                                L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s, xbar,
-                                                step_coef(0, K, eps, sigma_obs, obs_op).alpha));
+                        gram_operand(h, out, n, d, L.zb_hi, L.zb_lo, xbar, step_coef(0, K, eps, sigma_obs, obs_op).alpha,
+                                     nullptr, s));
     }
     if (tc_wx)
         ENSF_LAUNCH(h, P_SPLIT, s,
@@ -421,6 +439,10 @@ ensf::TcWxArgs wx_args(ensf_handle *h, int n, int64_t d, const float *y, const u
     a.z = out;
     a.zb_hi = is_tc(h->cfg.gram) ? h->at<__nv_bfloat16>(L.zb_hi) : nullptr;
     a.zb_lo = (is_tc(h->cfg.gram) && L.zb_lo) ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
+    if (h->cfg.gram == ENSF_PREC_TF32) {  // the TF32 Gram reads FP32 centred particles
+        a.zc32 = h->at<float>(L.zb_hi);
+        a.zb_hi = a.zb_lo = nullptr;
+    }
     a.y = y;
     a.mask = obs_mask;
     a.noise = noise->buf ? noise->buf + (size_t)(k + 1) * n * d
@@ -493,8 +515,9 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
                         ensf::launch_wx_em_fp32(h->at<float>(L.w), n, prior, n, n, d, out, y, obs_mask, noise->buf,
                                                 noise->seed, noise->offset, c, s));
             if (tc_gram && !gram_f32)
-                ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(out, n, d, zb_hi, zb_lo, d, s, xbar,
-                                                                   step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha));
+                ENSF_LAUNCH(h, P_SPLIT, s,
+                            gram_operand(h, out, n, d, L.zb_hi, L.zb_lo, xbar,
+                                         step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha, nullptr, s));
         } else {
             ensf::TcWxArgs a = wx_args(h, n, d, y, obs_mask, noise, out, c,
                                        step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha, k, x0, nm);
@@ -614,6 +637,11 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         ga.z32 = out;
         ga.centre = h->at<float>(L.xbar);
         ga.alpha = c.alpha;
+        if (h->cfg.gram == ENSF_PREC_TF32) {
+            ga.tf32 = true;
+            ga.zc32 = h->at<float>(L.zb_hi);
+            ga.xc32 = h->at<float>(L.xb_hi);
+        }
     }
     ensf::TcWxArgs wa;
     if (tc_wx) {
@@ -674,7 +702,8 @@ ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning 
     g.a_fp32 = t->gram_fp32_particles;
     const bool split3 = h->cfg.gram == ENSF_PREC_SPLIT_BF16X3;
     const bool wx_split = h->cfg.wx == ENSF_PREC_SPLIT_BF16X3;
-    if (ensf::tc_set_tuning(h->tc, n, n, d, split3, g, is_tc(h->cfg.wx) ? t->wx_tile_n : 0, wx_split) != cudaSuccess)
+    if (ensf::tc_set_tuning(h->tc, n, n, d, split3, g, is_tc(h->cfg.wx) ? t->wx_tile_n : 0, wx_split,
+                            h->cfg.gram == ENSF_PREC_TF32) != cudaSuccess)
         return fail(ENSF_EINVAL, "ensf_set_tuning: no kernel for that launch shape");
     return ENSF_OK;
 }
@@ -696,12 +725,8 @@ ensf_status ensf_weights(ensf_handle *h, const float *z, int n, const float *pri
     ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_col_mean(prior, n_x, d, xbar, s));
     ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n_x, d, h->at<double>(L.norms), s, xbar));
     if (is_tc(h->cfg.gram)) {
-        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(prior, n_x, d, h->at<__nv_bfloat16>(L.xb_hi),
-                                                           L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr, d, s,
-                                                           xbar, 1.0f));
-        ENSF_LAUNCH(h, P_SPLIT, s, ensf::launch_split_bf16(z, n, d, h->at<__nv_bfloat16>(L.zb_hi),
-                                                           L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr, d, s,
-                                                           xbar, (float)alpha));
+        ENSF_LAUNCH(h, P_SPLIT, s, gram_operand(h, prior, n_x, d, L.xb_hi, L.xb_lo, xbar, 1.0f, nullptr, s));
+        ENSF_LAUNCH(h, P_SPLIT, s, gram_operand(h, z, n, d, L.zb_hi, L.zb_lo, xbar, (float)alpha, nullptr, s));
     }
     ensf::StepCoef c{};
     c.alpha = (float)alpha;
@@ -941,8 +966,8 @@ size_t ensf_batch_workspace_bytes(const ensf_config *cfg, const ensf_instance *i
 ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int count, int K, float eps,
                                   void *workspace, size_t ws_bytes, void *stream) {
     if (!h) return fail(ENSF_EINVAL, "ensf_analysis_batched: NULL handle");
-    if (!is_tc(h->cfg.gram) || !is_tc(h->cfg.wx))
-        return fail(ENSF_EUNSUPPORTED, "ensf_analysis_batched: needs tensor-core precisions for Gram and W X");
+    if (!is_tc(h->cfg.gram) || !is_tc(h->cfg.wx) || h->cfg.gram == ENSF_PREC_TF32)
+        return fail(ENSF_EUNSUPPORTED, "ensf_analysis_batched: needs BF16-based tensor-core precisions");
     if (!inst || count < 1) return fail(ENSF_EINVAL, "ensf_analysis_batched: no instances");
     if (K < 1 || !(eps > 0.0f && eps < 1.0f)) return fail(ENSF_EINVAL, "ensf_analysis_batched: bad K or eps");
     for (int i = 0; i < count; ++i) {

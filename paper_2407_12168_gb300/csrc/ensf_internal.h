@@ -63,6 +63,8 @@ cudaError_t launch_analysis_small(const float *x, const double *norms, const flo
                                   int64_t partial_floats, float *w, unsigned *bar, int *err, int sms,
                                   cudaStream_t s);
 cudaError_t launch_selftest_grid_barrier(unsigned *bar, int *err, cudaStream_t s);
+cudaError_t launch_centre_copy(const float *x, int rows, int64_t cols, float *out, const float *centre, float scale,
+                               const int *rowmap, cudaStream_t s);
 cudaError_t launch_model_error(float *state, int batch, int64_t d, const float *coef, int nproc, uint64_t seed,
                                uint32_t cycle, cudaStream_t s);
 cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, float a, int mode, cudaStream_t s);

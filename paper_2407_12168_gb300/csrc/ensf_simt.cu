@@ -321,6 +321,24 @@ __global__ void k_split_bf16(const float *__restrict__ x, int64_t cols, __nv_bfl
     if (lo) *reinterpret_cast<uint2 *>(lo + (int64_t)r * ldo + q * 4) = *reinterpret_cast<uint2 *>(l);
 }
 
+// The FP32 centred copy out[r][c] = x[row(r)][c] - scale * m[c] (the TF32
+// Gram's operand), rounded as the splits round it.
+__global__ void k_centre_copy(const float *__restrict__ x, int64_t cols, float *__restrict__ out,
+                              const float *__restrict__ centre, float scale, const int *__restrict__ rows) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int r = blockIdx.y;
+    if (q * 4 >= cols) return;
+    float4 v = ld4(x + (int64_t)(rows ? rows[r] : r) * cols + q * 4);
+    if (centre) {
+        const float4 m = ld4(centre + q * 4);
+        v.x = __fsub_rn(v.x, __fmul_rn(scale, m.x));
+        v.y = __fsub_rn(v.y, __fmul_rn(scale, m.y));
+        v.z = __fsub_rn(v.z, __fmul_rn(scale, m.z));
+        v.w = __fsub_rn(v.w, __fmul_rn(scale, m.w));
+    }
+    *reinterpret_cast<float4 *>(out + (int64_t)r * cols + q * 4) = v;
+}
+
 // Transposed split through a 32x32 shared tile: xT[c][j] from x[j][c].
 __global__ void k_split_bf16_t(const float *__restrict__ x, int rows, int64_t cols,
                                __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
@@ -539,6 +557,13 @@ cudaError_t launch_split_bf16(const float *x, int rows, int64_t cols, __nv_bfloa
                               const int *rowmap) {
     dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)rows);
     k_split_bf16<<<grid, 256, 0, s>>>(x, cols, hi, lo, ldo, centre, scale, rowmap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centre_copy(const float *x, int rows, int64_t cols, float *out, const float *centre, float scale,
+                               const int *rowmap, cudaStream_t s) {
+    dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)rows);
+    k_centre_copy<<<grid, 256, 0, s>>>(x, cols, out, centre, scale, rowmap);
     return cudaGetLastError();
 }
 

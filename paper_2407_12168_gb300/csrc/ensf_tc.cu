@@ -155,11 +155,12 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
     return d;
 }
 
-// Descriptor of a K-major tile whose k-block is KB elements wide.
-template <int KB>
+// Descriptor of a K-major tile whose k-block rows are ROWB bytes (128: the
+// 128-byte swizzle, 64: the 64-byte swizzle).
+template <int ROWB>
 __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
-    static_assert(KB == 64 || KB == 32, "k-block width");
-    return KB == 64 ? desc_sw128(saddr) : desc_sw64(saddr);
+    static_assert(ROWB == 128 || ROWB == 64, "k-block row bytes");
+    return ROWB == 128 ? desc_sw128(saddr) : desc_sw64(saddr);
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, A and B BF16, both
@@ -167,6 +168,21 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
            (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+// Instruction descriptor, kind::tf32: FP32 accumulator, A and B TF32 (format 2).
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+           (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -217,10 +233,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // ----------------------------------------------------- shared-memory plan
-template <int BN, int STAGES, bool SPLIT, int KB = BK>
+template <int BN, int STAGES, bool SPLIT, int KB = BK, int ES = 2>
 struct Plan {
-    static constexpr int kA = BM * KB * 2;  // one A plane of a stage
-    static constexpr int kB = BN * KB * 2;  // one B plane
+    static constexpr int kA = BM * KB * ES;  // one A plane of a stage
+    static constexpr int kB = BN * KB * ES;  // one B plane
     static constexpr int kPlanes = SPLIT ? 2 : 1;
     static constexpr int kStage = (kA + kB) * kPlanes;
     static constexpr int kBarOff = kStage * STAGES;
@@ -274,10 +290,10 @@ __device__ __forceinline__ uint32_t setup(const Ctl &c, int warp) {
 
 // Producer (one thread): k-blocks kb0 .. kb0+nkb-1 (KB elements wide) of A
 // rows m0.. and B rows n0..
-template <int BN, int STAGES, bool SPLIT, int KB = BK>
+template <int BN, int STAGES, bool SPLIT, int KB = BK, int ES = 2>
 __device__ void produce(const Ctl &c, const CUtensorMap *a_hi, const CUtensorMap *a_lo, const CUtensorMap *b_hi,
                         const CUtensorMap *b_lo, int m0, int n0, int kb0, int nkb, int *err) {
-    using P = Plan<BN, STAGES, SPLIT, KB>;
+    using P = Plan<BN, STAGES, SPLIT, KB, ES>;
     int issued = 0;
     for (int i = 0; i < nkb; ++i) {
         const int s = i % STAGES;
@@ -305,10 +321,11 @@ __device__ void produce(const Ctl &c, const CUtensorMap *a_hi, const CUtensorMap
 }
 
 // MMA issuer (one thread): accumulate the tile in TMEM, then signal accum.
-template <int BN, int STAGES, bool SPLIT, int KB = BK>
+template <int BN, int STAGES, bool SPLIT, int KB = BK, int ES = 2>
 __device__ void mma_loop(const Ctl &c, uint32_t tmem, int nkb, int *err) {
-    using P = Plan<BN, STAGES, SPLIT, KB>;
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    using P = Plan<BN, STAGES, SPLIT, KB, ES>;
+    constexpr int kRowB = KB * ES;  // bytes per k-block row (one swizzle row)
+    constexpr uint32_t idesc = ES == 4 ? idesc_tf32(BM, BN) : idesc_bf16(BM, BN);
     for (int i = 0; i < nkb; ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (i / STAGES) & 1;
@@ -319,13 +336,19 @@ __device__ void mma_loop(const Ctl &c, uint32_t tmem, int nkb, int *err) {
         const uint32_t b_hi = a_hi + P::kA * P::kPlanes;
         const uint32_t b_lo = b_hi + P::kB;
 #pragma unroll
-        for (int kk = 0; kk < KB / 16; ++kk) {
-            const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes along the swizzled row
-            mma_bf16(tmem, desc_kmajor<KB>(a_hi + off), desc_kmajor<KB>(b_hi + off), idesc,
+        for (int kk = 0; kk < kRowB / 32; ++kk) {
+            // one MMA covers 32 bytes along the swizzled row: K = 16 BF16 or K = 8 TF32
+            const uint32_t off = kk * 32;
+            if (ES == 4) {
+                mma_tf32(tmem, desc_kmajor<kRowB>(a_hi + off), desc_kmajor<kRowB>(b_hi + off), idesc,
+                         (i > 0 || kk > 0) ? 1u : 0u);
+                continue;
+            }
+            mma_bf16(tmem, desc_kmajor<kRowB>(a_hi + off), desc_kmajor<kRowB>(b_hi + off), idesc,
                      (i > 0 || kk > 0) ? 1u : 0u);
             if (SPLIT) {
-                mma_bf16(tmem, desc_kmajor<KB>(a_hi + off), desc_kmajor<KB>(b_lo + off), idesc, 1u);
-                mma_bf16(tmem, desc_kmajor<KB>(a_lo + off), desc_kmajor<KB>(b_hi + off), idesc, 1u);
+                mma_bf16(tmem, desc_kmajor<kRowB>(a_hi + off), desc_kmajor<kRowB>(b_lo + off), idesc, 1u);
+                mma_bf16(tmem, desc_kmajor<kRowB>(a_lo + off), desc_kmajor<kRowB>(b_hi + off), idesc, 1u);
             }
         }
         mma_commit(&c.empty[s]);
@@ -394,11 +417,11 @@ __device__ __forceinline__ void gram_noise_share(const GramParams &p) {
     }
 }
 
-template <int BN, int STAGES, bool SPLIT, int KB>
+template <int BN, int STAGES, bool SPLIT, int KB, int ES = 2>
 __global__ void __launch_bounds__(kGramThreads, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
           const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
-    using P = Plan<BN, STAGES, SPLIT, KB>;
+    using P = Plan<BN, STAGES, SPLIT, KB, ES>;
     extern __shared__ uint8_t smem_raw[];
     const Ctl c = carve<P>(smem_raw, STAGES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -409,9 +432,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUte
     const uint32_t tmem = setup<BN, STAGES>(c, warp);
 
     if (warp == 0) {
-        if (lane == 0) produce<BN, STAGES, SPLIT, KB>(c, &a_hi, &a_lo, &b_hi, &b_lo, m0, n0, kb0, nkb, p.err);
+        if (lane == 0) produce<BN, STAGES, SPLIT, KB, ES>(c, &a_hi, &a_lo, &b_hi, &b_lo, m0, n0, kb0, nkb, p.err);
     } else if (warp == 1) {
-        if (lane == 0) mma_loop<BN, STAGES, SPLIT, KB>(c, tmem, nkb, p.err);
+        if (lane == 0) mma_loop<BN, STAGES, SPLIT, KB, ES>(c, tmem, nkb, p.err);
     } else {
         if (p.noise && warp >= p.noise_warp0) gram_noise_share(p);
         if (warp >= 6) {
@@ -968,6 +991,7 @@ struct WxParams {
     int n_tiles;   // ceil(n / BN)
     float *z;
     __nv_bfloat16 *zb_hi, *zb_lo;
+    float *zc32;             // FP32 z - alpha_next m for a TF32 Gram (NULL: none)
     const float *y;
     const uint8_t *mask;
     const float *noise;  // xi[k+1] slice [n][d] (pre-generated form)
@@ -1136,6 +1160,7 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
                     const float zn = em_update(cf, zv[e], u[e], g, xi[e]);
                     const int64_t off = base + e * p.d;
                     p.z[off] = zn;
+                    if (p.zc32) p.zc32[off] = __fsub_rn(zn, shift);
                     if (p.zb_hi) {
                         const float zc = __fsub_rn(zn, shift);  // rounded as the FP32-operand Gram rounds it
                         const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
@@ -1460,10 +1485,10 @@ cudaError_t set_smem(K kernel, int bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <int BN, int STAGES, bool SPLIT, int KB = BK>
+template <int BN, int STAGES, bool SPLIT, int KB = BK, int ES = 2>
 cudaError_t run_gram(const CUtensorMap (&maps)[4], const GramParams &p, dim3 grid, cudaStream_t s) {
-    using P = Plan<BN, STAGES, SPLIT, KB>;
-    auto kern = k_gram_tc<BN, STAGES, SPLIT, KB>;
+    using P = Plan<BN, STAGES, SPLIT, KB, ES>;
+    auto kern = k_gram_tc<BN, STAGES, SPLIT, KB, ES>;
     cudaError_t e = set_smem(kern, P::kBytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, kGramThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
@@ -1529,8 +1554,47 @@ GramChoice default_gram_choice(const TcGramArgs &a) {
     return g;
 }
 
+cudaError_t gram_launch_tf32(TcContext *ctx, const TcGramArgs &a, int sms, const GramChoice &ch, int *splits,
+                             int64_t *part_stride, int *ldp, cudaStream_t s) {
+    constexpr int KB = 32;  // 32 FP32 = one 128-byte swizzle row
+    const int BN = ch.bn == 128 ? 128 : 256;
+    CUtensorMap maps[4];
+    cudaError_t e;
+    if ((e = make_map_f32(ctx, &maps[0], a.zc32, a.d, a.n, BM)) != cudaSuccess) return e;
+    if ((e = make_map_f32(ctx, &maps[2], a.xc32, a.d, a.n_x, BN)) != cudaSuccess) return e;
+    memset(&maps[1], 0, sizeof(maps[1]));
+    memset(&maps[3], 0, sizeof(maps[3]));
+    const int mt = (a.n + BM - 1) / BM, nt = (a.n_x + BN - 1) / BN;
+    GramParams p;
+    p.n = a.n;
+    p.n_x = a.n_x;
+    p.kblocks = static_cast<int>((a.d + KB - 1) / KB);
+    const int64_t per_split = static_cast<int64_t>(a.n) * a.n_x;
+    int S = ch.splits > 0 ? ch.splits : choose_splits(mt * nt, p.kblocks, sms, per_split, a.partial_cap);
+    S = std::max(1, std::min<int>(S, static_cast<int>(std::min<int64_t>(p.kblocks, a.partial_cap / per_split))));
+    p.kb_per_split = (p.kblocks + S - 1) / S;
+    S = (p.kblocks + p.kb_per_split - 1) / p.kb_per_split;
+    p.partial = a.partial;
+    p.err = a.err;
+    p.noise = a.noise;
+    p.seed = a.seed;
+    p.offset = a.offset;
+    p.noise_k = a.noise_k;
+    p.d = a.d;
+    p.noise_warp0 = ch.noise_warps == 4 ? 6 : 2;
+    p.alpha = 0.f;
+    p.centre = nullptr;
+    *splits = S;
+    *part_stride = per_split;
+    *ldp = a.n_x;
+    dim3 grid(mt, nt, S);
+    if (BN == 256) return run_gram<256, 4, false, KB, 4>(maps, p, grid, s);
+    return run_gram<128, 6, false, KB, 4>(maps, p, grid, s);
+}
+
 cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const GramChoice &ch, int *splits,
                         int64_t *part_stride, int *ldp, cudaStream_t s) {
+    if (a.tf32) return gram_launch_tf32(ctx, a, sms, ch, splits, part_stride, ldp, s);
     // the pair Gram needs whole 256-row tiles on both sides (no tile of a CTA
     // lies entirely outside the operands)
     const bool pair = ch.pair && a.split3 && a.n % kPairTile == 0 && a.n_x % kPairTile == 0;
@@ -1639,6 +1703,7 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     p.n_tiles = 0;
     p.z = a.z;
     p.zb_hi = a.zb_hi;
+    p.zc32 = a.zc32;
     p.zb_lo = a.zb_lo;
     p.y = a.y;
     p.mask = a.mask;
@@ -1661,11 +1726,13 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
 }
 
 cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3, const GramChoice &g, int wx_bn,
-                          bool wx_split) {
+                          bool wx_split, bool tf32) {
     if (!ctx) return cudaErrorInvalidValue;
     const int bk = g.bk ? g.bk : BK;
     bool ok;
-    if (g.pair)
+    if (tf32)
+        ok = !g.pair && (bk == 32 || g.bk == 0) && ((g.bn == 128 && g.stages == 6) || (g.bn == 256 && g.stages == 4));
+    else if (g.pair)
         ok = split3 && g.bn == kPairTile && g.stages == kPairStages && bk == BK && n % kPairTile == 0 &&
              n_x % kPairTile == 0;
     else if (split3)
@@ -1680,7 +1747,7 @@ cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3
     if (g.noise_warps != 0 && g.noise_warps != 4 && g.noise_warps != 8) return cudaErrorInvalidValue;
     if (g.a_fp32 && !g.pair) return cudaErrorInvalidValue;
     GramChoice c = g;
-    c.bk = bk;
+    c.bk = tf32 ? 32 : bk;
     ctx->gram_tuned[std::make_tuple(n, n_x, d, split3)] = c;
     if (wx_bn) ctx->wx_tuned[std::make_tuple(n, d, wx_split)] = wx_bn;
     return cudaSuccess;
@@ -1865,7 +1932,10 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
         std::vector<Cand> cands;
         // (tile width, ring depth, k-block width, CTA pair, FP32 particle operand)
         const int shapes[][5] = {{128, 3, 64, 0, 0}, {256, 2, 64, 0, 0}, {256, 3, 64, 1, 0}, {256, 3, 64, 1, 1}};
-        for (const auto &sh : shapes) {
+        const int shapes_tf32[][5] = {{128, 6, 32, 0, 0}, {256, 4, 32, 0, 0}};
+        const int n_shapes = g->tf32 ? 2 : 4;
+        for (int si = 0; si < n_shapes; ++si) {
+            const int *sh = g->tf32 ? shapes_tf32[si] : shapes[si];
             const int bn = sh[0], kbw = sh[2], pr = sh[3], f32 = sh[4];
             if (f32 && !(g->z32 && w && w->zb_hi)) continue;
             if (pr && !(g->split3 && g->n % kPairTile == 0 && g->n_x % kPairTile == 0)) continue;

@@ -56,6 +56,10 @@ struct TcGramArgs {
     const float *z32 = nullptr;
     const float *centre = nullptr;
     float alpha = 0.f;
+    // TF32 Gram (kind::tf32): FP32 centred operands z - alpha m [n][d] and
+    // x - m [n_x][d] instead of BF16 planes
+    bool tf32 = false;
+    const float *zc32 = nullptr, *xc32 = nullptr;
 };
 
 struct TcWxArgs {
@@ -68,6 +72,7 @@ struct TcWxArgs {
     int64_t d;
     float *z;                            // particles [n][d], updated in place
     __nv_bfloat16 *zb_hi, *zb_lo;        // split copies of the updated particles (NULL: skip)
+    float *zc32 = nullptr;               // or the FP32 centred particles (TF32 Gram), NULL: skip
     const float *y;
     const uint8_t *mask;
     const float *noise;                  // xi[k+1] as a [n][d] slice (pre-generated), or NULL:
@@ -137,7 +142,7 @@ using AfterGram = cudaError_t (*)(void *ctx, int splits, int64_t part_stride, in
 // (wx_bn 0 leaves W X alone).  cudaErrorInvalidValue for a shape that has no
 // compiled kernel.
 cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3, const GramChoice &g, int wx_bn,
-                          bool wx_split);
+                          bool wx_split, bool tf32 = false);
 // Failure-detection self-test: a bounded mbarrier wait that must run out.
 cudaError_t launch_selftest_mbar_wait(int *err, cudaStream_t s);
 // True when the tuned Gram for this shape reads the FP32 particles (the W X

@@ -24,7 +24,8 @@ FLAG_CUDA_GRAPH = 2
 FLAG_PERSISTENT = 8
 FLAG_INLINE_NOISE = 4
 
-PRECISIONS = {"fp32": PREC_FP32, "split": PREC_SPLIT_BF16X3, "bf16": PREC_BF16}
+PREC_TF32 = 3
+PRECISIONS = {"fp32": PREC_FP32, "split": PREC_SPLIT_BF16X3, "bf16": PREC_BF16, "tf32": PREC_TF32}
 
 
 class EnsfConfig(ctypes.Structure):
@@ -196,7 +197,8 @@ class Filter:
 
     ``gram`` and ``wx`` choose the arithmetic of the Gram Z X^T and of the
     weighted sum W X: ``"fp32"`` (CUDA cores), ``"split"`` (BF16x3 on tensor
-    cores) or ``"bf16"`` (one BF16 product on tensor cores).  ``persistent``:
+    cores), ``"bf16"`` (one BF16 product on tensor cores) or, for the Gram
+    only, ``"tf32"`` (tensor cores on the FP32 centred operands).  ``persistent``:
     with FP32 precisions and n <= 128, all K steps run in one cooperative
     launch (small filters)."""
 

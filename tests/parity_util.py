@@ -40,6 +40,8 @@ def eps_path(prec: str, d: int) -> float:
         return 2.0 * 2.0 ** -24
     if prec == "split":
         return 3.0 * 2.0 ** -18 / np.sqrt(d) + 2.0 * 2.0 ** -24
+    if prec == "tf32":  # operands rounded to TF32 (10 stored mantissa bits)
+        return 2.0 * 2.0 ** -11 / np.sqrt(d) + 2.0 * 2.0 ** -24
     return 2.0 * 2.0 ** -9 / np.sqrt(d)
 
 

@@ -15,6 +15,9 @@ PATHS = {
     "fp32": ("fp32", "fp32", TOL_FP32),
     "split": ("split", "split", TOL_FP32),
     "split-bf16": ("split", "bf16", TOL_BF16),
+    # the TF32 Gram (kind::tf32 on FP32 centred operands) with the split W X:
+    # TF32 keeps 10 mantissa bits, so it is held to the BF16-level tolerance
+    "tf32": ("tf32", "split", TOL_BF16),
 }
 
 
@@ -100,8 +103,12 @@ def test_weights_match_oracle(path, n, n_x, d):
             ref, logit = o.weights(X, Z[i], s["alpha"], s["beta2"])
             gap = np.sort(logit)[-1] - np.sort(logit)[-2] if n_x > 1 else np.inf
             assert abs(w[i].sum() - 1.0) < 1e-5
-            if gap > 1e-2:
-                np.testing.assert_allclose(w[i], ref, atol=2e-4)
+            # the TF32 Gram keeps 10 mantissa bits of each operand: its logits
+            # carry errors of about 1e-2 at these sizes, hence the wider bound
+            # and the wider gap below which members count as tied
+            atol, min_gap = (5e-3, 0.5) if gram == "tf32" else (2e-4, 1e-2)
+            if gap > min_gap:
+                np.testing.assert_allclose(w[i], ref, atol=atol)
 
 
 # --------------------------------------------------------------- analysis ---
