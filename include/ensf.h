@@ -140,12 +140,17 @@ typedef struct {
     int gram_noise_warps; /* warps of a Gram CTA generating the next step's noise (8 or 4) */
     int gram_fp32_particles; /* 1 (pair tiles only): the Gram reads the FP32 particles and splits
                                 them itself, so the W X step writes no BF16 particle planes */
+    int noise_inline;  /* Philox noise with both stages on the tensor cores: 1 = evaluated in the
+                          W X epilogue, 0 = written a step ahead by the Gram's idle warps */
 } ensf_tuning;
 
 /* Autotuner for the tensor-core stages: times the candidate launch shapes of
  * the Gram (tile width, ring depth, split count) and of W X (tile width) on
  * these operands (same arguments as ensf_analysis, without K) and records the
  * fastest for this (n, d) in the handle; later analyses of that shape use it.
+ * When both stages run on the tensor cores with counter-based noise (no noise
+ * buffer, no ENSF_FLAG_INLINE_NOISE), it tunes both noise placements and
+ * keeps the one with the smaller Gram + softmax + W X time (noise_inline).
  * Overwrites `out` and the workspace, synchronises `stream`, and must not be
  * called while the stream is being captured.  `report` may be NULL.  A handle
  * with only CUDA-core precisions returns ENSF_OK with a zeroed report. */
@@ -155,8 +160,8 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
 
 /* Records launch shapes for analyses of this (n, d) without timing them,
  * e.g. a report saved from ensf_autotune in another process.  Uses the
- * gram_tile_n, gram_stages, gram_splits (0: the cost model), gram_k_block and
- * wx_tile_n (0: unchanged) fields of `t`.  Valid Gram shapes (tile width,
+ * gram_tile_n, gram_stages, gram_splits (0: the cost model), gram_k_block,
+ * wx_tile_n (0: unchanged) and noise_inline fields of `t`.  Valid Gram shapes (tile width,
  * ring depth, k-block) for the split-BF16x3 Gram: (128, 3, 64), (256, 2, 64),
  * (128, 6, 32), (256, 4, 32), (256, 3, 32), and with gram_cta_pair = 1
  * (256, 3, 64) when n is a multiple of 256 (optionally with

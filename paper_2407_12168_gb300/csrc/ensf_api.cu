@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/ensf.h"
@@ -175,6 +177,17 @@ struct ensf_handle {
     size_t staging_bytes = 0;
     cudaEvent_t staging_done = nullptr;
     bool staging_pending = false;
+    // (n, d) -> true when ensf_autotune (or ensf_set_tuning) chose to evaluate
+    // the noise in the W X epilogue rather than in the Gram's idle warps
+    std::map<std::pair<int, int64_t>, bool> noise_inline;
+
+    // whether the tensor-core W X of an (n, d) analysis evaluates its noise
+    // itself (no pre-generated slice)
+    bool inline_noise(int n, int64_t d) const {
+        if (cfg.flags & ENSF_FLAG_INLINE_NOISE) return true;
+        auto it = noise_inline.find(std::make_pair(n, d));
+        return it != noise_inline.end() && it->second;
+    }
 
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
     int *err() const { return at<int>(L.err); }
@@ -446,7 +459,7 @@ ensf::TcWxArgs wx_args(ensf_handle *h, int n, int64_t d, const float *y, const u
     a.y = y;
     a.mask = obs_mask;
     a.noise = noise->buf ? noise->buf + (size_t)(k + 1) * n * d
-                         : ((h->cfg.flags & ENSF_FLAG_INLINE_NOISE) ? nullptr : h->at<float>(L.noise));
+                         : (h->inline_noise(n, d) ? nullptr : h->at<float>(L.noise));
     a.seed = noise->seed;
     a.offset = noise->offset;
     a.centre = h->at<float>(L.xbar);
@@ -494,7 +507,7 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
     // slice: with a tensor-core Gram its idle epilogue warps write xi[k+1]
     // while the MMAs of step k run; otherwise a separate launch does.
     float *nslice = tc_wx ? h->at<float>(L.noise) : nullptr;
-    const bool pregen = tc_wx && !noise->buf && !(h->cfg.flags & ENSF_FLAG_INLINE_NOISE);
+    const bool pregen = tc_wx && !noise->buf && !h->inline_noise(n, d);
     for (int k = 0; k < K; ++k) {
         ensf::StepCoef c = step_coef(k, K, eps, sigma_obs, obs_op);
         NoiseRequest nr;
@@ -527,6 +540,85 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
     }
     if (h->cfg.flags & ENSF_FLAG_CHECK_FINITE)
         ENSF_LAUNCH(h, P_CHECK, s, ensf::launch_check_finite(out, (int64_t)n * d, h->err(), s));
+    return ENSF_OK;
+}
+
+// One pass of the autotuner with the noise mode currently recorded for (n, d):
+// fills W, builds the stage arguments and times the candidate shapes.
+ensf_status autotune_pass(ensf_handle *h, const float *prior, int n, int64_t d, const float *y,
+                          const uint8_t *obs_mask, int obs_op, float sigma_obs, float eps, const ensf_noise *noise,
+                          float *out, cudaStream_t s, ensf::TcTuneReport *rep) {
+    const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
+    ensf_status st = ENSF_OK;
+    const int K = 100;
+    st = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s);
+    if (st != ENSF_OK) return st;
+    ensf::StepCoef c = step_coef(K / 2, K, eps, sigma_obs, obs_op);
+    NoiseRequest nr;
+    const bool pregen = tc_wx && !noise->buf && !h->inline_noise(n, d);
+    if (pregen && tc_gram) {
+        nr.slice = h->at<float>(h->L.noise);
+        nr.seed = noise->seed;
+        nr.offset = noise->offset;
+        nr.k = K / 2 + 1;
+    }
+    st = gram_softmax(h, out, n, prior, n, d, c, !tc_wx, s, nr);  // fills W for the W X trials
+    if (st != ENSF_OK) return st;
+    ensf::TcGramArgs ga;
+    if (tc_gram) {
+        const Layout &L = h->L;
+        ga.zb_hi = h->at<__nv_bfloat16>(L.zb_hi);
+        ga.zb_lo = L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
+        ga.xb_hi = h->at<__nv_bfloat16>(L.xb_hi);
+        ga.xb_lo = L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr;
+        ga.n = n;
+        ga.n_x = n;
+        ga.d = d;
+        ga.split3 = (h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
+        ga.partial = h->at<float>(L.partial);
+        ga.partial_cap = L.partial_floats;
+        ga.err = h->err();
+        ga.noise = nr.slice;
+        ga.seed = nr.seed;
+        ga.offset = nr.offset;
+        ga.noise_k = nr.k;
+        ga.z32 = out;
+        ga.centre = h->at<float>(L.xbar);
+        ga.alpha = c.alpha;
+        if (h->cfg.gram == ENSF_PREC_TF32) {
+            ga.tf32 = true;
+            ga.zc32 = h->at<float>(L.zb_hi);
+            ga.xc32 = h->at<float>(L.xb_hi);
+        }
+    }
+    ensf::TcWxArgs wa;
+    if (tc_wx) {
+        if (pregen && !tc_gram)
+            ENSF_CUDA(ensf::launch_noise_slice(noise->seed, noise->offset, K / 2 + 1, n, d, h->at<float>(h->L.noise),
+                                               1 << 30, s));
+        wa = wx_args(h, n, d, y, obs_mask, noise, out, c, step_coef(K / 2 + 1, K, eps, sigma_obs, obs_op).alpha, K / 2);
+        if (noise->buf) wa.noise = noise->buf;  // any valid slice will do for timing
+    }
+    // judge each Gram shape by Gram + the softmax that consumes its partials
+    struct SoftmaxCtx {
+        ensf_handle *h;
+        int n;
+        ensf::StepCoef c;
+        bool tc_wx;
+    } sctx{h, n, c, tc_wx};
+    auto after = [](void *vp, int splits, int64_t part_stride, int ldp, cudaStream_t st) -> cudaError_t {
+        const SoftmaxCtx &x = *static_cast<const SoftmaxCtx *>(vp);
+        const Layout &L = x.h->L;
+        return ensf::launch_softmax_rows(x.h->at<float>(L.partial), splits, part_stride, ldp, x.n, x.n,
+                                         x.h->at<double>(L.norms), x.c.alpha_d, x.c.inv_2beta2_d,
+                                         x.tc_wx ? nullptr : x.h->at<float>(L.w), x.n,
+                                         x.tc_wx ? x.h->at<__nv_bfloat16>(L.wb_hi) : nullptr,
+                                         (x.tc_wx && L.wb_lo) ? x.h->at<__nv_bfloat16>(L.wb_lo) : nullptr,
+                                         (int)round_up(x.n, 8), st);
+    };
+    cudaError_t e = ensf::tc_autotune(h->tc, tc_gram ? &ga : nullptr, tc_wx ? &wa : nullptr, h->sms, s, rep,
+                                      tc_gram ? +after : nullptr, &sctx);
+    if (e != cudaSuccess) return cuda_fail(e, "tc_autotune");
     return ENSF_OK;
 }
 
@@ -602,76 +694,36 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
         return fail(ENSF_EINVAL, "ensf_autotune: the stream is capturing; tune before capture");
-    const int K = 100;
-    st = analysis_prep(h, prior, n, d, K, eps, sigma_obs, obs_op, noise, out, s);
-    if (st != ENSF_OK) return st;
-    ensf::StepCoef c = step_coef(K / 2, K, eps, sigma_obs, obs_op);
-    NoiseRequest nr;
-    const bool pregen = tc_wx && !noise->buf && !(h->cfg.flags & ENSF_FLAG_INLINE_NOISE);
-    if (pregen && tc_gram) {
-        nr.slice = h->at<float>(h->L.noise);
-        nr.seed = noise->seed;
-        nr.offset = noise->offset;
-        nr.k = K / 2 + 1;
-    }
-    st = gram_softmax(h, out, n, prior, n, d, c, !tc_wx, s, nr);  // fills W for the W X trials
-    if (st != ENSF_OK) return st;
-    ensf::TcGramArgs ga;
-    if (tc_gram) {
-        const Layout &L = h->L;
-        ga.zb_hi = h->at<__nv_bfloat16>(L.zb_hi);
-        ga.zb_lo = L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
-        ga.xb_hi = h->at<__nv_bfloat16>(L.xb_hi);
-        ga.xb_lo = L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr;
-        ga.n = n;
-        ga.n_x = n;
-        ga.d = d;
-        ga.split3 = (h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
-        ga.partial = h->at<float>(L.partial);
-        ga.partial_cap = L.partial_floats;
-        ga.err = h->err();
-        ga.noise = nr.slice;
-        ga.seed = nr.seed;
-        ga.offset = nr.offset;
-        ga.noise_k = nr.k;
-        ga.z32 = out;
-        ga.centre = h->at<float>(L.xbar);
-        ga.alpha = c.alpha;
-        if (h->cfg.gram == ENSF_PREC_TF32) {
-            ga.tf32 = true;
-            ga.zc32 = h->at<float>(L.zb_hi);
-            ga.xc32 = h->at<float>(L.xb_hi);
+    // With both stages on the tensor cores and Philox noise, the noise can be
+    // made by the Gram's idle warps a step ahead (one [n][d] slice written and
+    // read back) or evaluated inside the W X epilogue: tune both ways and keep
+    // the cheaper Gram + softmax + W X.
+    const bool both = tc_gram && tc_wx && !noise->buf && !(h->cfg.flags & ENSF_FLAG_INLINE_NOISE);
+    const auto key = std::make_pair(n, d);
+    ensf::TcTuneReport r;
+    if (!both) {
+        st = autotune_pass(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, eps, noise, out, s, &r);
+        if (st != ENSF_OK) return st;
+    } else {
+        ensf::TcTuneReport r_slice, r_inline;
+        h->noise_inline[key] = false;
+        st = autotune_pass(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, eps, noise, out, s, &r_slice);
+        if (st != ENSF_OK) return st;
+        h->noise_inline[key] = true;
+        st = autotune_pass(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, eps, noise, out, s, &r_inline);
+        if (st != ENSF_OK) return st;
+        const bool inl = r_inline.gram_ms + r_inline.wx_ms < r_slice.gram_ms + r_slice.wx_ms;
+        h->noise_inline[key] = inl;
+        r = inl ? r_inline : r_slice;
+        if (!inl) {  // the second pass overwrote the shapes of the first: record them again
+            ensf::GramChoice g{r.gram_bn, r.gram_stages, r.gram_splits, r.gram_bk, r.gram_pair};
+            g.noise_warps = r.gram_noise_warps;
+            g.a_fp32 = r.gram_a_fp32;
+            if (ensf::tc_set_tuning(h->tc, n, n, d, h->cfg.gram == ENSF_PREC_SPLIT_BF16X3, g, r.wx_bn,
+                                    h->cfg.wx == ENSF_PREC_SPLIT_BF16X3, h->cfg.gram == ENSF_PREC_TF32) != cudaSuccess)
+                return fail(ENSF_ECUDA, "ensf_autotune: could not record the chosen launch shapes");
         }
     }
-    ensf::TcWxArgs wa;
-    if (tc_wx) {
-        if (pregen && !tc_gram)
-            ENSF_CUDA(ensf::launch_noise_slice(noise->seed, noise->offset, K / 2 + 1, n, d, h->at<float>(h->L.noise),
-                                               1 << 30, s));
-        wa = wx_args(h, n, d, y, obs_mask, noise, out, c, step_coef(K / 2 + 1, K, eps, sigma_obs, obs_op).alpha, K / 2);
-        if (noise->buf) wa.noise = noise->buf;  // any valid slice will do for timing
-    }
-    // judge each Gram shape by Gram + the softmax that consumes its partials
-    struct SoftmaxCtx {
-        ensf_handle *h;
-        int n;
-        ensf::StepCoef c;
-        bool tc_wx;
-    } sctx{h, n, c, tc_wx};
-    auto after = [](void *vp, int splits, int64_t part_stride, int ldp, cudaStream_t st) -> cudaError_t {
-        const SoftmaxCtx &x = *static_cast<const SoftmaxCtx *>(vp);
-        const Layout &L = x.h->L;
-        return ensf::launch_softmax_rows(x.h->at<float>(L.partial), splits, part_stride, ldp, x.n, x.n,
-                                         x.h->at<double>(L.norms), x.c.alpha_d, x.c.inv_2beta2_d,
-                                         x.tc_wx ? nullptr : x.h->at<float>(L.w), x.n,
-                                         x.tc_wx ? x.h->at<__nv_bfloat16>(L.wb_hi) : nullptr,
-                                         (x.tc_wx && L.wb_lo) ? x.h->at<__nv_bfloat16>(L.wb_lo) : nullptr,
-                                         (int)round_up(x.n, 8), st);
-    };
-    ensf::TcTuneReport r;
-    cudaError_t e = ensf::tc_autotune(h->tc, tc_gram ? &ga : nullptr, tc_wx ? &wa : nullptr, h->sms, s, &r,
-                                      tc_gram ? +after : nullptr, &sctx);
-    if (e != cudaSuccess) return cuda_fail(e, "tc_autotune");
     if (report) {
         report->gram_tile_n = r.gram_bn;
         report->gram_stages = r.gram_stages;
@@ -683,6 +735,7 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         report->gram_cta_pair = r.gram_pair;
         report->gram_noise_warps = r.gram_noise_warps;
         report->gram_fp32_particles = r.gram_a_fp32;
+        report->noise_inline = h->inline_noise(n, d) ? 1 : 0;
     }
     return ENSF_OK;
 }
@@ -705,6 +758,7 @@ ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning 
     if (ensf::tc_set_tuning(h->tc, n, n, d, split3, g, is_tc(h->cfg.wx) ? t->wx_tile_n : 0, wx_split,
                             h->cfg.gram == ENSF_PREC_TF32) != cudaSuccess)
         return fail(ENSF_EINVAL, "ensf_set_tuning: no kernel for that launch shape");
+    h->noise_inline[std::make_pair(n, d)] = t->noise_inline != 0;
     return ENSF_OK;
 }
 

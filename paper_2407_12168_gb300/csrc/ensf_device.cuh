@@ -88,6 +88,35 @@ __device__ __forceinline__ float em_update(const StepCoef &c, float z, float u, 
 }
 
 
+// Knuth's TwoSum: (hi, lo) += v with the rounding error of hi + v carried
+// into lo, so hi + lo keeps about twice FP32's precision.  Explicit _rn
+// intrinsics keep the compiler from contracting or reordering the steps.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+// sum_{s0 <= s < s1} p[s * stride], ascending s, as a compensated FP32 sum
+// returned in FP64 (error of order s1 - s0 squared times 2^-48 relative to
+// sum |p|; FP64 units are few on this part, FP32 ones are not).  Eight loads
+// are in flight at a time: the partials sit in L2 and each load waits on it.
+__device__ __forceinline__ double sum_partials(const float *__restrict__ p, int64_t stride, int s0, int s1) {
+    float hi = 0.f, lo = 0.f;
+    int s = s0;
+    for (; s + 8 <= s1; s += 8) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + (int64_t)(s + q) * stride);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) df_add(hi, lo, v[q]);
+    }
+    for (; s < s1; ++s) df_add(hi, lo, __ldcg(p + (int64_t)s * stride));
+    return (double)hi + (double)lo;
+}
+
 // One row i of the softmax of Eq. 16 from split-K partial Grams (read through
 // L2 only: they may come from other blocks of the same launch; block of 256
 // threads; lg = n_x doubles of shared memory, red = 256 doubles):
@@ -111,8 +140,7 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
     double lmax = -DBL_MAX;
     if (groups == 1) {
         for (int j = tid; j < n_x; j += 256) {
-            double g = 0.0;
-            for (int s = 0; s < splits; ++s) g += (double)__ldcg(partial + s * part_stride + (int64_t)i * ldp + j);
+            const double g = sum_partials(partial + (int64_t)i * ldp + j, part_stride, 0, splits);
             double l = (2.0 * alpha * g - alpha * alpha * norms[j]) * inv_2beta2;
             lg[j] = l;
             lmax = fmax(lmax, l);
@@ -120,10 +148,8 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
     } else {
         const int j = tid % n_x, grp = tid / n_x;
         if (grp < groups) {
-            double g = 0.0;
             const int s0 = grp * per, s1 = min(splits, s0 + per);
-            for (int s = s0; s < s1; ++s) g += (double)__ldcg(partial + s * part_stride + (int64_t)i * ldp + j);
-            red[grp * n_x + j] = g;
+            red[grp * n_x + j] = sum_partials(partial + (int64_t)i * ldp + j, part_stride, s0, s1);
         }
         __syncthreads();
         if (tid < n_x) {

@@ -26,14 +26,6 @@ __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast
 // is updated with Knuth's error-free two-sum, so the per-thread sums carry
 // about 48 bits at FP32 speed (GB300 issues FP64 at a small fraction of the
 // FP32 rate); the 256 thread sums are combined in FP64 in a fixed order.
-__device__ __forceinline__ void df_add(float &hi, float &lo, float v) {
-    const float s = __fadd_rn(hi, v);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
-    hi = s;
-    lo = __fadd_rn(lo, err);
-}
-
 __device__ __forceinline__ void df_add_square(float &hi, float &lo, float v) {
     const float p = __fmul_rn(v, v);
     const float e = fmaf(v, v, -p);  // v*v - p exactly

@@ -1980,11 +1980,19 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
             }
         GramChoice best = default_gram_choice(*g);
         float best_ms = 1e30f;
+        for (const Cand &c : cands) best_ms = std::min(best_ms, c.ms);
+        // within 1 % of the fastest (timing noise), the fewest split-K slices:
+        // fewer partial Grams written, read by the softmax and held in L2
+        float chosen_ms = 1e30f;
+        int chosen_splits = 1 << 30;
         for (const Cand &c : cands)
-            if (c.ms < best_ms) {
-                best_ms = c.ms;
+            if (c.ms <= best_ms * 1.01f &&
+                (c.ch.splits < chosen_splits || (c.ch.splits == chosen_splits && c.ms < chosen_ms))) {
+                chosen_splits = c.ch.splits;
+                chosen_ms = c.ms;
                 best = c.ch;
             }
+        best_ms = chosen_ms;
         std::lock_guard<std::mutex> lock(ctx->mu);
         ctx->gram_tuned[std::make_tuple(g->n, g->n_x, g->d, g->split3)] = best;
         if (rep) {

@@ -247,6 +247,7 @@ def test_autotuned_analysis_matches_oracle():
     rep = f.autotune(prior, y, None, p.sigma_obs, p.eps, p.obs_op, seed=7)
     assert rep["gram_tile_n"] in (128, 256) and rep["wx_tile_n"] in (64, 128, 256)
     assert rep["gram_splits"] >= 1 and rep["gram_ms"] > 0 and rep["wx_ms"] > 0
+    assert rep["noise_inline"] in (0, 1)
     got = _gpu_analysis(p, "split", "split", filt=f)
     ref = run_oracle(p)
     cond = conditioning(p, ref, prec="split")
@@ -320,6 +321,20 @@ def test_inline_noise_is_bitwise_the_pregenerated_noise():
     outs = []
     for inline in (False, True):
         f = ensf.Filter(p.n, p.d, gram="split", wx="bf16", inline_noise=inline)
+        outs.append(_gpu_analysis(p, "split", "bf16", filt=f))
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_recorded_noise_placement_is_bitwise():
+    """The noise placement recorded for a shape (by ensf_set_tuning here, by
+    ensf_autotune otherwise) moves the draws from the Gram's spare warps to the
+    W X epilogue without changing them: both analyses are bitwise equal."""
+    p = inputs.small_case(seed=33, n=128, grid=32, layers=2, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
+    from paper_2407_12168_gb300 import ensf
+    outs = []
+    for inl in (0, 1):
+        f = ensf.Filter(p.n, p.d, gram="split", wx="bf16")
+        f.set_tuning(p.n, p.d, 128, 3, gram_splits=2, wx_tile_n=128, noise_inline=inl)
         outs.append(_gpu_analysis(p, "split", "bf16", filt=f))
     np.testing.assert_array_equal(outs[0], outs[1])
 
