@@ -325,16 +325,18 @@ def test_inline_noise_is_bitwise_the_pregenerated_noise():
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
-def test_recorded_noise_placement_is_bitwise():
+@pytest.mark.parametrize("wx_tile", [64, 128, 256])
+def test_recorded_noise_placement_is_bitwise(wx_tile):
     """The noise placement recorded for a shape (by ensf_set_tuning here, by
     ensf_autotune otherwise) moves the draws from the Gram's spare warps to the
-    W X epilogue without changing them: both analyses are bitwise equal."""
-    p = inputs.small_case(seed=33, n=128, grid=32, layers=2, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
+    W X epilogue without changing them: both analyses are bitwise equal
+    (130 particles: the last W X column group is ragged)."""
+    p = inputs.small_case(seed=33, n=130, grid=32, layers=2, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
     from paper_2407_12168_gb300 import ensf
     outs = []
     for inl in (0, 1):
         f = ensf.Filter(p.n, p.d, gram="split", wx="bf16")
-        f.set_tuning(p.n, p.d, 128, 3, gram_splits=2, wx_tile_n=128, noise_inline=inl)
+        f.set_tuning(p.n, p.d, 128, 3, gram_splits=2, wx_tile_n=wx_tile, noise_inline=inl)
         outs.append(_gpu_analysis(p, "split", "bf16", filt=f))
     np.testing.assert_array_equal(outs[0], outs[1])
 
