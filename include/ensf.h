@@ -166,7 +166,9 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
  * (128, 6, 32), (256, 4, 32), (256, 3, 32), and with gram_cta_pair = 1
  * (256, 3, 64) when n is a multiple of 256 (optionally with
  * gram_fp32_particles = 1); for the BF16 Gram: (128, 6, 64),
- * (256, 4, 64), (128, 12, 32), (256, 8, 32).  EINVAL for any other shape, for
+ * (256, 4, 64), (128, 12, 32), (256, 8, 32); for the TF32 Gram: (128, 6, 32),
+ * (256, 4, 32), and with gram_cta_pair = 1 (256, 6, 32) when n is a
+ * multiple of 256.  EINVAL for any other shape, for
  * n or d outside the handle's limits, or for a handle whose Gram runs on
  * CUDA cores. */
 ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning *t);

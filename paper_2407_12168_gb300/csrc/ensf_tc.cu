@@ -480,14 +480,20 @@ k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUte
 // and the deallocation are reached by every thread of both CTAs (no early
 // exit), and the decision to skip the work after an earlier failure is taken
 // jointly by the pair.
-constexpr int kPairStages = 3;
+constexpr int kPairStages = 3;      // split-BF16x3: 64 KB per k-block
+constexpr int kPairStagesTf32 = 6;  // TF32: 32 KB per k-block
 constexpr int kPairTile = 256;
 
+// Per k-block of 128 bytes per row (64 BF16 or 32 FP32 elements): this CTA's
+// 128 rows of A and of B, as hi and lo planes (split-BF16x3) or one FP32
+// plane each (TF32).
+template <bool TF32>
 struct PairPlan {
-    static constexpr int kA = 128 * BK * 2;  // this CTA's 128 rows of A, one plane
-    static constexpr int kB = 128 * BK * 2;  // this CTA's 128 rows of B, one plane
-    static constexpr int kStage = (kA + kB) * 2;
-    static constexpr int kBarOff = kStage * kPairStages + 32 * 1024;  // + guard after the ring
+    static constexpr int kStages = TF32 ? kPairStagesTf32 : kPairStages;
+    static constexpr int kA = 128 * 128;  // this CTA's 128 rows of A, one plane
+    static constexpr int kB = 128 * 128;  // this CTA's 128 rows of B, one plane
+    static constexpr int kStage = (kA + kB) * (TF32 ? 1 : 2);
+    static constexpr int kBarOff = kStage * kStages + 32 * 1024;  // + guard after the ring
     static constexpr int kBytes = kBarOff + 256 + 1024;
     static_assert(kBytes <= 227 * 1024, "shared memory plan too large");
 };
@@ -563,6 +569,15 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint6
         : "memory");
 }
 
+__device__ __forceinline__ void mma_tf32_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 // Arrive on the barrier at this offset in both CTAs of the pair once the
 // leader's MMAs issued so far have completed.
 __device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
@@ -573,16 +588,21 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
         : "memory");
 }
 
+// TF32: one FP32 plane per operand (a_hi, b_hi; a_lo, b_lo unused), k-blocks
+// of 32 elements, one kind::tf32 product (K = 8 per MMA).
+template <bool TF32>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGramThreads, 1)
 k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
                const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
-    using P = PairPlan;
+    using P = PairPlan<TF32>;
+    constexpr int NST = P::kStages;          // ring depth
+    constexpr int KBW = TF32 ? 32 : BK;      // k-block width in elements
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     uint8_t *tiles = smem_raw + pad;
     uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
-    uint64_t *empty = full + kPairStages;
-    uint64_t *accum = empty + kPairStages;
+    uint64_t *empty = full + NST;
+    uint64_t *accum = empty + NST;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *skip_own = abort_flag + 1;
@@ -599,7 +619,7 @@ k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__
     int nkb = min(p.kblocks, kb0 + p.kb_per_split) - kb0;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kPairStages; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], leader ? 2 : 1);
             mbar_init(&empty[s], 1);
         }
@@ -628,23 +648,28 @@ k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__
         if (lane == 0) {
             int issued = 0;
             for (int i = 0; i < nkb; ++i) {
-                const int s = i % kPairStages;
-                const uint32_t ph = (i / kPairStages) & 1;
+                const int s = i % NST;
+                const uint32_t ph = (i / NST) & 1;
                 if (!mbar_wait_cl(&empty[s], ph ^ 1u, abort_flag, p.err)) break;
                 const uint32_t st = smem_u32(tiles + s * P::kStage);
                 mbar_expect_tx(&full[s], P::kStage);
-                const int kx = (kb0 + i) * BK;
-                tma_load_2d(st, &a_hi, &full[s], kx, m_own);
-                tma_load_2d(st + P::kA, &a_lo, &full[s], kx, m_own);
-                tma_load_2d(st + 2 * P::kA, &b_hi, &full[s], kx, n_own);
-                tma_load_2d(st + 2 * P::kA + P::kB, &b_lo, &full[s], kx, n_own);
+                const int kx = (kb0 + i) * KBW;
+                if (TF32) {
+                    tma_load_2d(st, &a_hi, &full[s], kx, m_own);
+                    tma_load_2d(st + P::kA, &b_hi, &full[s], kx, n_own);
+                } else {
+                    tma_load_2d(st, &a_hi, &full[s], kx, m_own);
+                    tma_load_2d(st + P::kA, &a_lo, &full[s], kx, m_own);
+                    tma_load_2d(st + 2 * P::kA, &b_hi, &full[s], kx, n_own);
+                    tma_load_2d(st + 2 * P::kA + P::kB, &b_lo, &full[s], kx, n_own);
+                }
                 issued = i + 1;
             }
             if (*abort_flag) {
                 const uint64_t t0 = globaltimer();
-                for (int i = issued > kPairStages ? issued - kPairStages : 0; i < issued; ++i) {
-                    const int s = i % kPairStages;
-                    while (!mbar_try_wait(&full[s], (i / kPairStages) & 1) && globaltimer() - t0 < kTimeoutNs) {
+                for (int i = issued > NST ? issued - NST : 0; i < issued; ++i) {
+                    const int s = i % NST;
+                    while (!mbar_try_wait(&full[s], (i / NST) & 1) && globaltimer() - t0 < kTimeoutNs) {
                     }
                 }
             }
@@ -652,23 +677,33 @@ k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__
     } else if (warp == 1) {
         if (lane == 0) {
             if (leader) {
-                constexpr uint32_t idesc = idesc_bf16(2 * BM, kPairTile);
+                constexpr uint32_t idesc = TF32 ? idesc_tf32(2 * BM, kPairTile) : idesc_bf16(2 * BM, kPairTile);
                 for (int i = 0; i < nkb; ++i) {
-                    const int s = i % kPairStages;
-                    const uint32_t ph = (i / kPairStages) & 1;
+                    const int s = i % NST;
+                    const uint32_t ph = (i / NST) & 1;
                     if (!mbar_wait_cl(&full[s], ph, abort_flag, p.err)) break;
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(tiles + s * P::kStage);
-                    const uint32_t a1 = a0 + P::kA;
-                    const uint32_t b0 = a0 + 2 * P::kA;
-                    const uint32_t b1 = b0 + P::kB;
+                    if (TF32) {
+                        const uint32_t b0 = a0 + P::kA;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint32_t off = kk * 32;
-                        mma_bf16_pair(tmem, desc_sw128(a0 + off), desc_sw128(b0 + off), idesc,
-                                      (i > 0 || kk > 0) ? 1u : 0u);
-                        mma_bf16_pair(tmem, desc_sw128(a0 + off), desc_sw128(b1 + off), idesc, 1u);
-                        mma_bf16_pair(tmem, desc_sw128(a1 + off), desc_sw128(b0 + off), idesc, 1u);
+                        for (int kk = 0; kk < 4; ++kk) {  // K = 8 FP32 = 32 bytes per MMA
+                            const uint32_t off = kk * 32;
+                            mma_tf32_pair(tmem, desc_sw128(a0 + off), desc_sw128(b0 + off), idesc,
+                                          (i > 0 || kk > 0) ? 1u : 0u);
+                        }
+                    } else {
+                        const uint32_t a1 = a0 + P::kA;
+                        const uint32_t b0 = a0 + 2 * P::kA;
+                        const uint32_t b1 = b0 + P::kB;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint32_t off = kk * 32;
+                            mma_bf16_pair(tmem, desc_sw128(a0 + off), desc_sw128(b0 + off), idesc,
+                                          (i > 0 || kk > 0) ? 1u : 0u);
+                            mma_bf16_pair(tmem, desc_sw128(a0 + off), desc_sw128(b1 + off), idesc, 1u);
+                            mma_bf16_pair(tmem, desc_sw128(a1 + off), desc_sw128(b0 + off), idesc, 1u);
+                        }
                     }
                     mma_commit_pair(&empty[s]);
                 }
@@ -676,8 +711,8 @@ k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__
             } else {
                 // forward the completion of this CTA's loads to the leader
                 for (int i = 0; i < nkb; ++i) {
-                    const int s = i % kPairStages;
-                    if (!mbar_wait(&full[s], (i / kPairStages) & 1, abort_flag, p.err)) break;
+                    const int s = i % NST;
+                    if (!mbar_wait(&full[s], (i / NST) & 1, abort_flag, p.err)) break;
                     mbar_arrive_cluster(mapa_shared(smem_u32(&full[s]), 0));
                 }
             }
@@ -1502,10 +1537,12 @@ cudaError_t run_gram_pair_f32(const CUtensorMap (&maps)[4], const GramParams &p,
     return cudaGetLastError();
 }
 
+template <bool TF32>
 cudaError_t run_gram_pair(const CUtensorMap (&maps)[4], const GramParams &p, dim3 grid, cudaStream_t s) {
-    cudaError_t e = set_smem(k_gram_tc_pair, PairPlan::kBytes);
+    using P = PairPlan<TF32>;
+    cudaError_t e = set_smem(k_gram_tc_pair<TF32>, P::kBytes);
     if (e != cudaSuccess) return e;
-    k_gram_tc_pair<<<grid, kGramThreads, PairPlan::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
+    k_gram_tc_pair<TF32><<<grid, kGramThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
     return cudaGetLastError();
 }
 
@@ -1557,11 +1594,13 @@ GramChoice default_gram_choice(const TcGramArgs &a) {
 cudaError_t gram_launch_tf32(TcContext *ctx, const TcGramArgs &a, int sms, const GramChoice &ch, int *splits,
                              int64_t *part_stride, int *ldp, cudaStream_t s) {
     constexpr int KB = 32;  // 32 FP32 = one 128-byte swizzle row
-    const int BN = ch.bn == 128 ? 128 : 256;
+    // the pair form needs whole 256-row tiles on both sides
+    const bool pair = ch.pair && a.n % kPairTile == 0 && a.n_x % kPairTile == 0;
+    const int BN = (pair || ch.bn != 128) ? 256 : 128;
     CUtensorMap maps[4];
     cudaError_t e;
     if ((e = make_map_f32(ctx, &maps[0], a.zc32, a.d, a.n, BM)) != cudaSuccess) return e;
-    if ((e = make_map_f32(ctx, &maps[2], a.xc32, a.d, a.n_x, BN)) != cudaSuccess) return e;
+    if ((e = make_map_f32(ctx, &maps[2], a.xc32, a.d, a.n_x, pair ? 128 : BN)) != cudaSuccess) return e;
     memset(&maps[1], 0, sizeof(maps[1]));
     memset(&maps[3], 0, sizeof(maps[3]));
     const int mt = (a.n + BM - 1) / BM, nt = (a.n_x + BN - 1) / BN;
@@ -1588,6 +1627,7 @@ cudaError_t gram_launch_tf32(TcContext *ctx, const TcGramArgs &a, int sms, const
     *part_stride = per_split;
     *ldp = a.n_x;
     dim3 grid(mt, nt, S);
+    if (pair) return run_gram_pair<true>(maps, p, grid, s);  // mt = 2 x pair tiles: one CTA per 128 rows
     if (BN == 256) return run_gram<256, 4, false, KB, 4>(maps, p, grid, s);
     return run_gram<128, 6, false, KB, 4>(maps, p, grid, s);
 }
@@ -1642,7 +1682,7 @@ cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const Gram
     *ldp = a.n_x;
     dim3 grid(mt, nt, S);
     if (f32a) return run_gram_pair_f32(maps, p, grid, s);
-    if (pair) return run_gram_pair(maps, p, grid, s);  // mt = 2 x pair tiles: one CTA per 128 rows
+    if (pair) return run_gram_pair<false>(maps, p, grid, s);  // mt = 2 x pair tiles: one CTA per 128 rows
     if (KB == 32) {  // narrow k-blocks: twice the ring depth for the same bytes in flight
         if (a.split3) {
             if (BN == 256) return ch.stages == 3 ? run_gram<256, 3, true, 32>(maps, p, grid, s)
@@ -1731,7 +1771,10 @@ cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3
     const int bk = g.bk ? g.bk : BK;
     bool ok;
     if (tf32)
-        ok = !g.pair && (bk == 32 || g.bk == 0) && ((g.bn == 128 && g.stages == 6) || (g.bn == 256 && g.stages == 4));
+        ok = (bk == 32 || g.bk == 0) &&
+             (g.pair ? (g.bn == kPairTile && g.stages == kPairStagesTf32 && n % kPairTile == 0 &&
+                        n_x % kPairTile == 0 && !g.a_fp32)
+                     : ((g.bn == 128 && g.stages == 6) || (g.bn == 256 && g.stages == 4)));
     else if (g.pair)
         ok = split3 && g.bn == kPairTile && g.stages == kPairStages && bk == BK && n % kPairTile == 0 &&
              n_x % kPairTile == 0;
@@ -1932,20 +1975,27 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
         std::vector<Cand> cands;
         // (tile width, ring depth, k-block width, CTA pair, FP32 particle operand)
         const int shapes[][5] = {{128, 3, 64, 0, 0}, {256, 2, 64, 0, 0}, {256, 3, 64, 1, 0}, {256, 3, 64, 1, 1}};
-        const int shapes_tf32[][5] = {{128, 6, 32, 0, 0}, {256, 4, 32, 0, 0}};
-        const int n_shapes = g->tf32 ? 2 : 4;
+        const int shapes_tf32[][5] = {{128, 6, 32, 0, 0}, {256, 4, 32, 0, 0}, {256, 6, 32, 1, 0}};
+        const int n_shapes = g->tf32 ? 3 : 4;
         for (int si = 0; si < n_shapes; ++si) {
             const int *sh = g->tf32 ? shapes_tf32[si] : shapes[si];
             const int bn = sh[0], kbw = sh[2], pr = sh[3], f32 = sh[4];
             if (f32 && !(g->z32 && w && w->zb_hi)) continue;
-            if (pr && !(g->split3 && g->n % kPairTile == 0 && g->n_x % kPairTile == 0)) continue;
+            if (pr && !((g->split3 || g->tf32) && g->n % kPairTile == 0 && g->n_x % kPairTile == 0)) continue;
             if (bn == 256 && g->n_x <= 128) continue;
-            const int stages = g->split3 ? sh[1] : (bn == 256 ? 4 : 6);
+            const int stages = (g->split3 || g->tf32) ? sh[1] : (bn == 256 ? 4 : 6);
             const int mt = (g->n + BM - 1) / BM, nt = (g->n_x + bn - 1) / bn;
             const int kblocks = static_cast<int>((g->d + kbw - 1) / kbw);
             const int s0 = choose_splits(mt * nt, kblocks, sms, static_cast<int64_t>(g->n) * g->n_x, g->partial_cap);
-            for (int sp : {s0, std::max(1, s0 / 2), s0 * 2, std::max(1, (s0 * 3) / 4), (s0 * 3) / 2,
-                           std::max(1, s0 / 4), std::max(1, s0 / 8)}) {
+            std::vector<int> sps = {s0, std::max(1, s0 / 2), s0 * 2, std::max(1, (s0 * 3) / 4), (s0 * 3) / 2,
+                                    std::max(1, s0 / 4), std::max(1, s0 / 8)};
+            // and the split counts whose CTAs fill whole waves of the SMs
+            // (the grid is tiles x splits CTAs, one resident per SM)
+            for (int w = 1; w <= 8; ++w) {
+                const int sp = (w * sms) / (mt * nt);
+                if (sp >= 1 && std::find(sps.begin(), sps.end(), sp) == sps.end()) sps.push_back(sp);
+            }
+            for (int sp : sps) {
                 GramChoice ch{bn, stages, sp, kbw, pr};
                 ch.a_fp32 = f32;
                 float ms = 0.f;

@@ -515,6 +515,44 @@ def test_pair_gram_ragged_state_matches_oracle(f32):
     assert tie.sum() <= max(1, p.n // 50), describe(rel, tie, bad)
 
 
+def test_tf32_pair_gram_matches_single_cta_bitwise():
+    """The TF32 Gram on a CTA pair (tcgen05 cta_group::2 kind::tf32, 256 x 256
+    tiles, six-deep ring of 32-element k-blocks) accumulates the K = 8 chunks
+    in the single-CTA order: with the same split boundaries the analyses are
+    bitwise those of the two single-CTA TF32 shapes (N = 512)."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    p = inputs.small_case(seed=66, n=512, grid=48, layers=2, K=3, obs_op=1, obs_frac=0.5, sigma_obs=0.5)
+    prior, y = torch.from_numpy(p.prior).cuda(), torch.from_numpy(p.y).cuda()
+    mask = torch.from_numpy(p.mask).cuda()
+    outs = []
+    for pair, bn, stages, nw in [(0, 256, 4, 8), (1, 256, 6, 8), (0, 128, 6, 8), (1, 256, 6, 4)]:
+        f = ensf.Filter(p.n, p.d, gram="tf32", wx="split", check_finite=True)
+        f.set_tuning(p.n, p.d, bn, stages, gram_k_block=32, gram_splits=2, gram_cta_pair=pair,
+                     gram_noise_warps=nw)
+        outs.append(f.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed).cpu().numpy())
+        assert f.status_sync() == 0
+    for o_ in outs[1:]:
+        np.testing.assert_array_equal(o_, outs[0])
+
+
+def test_tf32_pair_gram_ragged_state_matches_oracle():
+    """One TF32 pair tile (N = 256), a ragged state tail (d = 2888 is not a
+    multiple of the 32-wide FP32 k-block) and three uneven splits, against
+    the oracle at the TF32 path's tolerance."""
+    from paper_2407_12168_gb300 import ensf
+    gram, wx, tol = PATHS["tf32"]
+    p = inputs.small_case(seed=67, n=256, grid=38, layers=2, K=5, obs_op=1, obs_frac=0.5, sigma_obs=0.5)
+    ref = run_oracle(p)
+    cond = conditioning(p, ref, prec=_cond_prec(gram, wx))
+    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, check_finite=True)
+    f.set_tuning(p.n, p.d, 256, 6, gram_k_block=32, gram_splits=3, gram_cta_pair=1)
+    got = _gpu_analysis(p, gram, wx, filt=f)
+    rel, tie, bad = compare_members(got, ref, cond, tol)
+    assert not bad.any(), describe(rel, tie, bad)
+    assert tie.sum() <= max(1, p.n // 50), describe(rel, tie, bad)
+
+
 def test_pair_gram_needs_whole_pair_tiles():
     from paper_2407_12168_gb300 import ensf
     f = ensf.Filter(300, 4096, gram="split", wx="bf16")
@@ -523,6 +561,11 @@ def test_pair_gram_needs_whole_pair_tiles():
     g = ensf.Filter(512, 4096, gram="bf16", wx="bf16")
     with pytest.raises(ensf.EnsfError):
         g.set_tuning(512, 4096, 256, 3, gram_cta_pair=1)
+    t = ensf.Filter(300, 4096, gram="tf32", wx="split")
+    with pytest.raises(ensf.EnsfError):  # TF32 pair: whole tiles, ring depth 6
+        t.set_tuning(300, 4096, 256, 6, gram_k_block=32, gram_cta_pair=1)
+    with pytest.raises(ensf.EnsfError):
+        t.set_tuning(256, 4096, 256, 4, gram_k_block=32, gram_cta_pair=1)
 
 
 @pytest.mark.parametrize("f32", [0, 1])
