@@ -530,12 +530,31 @@ def run_ours(args):
     _, prior_rmse = ensf.ensemble_stats(prior, truth_dev)
     # the members themselves, for a per-member comparison with the oracle (small workloads)
     acc_members = acc_out.cpu().numpy() if p.n * p.d <= (64 << 20) else None
+    # the big configuration: 64 members against the stored FP64 oracle rows
+    # (tests/golden/make_large512_subsample.py; the oracle is exact on any
+    # subset of members)
+    subsample = None
+    golden = os.path.join(ROOT, "tests", "golden", "large512_subsample64.npz")
+    if p.name == "large-512" and not J and os.path.exists(golden):
+        g = np.load(golden)
+        sub = acc_out[torch.from_numpy(g["rows"].astype(np.int64)).to(dev)].cpu().numpy().astype(np.float64)
+        truth64 = p.truth.astype(np.float32).astype(np.float64)
+        sub_rmse = float(np.sqrt(np.mean((sub.mean(axis=0) - truth64) ** 2)))
+        ref_vals = g["values"]
+        rel = np.linalg.norm(sub[:, g["idx"]] - ref_vals, axis=1) / np.linalg.norm(ref_vals, axis=1)
+        subsample = {"members": int(len(g["rows"])), "gpu_rmse": sub_rmse, "oracle_rmse": float(g["rmse"]),
+                     "rmse_rel_diff": abs(sub_rmse - float(g["rmse"])) / float(g["rmse"]),
+                     "member_rel_err_on_sampled_entries": {"median": float(np.median(rel)),
+                                                           "max": float(rel.max()), "entries": int(len(g["idx"]))},
+                     "oracle": "FP64, %d host threads, %.0f s" % (int(g["threads"]), float(g["seconds"]))}
     del acc_out
 
     def _rmse(mean):
         return float(np.sqrt(np.mean((mean - p.truth.astype(np.float32).astype(np.float64)) ** 2)))
     accuracy = {"analysis_rmse": float(gpu_rmse.item()), "prior_rmse": float(prior_rmse.item()),
                 "oracle_rmse": None}
+    if subsample is not None:
+        accuracy["oracle_subsample"] = subsample
 
     # ---- max over ranks ----
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, dev)

@@ -142,6 +142,11 @@ typedef struct {
                                 them itself, so the W X step writes no BF16 particle planes */
     int noise_inline;  /* Philox noise with both stages on the tensor cores: 1 = evaluated in the
                           W X epilogue, 0 = written a step ahead by the Gram's idle warps */
+    int pdl;           /* 1: the per-step kernels (Gram, row softmax, W X) are launched with
+                          programmatic dependent launch (each may start while its predecessor
+                          finishes, and waits for it on the device), 0: ordinary launches.
+                          Untuned shapes use it while n * d <= 2^24.  For ensf_set_tuning,
+                          -1 keeps the current choice. */
 } ensf_tuning;
 
 /* Autotuner for the tensor-core stages: times the candidate launch shapes of
@@ -151,6 +156,8 @@ typedef struct {
  * When both stages run on the tensor cores with counter-based noise (no noise
  * buffer, no ENSF_FLAG_INLINE_NOISE), it tunes both noise placements and
  * keeps the one with the smaller Gram + softmax + W X time (noise_inline).
+ * It then times whole steps with and without programmatic dependent launch
+ * (pdl) and keeps the faster.
  * Overwrites `out` and the workspace, synchronises `stream`, and must not be
  * called while the stream is being captured.  `report` may be NULL.  A handle
  * with only CUDA-core precisions returns ENSF_OK with a zeroed report. */
@@ -161,7 +168,7 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
 /* Records launch shapes for analyses of this (n, d) without timing them,
  * e.g. a report saved from ensf_autotune in another process.  Uses the
  * gram_tile_n, gram_stages, gram_splits (0: the cost model), gram_k_block,
- * wx_tile_n (0: unchanged) and noise_inline fields of `t`.  Valid Gram shapes (tile width,
+ * wx_tile_n (0: unchanged), noise_inline and pdl (-1: unchanged) fields of `t`.  Valid Gram shapes (tile width,
  * ring depth, k-block) for the split-BF16x3 Gram: (128, 3, 64), (256, 2, 64),
  * (128, 6, 32), (256, 4, 32), (256, 3, 32), and with gram_cta_pair = 1
  * (256, 3, 64) when n is a multiple of 256 (optionally with

@@ -189,6 +189,20 @@ struct ensf_handle {
         return it != noise_inline.end() && it->second;
     }
 
+    // (n, d) -> whether the per-step kernels (Gram, row softmax, W X) are
+    // launched with programmatic dependent launch, as chosen by ensf_autotune
+    // or ensf_set_tuning
+    std::map<std::pair<int, int64_t>, bool> pdl_tuned;
+
+    // that choice for an (n, d) analysis; untuned shapes use it while a step
+    // moves at most 2^24 particle elements (there the launch gaps are a
+    // sizeable part of a step; with large steps it measured slower)
+    bool use_pdl(int n, int64_t d) const {
+        auto it = pdl_tuned.find(std::make_pair(n, d));
+        if (it != pdl_tuned.end()) return it->second;
+        return static_cast<int64_t>(n) * d <= (int64_t(1) << 24);
+    }
+
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
     int *err() const { return at<int>(L.err); }
 };
@@ -272,6 +286,7 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
             a.zc32 = h->at<float>(L.zb_hi);
             a.xc32 = h->at<float>(L.xb_hi) + (size_t)x0 * d;
         }
+        a.pdl = h->use_pdl(n, d);
         ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_tc(h->tc, a, h->sms, &splits, &part_stride, &ldp, s));
     }
     __nv_bfloat16 *wb_hi = nullptr, *wb_lo = nullptr;
@@ -284,7 +299,7 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
     ENSF_LAUNCH(h, P_SOFTMAX, s,
                 ensf::launch_softmax_rows(partial, splits, part_stride, ldp, n, n_x, h->at<double>(L.norms) + x0,
                                           c.alpha_d, c.inv_2beta2_d, want_fp32 ? h->at<float>(L.w) : nullptr,
-                                          n_x, wb_hi, wb_lo, ldwb, s));
+                                          n_x, wb_hi, wb_lo, ldwb, s, h->use_pdl(n, d)));
     return ENSF_OK;
 }
 
@@ -466,6 +481,7 @@ ensf::TcWxArgs wx_args(ensf_handle *h, int n, int64_t d, const float *y, const u
     a.alpha_next = alpha_next;
     a.coef = c;
     a.err = h->err();
+    a.pdl = h->use_pdl(n, d);
     return a;
 }
 
@@ -606,7 +622,7 @@ ensf_status autotune_pass(ensf_handle *h, const float *prior, int n, int64_t d, 
         ensf::StepCoef c;
         bool tc_wx;
     } sctx{h, n, c, tc_wx};
-    auto after = [](void *vp, int splits, int64_t part_stride, int ldp, cudaStream_t st) -> cudaError_t {
+    auto after = [](void *vp, int splits, int64_t part_stride, int ldp, cudaStream_t st, bool pdl) -> cudaError_t {
         const SoftmaxCtx &x = *static_cast<const SoftmaxCtx *>(vp);
         const Layout &L = x.h->L;
         return ensf::launch_softmax_rows(x.h->at<float>(L.partial), splits, part_stride, ldp, x.n, x.n,
@@ -614,7 +630,7 @@ ensf_status autotune_pass(ensf_handle *h, const float *prior, int n, int64_t d, 
                                          x.tc_wx ? nullptr : x.h->at<float>(L.w), x.n,
                                          x.tc_wx ? x.h->at<__nv_bfloat16>(L.wb_hi) : nullptr,
                                          (x.tc_wx && L.wb_lo) ? x.h->at<__nv_bfloat16>(L.wb_lo) : nullptr,
-                                         (int)round_up(x.n, 8), st);
+                                         (int)round_up(x.n, 8), st, pdl);
     };
     cudaError_t e = ensf::tc_autotune(h->tc, tc_gram ? &ga : nullptr, tc_wx ? &wa : nullptr, h->sms, s, rep,
                                       tc_gram ? +after : nullptr, &sctx);
@@ -724,6 +740,7 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
                 return fail(ENSF_ECUDA, "ensf_autotune: could not record the chosen launch shapes");
         }
     }
+    if (r.pdl >= 0) h->pdl_tuned[key] = r.pdl != 0;
     if (report) {
         report->gram_tile_n = r.gram_bn;
         report->gram_stages = r.gram_stages;
@@ -736,6 +753,7 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         report->gram_noise_warps = r.gram_noise_warps;
         report->gram_fp32_particles = r.gram_a_fp32;
         report->noise_inline = h->inline_noise(n, d) ? 1 : 0;
+        report->pdl = h->use_pdl(n, d) ? 1 : 0;
     }
     return ENSF_OK;
 }
@@ -759,6 +777,7 @@ ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning 
                             h->cfg.gram == ENSF_PREC_TF32) != cudaSuccess)
         return fail(ENSF_EINVAL, "ensf_set_tuning: no kernel for that launch shape");
     h->noise_inline[std::make_pair(n, d)] = t->noise_inline != 0;
+    if (t->pdl == 0 || t->pdl == 1) h->pdl_tuned[std::make_pair(n, d)] = t->pdl == 1;
     return ENSF_OK;
 }
 

@@ -88,6 +88,18 @@ __device__ __forceinline__ float em_update(const StepCoef &c, float z, float u, 
 }
 
 
+// Programmatic dependent launch.  The per-step kernels (Gram, row softmax,
+// W X) are launched with programmatic stream serialization: a kernel may be
+// launched while its predecessor in the stream still runs, so every thread
+// first waits until that predecessor has completed and its writes are
+// visible (pdl_wait), and then lets the next kernel be launched
+// (pdl_launch_dependents), whose blocks in turn wait at their own pdl_wait.
+// Both are no-ops in a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Knuth's TwoSum: (hi, lo) += v with the rounding error of hi + v carried
 // into lo, so hi + lo keeps about twice FP32's precision.  Explicit _rn
 // intrinsics keep the compiler from contracting or reordering the steps.
@@ -101,29 +113,31 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float v) {
 
 // sum_{s0 <= s < s1} p[s * stride], ascending s, as a compensated FP32 sum
 // returned in FP64 (error of order s1 - s0 squared times 2^-48 relative to
-// sum |p|; FP64 units are few on this part, FP32 ones are not).  Eight loads
-// are in flight at a time: the partials sit in L2 and each load waits on it.
+// sum |p|; FP64 units are few on this part, FP32 ones are not).  The loads
+// go out eight at a time, also for a short tail: the partials sit in L2 and
+// each load waits on it.
 __device__ __forceinline__ double sum_partials(const float *__restrict__ p, int64_t stride, int s0, int s1) {
     float hi = 0.f, lo = 0.f;
-    int s = s0;
-    for (; s + 8 <= s1; s += 8) {
+    for (int s = s0; s < s1; s += 8) {
         float v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + (int64_t)(s + q) * stride);
+        for (int q = 0; q < 8; ++q) v[q] = (s + q < s1) ? __ldcg(p + (int64_t)(s + q) * stride) : 0.f;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) df_add(hi, lo, v[q]);
+        for (int q = 0; q < 8; ++q)
+            if (s + q < s1) df_add(hi, lo, v[q]);
     }
-    for (; s < s1; ++s) df_add(hi, lo, __ldcg(p + (int64_t)s * stride));
     return (double)hi + (double)lo;
 }
 
 // One row i of the softmax of Eq. 16 from split-K partial Grams (read through
-// L2 only: they may come from other blocks of the same launch; block of 256
-// threads; lg = n_x doubles of shared memory, red = 256 doubles):
+// L2 only: they may come from other blocks of the same launch; block of NT
+// threads; lg = n_x doubles of shared memory, red = NT doubles):
 //   G_ij = sum_s partial[s][i][j]  (fixed order: deterministic),
 //   l_ij = (2 alpha G_ij - alpha^2 |x_j|^2) / (2 beta^2), w_ij = softmax_j(l_ij).
 // Writes FP32 w and/or the BF16 split w = w_hi + w_lo.  When the row is short,
-// `groups` threads share a column j, each summing a fixed range of splits.
+// `groups` threads share a column j, each summing a fixed range of splits
+// (the group sums are then added in group order: deterministic).
+template <int NT>
 __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ partial, int splits,
                                             int64_t part_stride, int ldp, int n_x,
                                             const double *__restrict__ norms, double alpha,
@@ -132,14 +146,11 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
                                             __nv_bfloat16 *__restrict__ w_lo, int ldwb, double *lg,
                                             double *red) {
     const int tid = threadIdx.x;
-    // sum of the split-K partials: when the row is short, `groups` threads
-    // share one column j, each summing a fixed range of splits; the group
-    // sums are then added in group order (deterministic)
-    const int groups = n_x >= 256 ? 1 : min(256 / n_x, splits);
+    const int groups = n_x >= NT ? 1 : min(NT / n_x, splits);
     const int per = (splits + groups - 1) / groups;
     double lmax = -DBL_MAX;
     if (groups == 1) {
-        for (int j = tid; j < n_x; j += 256) {
+        for (int j = tid; j < n_x; j += NT) {
             const double g = sum_partials(partial + (int64_t)i * ldp + j, part_stride, 0, splits);
             double l = (2.0 * alpha * g - alpha * alpha * norms[j]) * inv_2beta2;
             lg[j] = l;
@@ -163,26 +174,26 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
     }
     red[tid] = lmax;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
+    for (int s = NT / 2; s > 0; s >>= 1) {
         if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
         __syncthreads();
     }
     const double m = red[0];
     __syncthreads();
     double sum = 0.0;
-    for (int j = tid; j < n_x; j += 256) {
+    for (int j = tid; j < n_x; j += NT) {
         double e = (double)expf((float)(lg[j] - m));
         lg[j] = e;
         sum += e;
     }
     red[tid] = sum;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
+    for (int s = NT / 2; s > 0; s >>= 1) {
         if (tid < s) red[tid] += red[tid + s];
         __syncthreads();
     }
     const double inv = 1.0 / red[0];
-    for (int j = tid; j < n_x; j += 256) {
+    for (int j = tid; j < n_x; j += NT) {
         float wv = (float)(lg[j] * inv);
         if (w) w[(int64_t)i * ldw + j] = wv;
         if (w_hi) {

@@ -10,6 +10,24 @@
 
 namespace ensf {
 
+// Launch `kern`; with `pdl`, with programmatic stream serialization (the
+// kernel must begin with pdl_wait(); see ensf_device.cuh).
+template <class... KArgs, class... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                     Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 // ---- CUDA-core kernels (ensf_simt.cu) ----------------------------------
 // z[i][c] <- xi[0][i][c] (noise buffer or Philox stream)
 cudaError_t launch_init_particles(float *z, int n, int64_t d, const float *noise_buf,
@@ -35,7 +53,7 @@ cudaError_t launch_gram_fp32(const float *z, int n, const float *x, int n_x, int
 cudaError_t launch_softmax_rows(const float *partial, int splits, int64_t part_stride, int ldp,
                                 int n, int n_x, const double *norms, double alpha,
                                 double inv_2beta2, float *w, int ldw, __nv_bfloat16 *w_hi,
-                                __nv_bfloat16 *w_lo, int ldwb, cudaStream_t s);
+                                __nv_bfloat16 *w_lo, int ldwb, cudaStream_t s, bool pdl = false);
 // z <- EM step with u = W X computed on FP32 CUDA cores, fused epilogue.
 cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, int n_x, int64_t d,
                               float *z, const float *y, const uint8_t *mask,

@@ -198,15 +198,19 @@ k_gram_fp32(const float *__restrict__ z, int n, const float *__restrict__ x, int
 // ---------------------------------------------------------------------------
 // Row softmax of the logits  l_ij = (2 alpha G_ij - alpha^2 |x_j|^2) / (2 beta^2)
 // (Eq. 12 expanded; the row constant -|z_i|^2/(2 beta^2) cancels in Eq. 16).
-__global__ void __launch_bounds__(256)
+// NT threads per row.
+template <int NT>
+__global__ void __launch_bounds__(NT)
 k_softmax_rows(const float *__restrict__ partial, int splits, int64_t part_stride, int ldp,
                int n_x, const double *__restrict__ norms, double alpha, double inv_2beta2,
                float *__restrict__ w, int ldw, __nv_bfloat16 *__restrict__ w_hi,
                __nv_bfloat16 *__restrict__ w_lo, int ldwb) {
+    pdl_wait();
+    pdl_launch_dependents();
     extern __shared__ double lg[];
-    __shared__ double red[256];
-    softmax_row(blockIdx.x, partial, splits, part_stride, ldp, n_x, norms, alpha, inv_2beta2, w, ldw, w_hi, w_lo,
-                ldwb, lg, red);
+    __shared__ double red[NT];
+    softmax_row<NT>(blockIdx.x, partial, splits, part_stride, ldp, n_x, norms, alpha, inv_2beta2, w, ldw, w_hi,
+                    w_lo, ldwb, lg, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -525,15 +529,17 @@ cudaError_t launch_gram_fp32(const float *z, int n, const float *x, int n_x, int
 cudaError_t launch_softmax_rows(const float *partial, int splits, int64_t part_stride, int ldp, int n,
                                 int n_x, const double *norms, double alpha, double inv_2beta2,
                                 float *w, int ldw, __nv_bfloat16 *w_hi, __nv_bfloat16 *w_lo, int ldwb,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool pdl) {
     size_t smem = sizeof(double) * (size_t)n_x;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_softmax_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 46 * 1024) {  // (beside the static 2 KB reduction buffer)
+        cudaError_t e = cudaFuncSetAttribute(k_softmax_rows<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_softmax_rows<<<n, 256, smem, s>>>(partial, splits, part_stride, ldp, n_x, norms, alpha, inv_2beta2,
-                                        w, ldw, w_hi, w_lo, ldwb);
-    return cudaGetLastError();
+    // (1024-thread rows, which spread short rows' partials over more threads,
+    // measured slower: 16 against 10 us per launch on 20- and 128-member rows)
+    return launch_k(k_softmax_rows<256>, dim3(n), dim3(256), smem, s, pdl, partial, splits, part_stride, ldp, n_x,
+                    norms, alpha, inv_2beta2, w, ldw, w_hi, w_lo, ldwb);
 }
 
 cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, int n_x, int64_t d,

@@ -185,8 +185,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_analysis_small(SmallArgs a
 
         // ---- B: softmax rows ----
         for (int i = blockIdx.x; i < n; i += gridDim.x) {
-            softmax_row(i, a.partial, a.gram_blocks, (int64_t)n * n, n, n, a.norms, c.alpha_d, c.inv_2beta2_d, a.w,
-                        n, nullptr, nullptr, 0, lg, red);
+            softmax_row<256>(i, a.partial, a.gram_blocks, (int64_t)n * n, n, n, a.norms, c.alpha_d,
+                             c.inv_2beta2_d, a.w, n, nullptr, nullptr, 0, lg, red);
             __syncthreads();
         }
         if (!grid_barrier(a.bar, a.err)) return;

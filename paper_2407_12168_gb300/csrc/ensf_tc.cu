@@ -42,6 +42,7 @@
 #include <tuple>
 #include <vector>
 
+#include "ensf_internal.h"
 #include "ensf_tc.h"
 
 namespace ensf {
@@ -384,6 +385,7 @@ struct GramParams {
     // FP32-operand form: A = z - alpha m split in the kernel (centre m, [d])
     float alpha;
     const float *centre;
+    bool pdl;  // host: launched with programmatic stream serialization
 };
 
 // This CTA's share of the next step's noise slice, written while the MMAs
@@ -421,6 +423,8 @@ template <int BN, int STAGES, bool SPLIT, int KB, int ES = 2>
 __global__ void __launch_bounds__(kGramThreads, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
           const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
+    pdl_wait();  // reads the particle planes of the previous step's W X
+    pdl_launch_dependents();
     using P = Plan<BN, STAGES, SPLIT, KB, ES>;
     extern __shared__ uint8_t smem_raw[];
     const Ctl c = carve<P>(smem_raw, STAGES);
@@ -594,6 +598,8 @@ template <bool TF32>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGramThreads, 1)
 k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
                const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
+    pdl_wait();  // reads the particle planes of the previous step's W X
+    pdl_launch_dependents();
     using P = PairPlan<TF32>;
     constexpr int NST = P::kStages;          // ring depth
     constexpr int KBW = TF32 ? 32 : BK;      // k-block width in elements
@@ -805,6 +811,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_k, __nv_bfloat1
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairF32Threads, 1)
 k_gram_tc_pair_f32(const __grid_constant__ CUtensorMap z32, const __grid_constant__ CUtensorMap unused,
                    const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo, GramParams p) {
+    pdl_wait();  // reads the particles written by the previous step's W X
+    pdl_launch_dependents();
     using P = PairF32Plan;
     constexpr int S = kPairF32Stages;
     extern __shared__ uint8_t smem_raw[];
@@ -1036,6 +1044,7 @@ struct WxParams {
     float alpha_next;    // z_hi/z_lo carry z - alpha_next m for the next Gram
     StepCoef coef;
     int *err;
+    bool pdl;  // host: launched with programmatic stream serialization
 };
 
 
@@ -1043,6 +1052,8 @@ template <int BN, int STAGES, bool SPLIT, bool INLINE_NOISE>
 __global__ void __launch_bounds__(kWxThreads, 1)
 k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CUtensorMap xt_lo,
            const __grid_constant__ CUtensorMap w_hi, const __grid_constant__ CUtensorMap w_lo, WxParams p) {
+    pdl_wait();  // reads the weights of the row softmax
+    pdl_launch_dependents();
     using P = WxPlan<BN, STAGES, SPLIT>;
     extern __shared__ uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1269,8 +1280,8 @@ k_softmax_batched(const BRow *__restrict__ rows, const BInst *__restrict__ insts
     __shared__ double red[256];
     const BRow r = rows[blockIdx.x];
     const BInst &I = insts[r.inst];
-    softmax_row(r.row, I.partial, I.splits, static_cast<int64_t>(I.n) * I.n, I.n, I.n, I.norms, alpha, inv_2beta2,
-                nullptr, 0, I.wb_hi, I.wb_lo, I.ldw, lg, red);
+    softmax_row<256>(r.row, I.partial, I.splits, static_cast<int64_t>(I.n) * I.n, I.n, I.n, I.norms, alpha,
+                     inv_2beta2, nullptr, 0, I.wb_hi, I.wb_lo, I.ldw, lg, red);
 }
 
 // Persistent W X + EM over the tile list of all instances (U^T = X^T W^T as in
@@ -1526,15 +1537,14 @@ cudaError_t run_gram(const CUtensorMap (&maps)[4], const GramParams &p, dim3 gri
     auto kern = k_gram_tc<BN, STAGES, SPLIT, KB, ES>;
     cudaError_t e = set_smem(kern, P::kBytes);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kGramThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
-    return cudaGetLastError();
+    return launch_k(kern, grid, dim3(kGramThreads), P::kBytes, s, p.pdl, maps[0], maps[1], maps[2], maps[3], p);
 }
 
 cudaError_t run_gram_pair_f32(const CUtensorMap (&maps)[4], const GramParams &p, dim3 grid, cudaStream_t s) {
     cudaError_t e = set_smem(k_gram_tc_pair_f32, PairF32Plan::kBytes);
     if (e != cudaSuccess) return e;
-    k_gram_tc_pair_f32<<<grid, kPairF32Threads, PairF32Plan::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
-    return cudaGetLastError();
+    return launch_k(k_gram_tc_pair_f32, grid, dim3(kPairF32Threads), PairF32Plan::kBytes, s, p.pdl, maps[0],
+                    maps[1], maps[2], maps[3], p);
 }
 
 template <bool TF32>
@@ -1542,8 +1552,8 @@ cudaError_t run_gram_pair(const CUtensorMap (&maps)[4], const GramParams &p, dim
     using P = PairPlan<TF32>;
     cudaError_t e = set_smem(k_gram_tc_pair<TF32>, P::kBytes);
     if (e != cudaSuccess) return e;
-    k_gram_tc_pair<TF32><<<grid, kGramThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
-    return cudaGetLastError();
+    return launch_k(k_gram_tc_pair<TF32>, grid, dim3(kGramThreads), P::kBytes, s, p.pdl, maps[0], maps[1],
+                    maps[2], maps[3], p);
 }
 
 template <int BN, int STAGES, bool SPLIT, bool INLINE_NOISE>
@@ -1555,8 +1565,7 @@ cudaError_t run_wx(const CUtensorMap (&maps)[4], WxParams p, int sms, cudaStream
     p.n_tiles = (p.n + BN - 1) / BN;
     const int total = p.m_tiles * p.n_tiles;
     const int grid = total < sms ? total : sms;
-    kern<<<grid, kWxThreads, P::kBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
-    return cudaGetLastError();
+    return launch_k(kern, dim3(grid), dim3(kWxThreads), P::kBytes, s, p.pdl, maps[0], maps[1], maps[2], maps[3], p);
 }
 
 // Split count minimising (waves) x (k-blocks per split + epilogue cost), with
@@ -1619,6 +1628,7 @@ cudaError_t gram_launch_tf32(TcContext *ctx, const TcGramArgs &a, int sms, const
     p.seed = a.seed;
     p.offset = a.offset;
     p.noise_k = a.noise_k;
+    p.pdl = a.pdl;
     p.d = a.d;
     p.noise_warp0 = ch.noise_warps == 4 ? 6 : 2;
     p.alpha = 0.f;
@@ -1672,6 +1682,7 @@ cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const Gram
     p.seed = a.seed;
     p.offset = a.offset;
     p.noise_k = a.noise_k;
+    p.pdl = a.pdl;
     p.d = a.d;
     // the FP32 form's warps 2-9 split A and warps 10-15 generate the noise
     p.noise_warp0 = f32a ? 2 + kPairF32Convert : (ch.noise_warps == 4 ? 6 : 2);
@@ -1754,6 +1765,7 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     p.alpha_next = a.alpha_next;
     p.coef = a.coef;
     p.err = a.err;
+    p.pdl = a.pdl;
     const bool inl = a.noise == nullptr;  // no slice: Philox in the epilogue
     if (split) {
         if (BN == 256) return inl ? run_wx<256, 2, true, true>(maps, p, sms, s) : run_wx<256, 2, true, false>(maps, p, sms, s);
@@ -1959,7 +1971,7 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
             cudaError_t r = time_launches(
                 [&] {
                     cudaError_t q = gram_launch(ctx, *g, sms, ch, &splits, &ps, &ldp, s);
-                    if (q == cudaSuccess && after_gram) q = after_gram(after_ctx, splits, ps, ldp, s);
+                    if (q == cudaSuccess && after_gram) q = after_gram(after_ctx, splits, ps, ldp, s, false);
                     return q;
                 },
                 reps, s, ms);
@@ -2054,6 +2066,40 @@ cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, 
             rep->gram_noise_warps = best.a_fp32 ? 4 : (best.noise_warps ? best.noise_warps : 8);
             rep->gram_a_fp32 = best.a_fp32;
             rep->gram_ms = best_ms;
+        }
+    }
+    if (g && w && after_gram) {
+        // Whole steps (Gram + softmax + W X, three in a row) with the recorded
+        // shapes, launched the ordinary way and with programmatic dependent
+        // launch; two interleaved passes, best of each.
+        float t[2] = {1e30f, 1e30f};
+        for (int pass = 0; pass < 2; ++pass)
+            for (int pdl = 0; pdl < 2; ++pdl) {
+                TcGramArgs ga = *g;
+                ga.pdl = pdl != 0;
+                TcWxArgs wa = *w;
+                wa.pdl = pdl != 0;
+                wa.force_bn = 0;
+                float ms = 0.f;
+                e = time_launches(
+                    [&] {
+                        cudaError_t q = cudaSuccess;
+                        for (int st = 0; st < 3 && q == cudaSuccess; ++st) {
+                            int splits = 0, ldp = 0;
+                            int64_t ps = 0;
+                            q = launch_gram_tc(ctx, ga, sms, &splits, &ps, &ldp, s);
+                            if (q == cudaSuccess) q = after_gram(after_ctx, splits, ps, ldp, s, pdl != 0);
+                            if (q == cudaSuccess) q = launch_wx_em_tc(ctx, wa, sms, s);
+                        }
+                        return q;
+                    },
+                    5, s, &ms);
+                if (e != cudaSuccess) return e;
+                t[pdl] = std::min(t[pdl], ms / 3);
+            }
+        if (rep) {
+            rep->pdl = t[1] < t[0] ? 1 : 0;
+            rep->step_ms = std::min(t[0], t[1]);
         }
     }
     return cudaSuccess;

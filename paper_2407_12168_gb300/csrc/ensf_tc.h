@@ -28,6 +28,8 @@ struct TcTuneReport {
     float gram_ms = 0.f;
     int wx_bn = 0;
     float wx_ms = 0.f;
+    int pdl = -1;        // 1/0: whether programmatic dependent launch made a step faster (-1: not timed)
+    float step_ms = 0.f; // one Gram + softmax + W X step with that choice
 };
 
 cudaError_t tc_context_create(TcContext **out);
@@ -60,6 +62,7 @@ struct TcGramArgs {
     // x - m [n_x][d] instead of BF16 planes
     bool tf32 = false;
     const float *zc32 = nullptr, *xc32 = nullptr;
+    bool pdl = false;                    // launch with programmatic stream serialization
 };
 
 struct TcWxArgs {
@@ -83,6 +86,7 @@ struct TcWxArgs {
     StepCoef coef;
     int *err;
     int force_bn = 0;                    // autotuner: particle tile width to use (0: tuned/default)
+    bool pdl = false;                    // launch with programmatic stream serialization
 };
 
 // ------------------------------------------------------------- batched
@@ -135,9 +139,11 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
 // split count) and of W X (particle tile width) on these very operands and
 // records the fastest per problem shape; later launches of that shape use it.
 // Synchronises `s`; either argument may be NULL.
-// `after_gram(splits, part_stride, ldp)` enqueues whatever consumes the
+// `after_gram(splits, part_stride, ldp, pdl)` enqueues whatever consumes the
 // partials (the row softmax), so that a shape is judged by Gram + reduction.
-using AfterGram = cudaError_t (*)(void *ctx, int splits, int64_t part_stride, int ldp, cudaStream_t s);
+// With both stages, it also times whole steps with and without programmatic
+// dependent launch and reports which was faster (rep->pdl).
+using AfterGram = cudaError_t (*)(void *ctx, int splits, int64_t part_stride, int ldp, cudaStream_t s, bool pdl);
 // Records a launch shape for (n, n_x, d) as if the autotuner had chosen it
 // (wx_bn 0 leaves W X alone).  cudaErrorInvalidValue for a shape that has no
 // compiled kernel.

@@ -53,7 +53,7 @@ class EnsfTuning(ctypes.Structure):
                 ("gram_ms", ctypes.c_float), ("wx_tile_n", ctypes.c_int), ("wx_ms", ctypes.c_float),
                 ("gram_k_block", ctypes.c_int), ("gram_cta_pair", ctypes.c_int),
                 ("gram_noise_warps", ctypes.c_int), ("gram_fp32_particles", ctypes.c_int),
-                ("noise_inline", ctypes.c_int)]
+                ("noise_inline", ctypes.c_int), ("pdl", ctypes.c_int)]
 
 
 class EnsfSqgParams(ctypes.Structure):
@@ -279,14 +279,15 @@ class Filter:
 
     def set_tuning(self, n: int, d: int, gram_tile_n: int, gram_stages: int, gram_k_block: int = 64,
                    gram_splits: int = 0, wx_tile_n: int = 0, gram_cta_pair: int = 0, gram_noise_warps: int = 0,
-                   gram_fp32_particles: int = 0, noise_inline: int = 0):
-        """Record tensor-core launch shapes (and the noise placement) for
-        analyses of this (n, d) without timing them (e.g. a report saved from
-        ``autotune``)."""
+                   gram_fp32_particles: int = 0, noise_inline: int = 0, pdl: int = -1):
+        """Record tensor-core launch shapes (and the noise placement and
+        whether the step kernels use programmatic dependent launch, ``pdl``
+        1/0, -1 = keep) for analyses of this (n, d) without timing them (e.g.
+        a report saved from ``autotune``)."""
         t = EnsfTuning(gram_tile_n=gram_tile_n, gram_stages=gram_stages, gram_splits=gram_splits,
                        wx_tile_n=wx_tile_n, gram_k_block=gram_k_block, gram_cta_pair=gram_cta_pair,
                        gram_noise_warps=gram_noise_warps, gram_fp32_particles=gram_fp32_particles,
-                       noise_inline=noise_inline)
+                       noise_inline=noise_inline, pdl=pdl)
         _check(load().ensf_set_tuning(self._h, int(n), int(d), ctypes.byref(t)), "ensf_set_tuning")
 
     def autotune(self, prior, y, mask, sigma_obs: float, eps: float, obs_op: int = OBS_IDENTITY, seed: int = 0,

@@ -1,12 +1,14 @@
 """GPU parity: the CUDA path, called through the C ABI, against the FP64 CPU
 oracle on the same seeded inputs, element by element (tolerances and the
 near-tie clause are documented in parity_util)."""
+import os
+
 import numpy as np
 import pytest
 
 from oracle import oracle as o
 from paper_2407_12168_gb300 import inputs
-from tests.parity_util import TOL_BF16, TOL_FP32, compare_members, conditioning, describe, run_oracle
+from tests.parity_util import TOL_BF16, TOL_FP32, compare_members, conditioning, describe, eps_path, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -247,7 +249,7 @@ def test_autotuned_analysis_matches_oracle():
     rep = f.autotune(prior, y, None, p.sigma_obs, p.eps, p.obs_op, seed=7)
     assert rep["gram_tile_n"] in (128, 256) and rep["wx_tile_n"] in (64, 128, 256)
     assert rep["gram_splits"] >= 1 and rep["gram_ms"] > 0 and rep["wx_ms"] > 0
-    assert rep["noise_inline"] in (0, 1)
+    assert rep["noise_inline"] in (0, 1) and rep["pdl"] in (0, 1)
     got = _gpu_analysis(p, "split", "split", filt=f)
     ref = run_oracle(p)
     cond = conditioning(p, ref, prec="split")
@@ -325,6 +327,33 @@ def test_inline_noise_is_bitwise_the_pregenerated_noise():
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("n,pair,inline", [(130, 0, 0), (130, 0, 1), (512, 1, 0)])
+def test_programmatic_dependent_launch_is_bitwise(n, pair, inline):
+    """The step kernels (Gram, row softmax, W X) launched with programmatic
+    dependent launch, where each waits on the device for its predecessor,
+    give bitwise the analysis of ordinary launches, eagerly and replayed from
+    a CUDA graph."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    p = inputs.small_case(seed=34, n=n, grid=32, layers=2, K=5, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
+    prior, y = torch.from_numpy(p.prior).cuda(), torch.from_numpy(p.y).cuda()
+    mask = torch.from_numpy(p.mask).cuda()
+    bn, stages = (256, 3) if pair else (128, 3)
+    stream = torch.cuda.Stream()
+    outs = []
+    for pdl, graph in [(0, False), (1, False), (1, True)]:
+        f = ensf.Filter(p.n, p.d, gram="split", wx="bf16", graph=graph, check_finite=True)
+        f.set_tuning(p.n, p.d, bn, stages, gram_splits=2, gram_cta_pair=pair, wx_tile_n=128,
+                     noise_inline=inline, pdl=pdl)
+        with torch.cuda.stream(stream):
+            o_ = f.analysis(prior, y, mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed)
+        stream.synchronize()
+        assert f.status_sync() == 0
+        outs.append(o_.cpu().numpy())
+    for o_ in outs[1:]:
+        np.testing.assert_array_equal(o_, outs[0])
+
+
 @pytest.mark.parametrize("wx_tile", [64, 128, 256])
 def test_recorded_noise_placement_is_bitwise(wx_tile):
     """The noise placement recorded for a shape (by ensf_set_tuning here, by
@@ -382,6 +411,25 @@ def test_minibatch_with_all_members_is_bitwise_the_full_analysis():
     np.testing.assert_array_equal(a, b)
 
 
+def _check_large_subsample(p, g, sub, gram, wx, tol):
+    """64 members of the large-512 analysis against the stored FP64 oracle
+    rows (written by tests/golden/make_large512_subsample.py): the ensemble
+    RMSE of the 64-member subsample within 1 % of the oracle's, and each
+    member's relative error on 4096 seeded state indices within the path's
+    tolerance unless the oracle's top-two log-kernel gap says the member sits
+    near a tie (at most one such member)."""
+    truth = p.truth.astype(np.float32).astype(np.float64)
+    mean = sub.astype(np.float64).mean(axis=0)
+    rmse = float(np.sqrt(np.mean((mean - truth) ** 2)))
+    assert abs(rmse - float(g["rmse"])) <= 0.01 * float(g["rmse"]), (rmse, float(g["rmse"]))
+    vals = sub[:, g["idx"]].astype(np.float64)
+    rel = np.linalg.norm(vals - g["values"], axis=1) / np.linalg.norm(g["values"], axis=1)
+    near_tie = g["gap_ratio"] < 4.0 * eps_path(_cond_prec(gram, wx), p.d)
+    bad = (rel > tol) & ~near_tie
+    assert not bad.any(), (rel.max(), np.flatnonzero(bad).tolist())
+    assert near_tie.sum() <= 1, np.flatnonzero(near_tie).tolist()
+
+
 def test_analysis_large_512_rows_in_the_bench_configuration():
     """d = 2x512x512, N = 1024, K = 100 (2 GiB forecast ensemble) on the
     headline path (split-BF16x3 Gram + BF16 W X, autotuned launch shapes, as
@@ -401,7 +449,14 @@ def test_analysis_large_512_rows_in_the_bench_configuration():
     f.analysis(prior, y, None, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed, out=out)
     assert f.status_sync() == 0
     got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large512_subsample64.npz")
+    sub = None
+    if os.path.exists(golden):
+        g = np.load(golden)
+        sub = out[torch.from_numpy(g["rows"].astype(np.int64)).cuda()].cpu().numpy()
     del prior, out
+    if sub is not None:
+        _check_large_subsample(p, g, sub, gram, wx, tol)
     ref = run_oracle(p, rows=rows)
     rel = np.sqrt(((got.astype(np.float64) - ref) ** 2).sum(axis=1) / (ref ** 2).sum(axis=1))
     cond = np.zeros(len(rows))
