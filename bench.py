@@ -449,26 +449,7 @@ def run_ours(args):
         one(w)
     torch.cuda.synchronize()
 
-    # ---- device-timed region: inputs resident in HBM ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
-        for s_ in range(args.steps):
-            if flush is not None:
-                flush.zero_()
-            ev[s_][0].record(stream)
-            one(100 + s_)
-            ev[s_][1].record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = float(sum(a.elapsed_time(b) for a, b in ev))
-    if f.status_sync() != 0:
-        raise RuntimeError("device error during the benchmark")
-
-    # ---- end to end: host buffers, copies inside the timed region ----
+    # ---- end-to-end buffers: pinned host copies of the inputs and the result ----
     h_prior = torch.from_numpy(p.prior).pin_memory()
     h_y = torch.from_numpy(p.y).pin_memory()
     h_mask = torch.from_numpy(p.mask).pin_memory() if p.mask is not None else None
@@ -482,8 +463,10 @@ def run_ours(args):
     d_prior.copy_(h_prior, non_blocking=True)
     h_out.copy_(d_prior, non_blocking=True)
     torch.cuda.synchronize()
-    # (no clock sampling in this loop: its driver queries slow the host copies)
-    for s_ in range(e2e_steps):
+
+    def e2e_step(s_):
+        """One analysis through host buffers: host-to-device copies of the
+        inputs, the analysis, the device-to-host read of the result."""
         if flush is not None:
             flush.zero_()
         ee[s_][0].record(stream)
@@ -495,9 +478,32 @@ def run_ours(args):
         h_out.copy_(out, non_blocking=True)
         ee[s_][1].record(stream)
         # the host takes the result before the next analysis is enqueued
-        # (without this wait the steps measured 15-50 % slower on GB300,
-        # growing step by step, though every copy is on the same stream)
         torch.cuda.synchronize()
+
+    # ---- timed region: K device-timed steps (inputs resident in HBM), the
+    # first few each followed by one end-to-end step, so that both figures
+    # are taken at the same clocks (a GB300 under its power cap slows as a
+    # long run heats it: end-to-end steps measured after the device steps of
+    # a warm GPU came out 15-40 % slower than the same steps interleaved) ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for s_ in range(args.steps):
+            if flush is not None:
+                flush.zero_()
+            ev[s_][0].record(stream)
+            one(100 + s_)
+            ev[s_][1].record(stream)
+            if s_ < e2e_steps:
+                e2e_step(s_)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    if f.status_sync() != 0:
+        raise RuntimeError("device error during the benchmark")
     e2e_each = [a.elapsed_time(b) for a, b in ee]
     e2e_ms = float(sum(e2e_each)) / e2e_steps
     h2d = p.prior.nbytes + p.y.nbytes + (p.mask.nbytes if p.mask is not None else 0)
