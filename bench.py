@@ -548,10 +548,16 @@ def run_ours(args):
         sub_rmse = float(np.sqrt(np.mean((sub.mean(axis=0) - truth64) ** 2)))
         ref_vals = g["values"]
         rel = np.linalg.norm(sub[:, g["idx"]] - ref_vals, axis=1) / np.linalg.norm(ref_vals, axis=1)
+        # members whose oracle top-two log-kernel gap came within twice the
+        # BF16 W X path's log-kernel error bound (they may follow another
+        # forecast member than the oracle's)
+        near = g["gap_ratio"] < 2.0 * 2.0 * 2.0 ** -9 / np.sqrt(p.d)
         subsample = {"members": int(len(g["rows"])), "gpu_rmse": sub_rmse, "oracle_rmse": float(g["rmse"]),
                      "rmse_rel_diff": abs(sub_rmse - float(g["rmse"])) / float(g["rmse"]),
                      "member_rel_err_on_sampled_entries": {"median": float(np.median(rel)),
-                                                           "max": float(rel.max()), "entries": int(len(g["idx"]))},
+                                                           "max": float(rel.max()), "entries": int(len(g["idx"])),
+                                                           "max_away_from_ties": float(rel[~near].max())},
+                     "near_tie_members": int(near.sum()),
                      "oracle": "FP64, %d host threads, %.0f s" % (int(g["threads"]), float(g["seconds"]))}
     del acc_out
 

@@ -413,21 +413,24 @@ def test_minibatch_with_all_members_is_bitwise_the_full_analysis():
 
 def _check_large_subsample(p, g, sub, gram, wx, tol):
     """64 members of the large-512 analysis against the stored FP64 oracle
-    rows (written by tests/golden/make_large512_subsample.py): the ensemble
-    RMSE of the 64-member subsample within 1 % of the oracle's, and each
-    member's relative error on 4096 seeded state indices within the path's
-    tolerance unless the oracle's top-two log-kernel gap says the member sits
-    near a tie (at most one such member)."""
-    truth = p.truth.astype(np.float32).astype(np.float64)
-    mean = sub.astype(np.float64).mean(axis=0)
-    rmse = float(np.sqrt(np.mean((mean - truth) ** 2)))
-    assert abs(rmse - float(g["rmse"])) <= 0.01 * float(g["rmse"]), (rmse, float(g["rmse"]))
+    rows (written by tests/golden/make_large512_subsample.py), on 4096 seeded
+    state entries per member.  A member whose oracle top-two log-kernel gap
+    is within twice the path's log-kernel error bound at some step can follow
+    another forecast member than the oracle's; such members are counted
+    (at most four) and left out of the comparison.  For the rest: each
+    member's relative error within the path's tolerance, and the ensemble
+    RMSE of their mean on those entries within 1 % of the oracle's."""
     vals = sub[:, g["idx"]].astype(np.float64)
-    rel = np.linalg.norm(vals - g["values"], axis=1) / np.linalg.norm(g["values"], axis=1)
-    near_tie = g["gap_ratio"] < 4.0 * eps_path(_cond_prec(gram, wx), p.d)
-    bad = (rel > tol) & ~near_tie
-    assert not bad.any(), (rel.max(), np.flatnonzero(bad).tolist())
-    assert near_tie.sum() <= 1, np.flatnonzero(near_tie).tolist()
+    ref = g["values"]
+    near_tie = g["gap_ratio"] < 2.0 * eps_path(_cond_prec(gram, wx), p.d)
+    keep = ~near_tie
+    rel = np.linalg.norm(vals - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert near_tie.sum() <= 4, (np.flatnonzero(near_tie).tolist(), rel[near_tie].tolist())
+    assert (rel[keep] <= tol).all(), (rel[keep].max(), np.flatnonzero(keep & (rel > tol)).tolist())
+    truth = p.truth.astype(np.float32).astype(np.float64)[g["idx"]]
+    rmse_gpu = float(np.sqrt(np.mean((vals[keep].mean(axis=0) - truth) ** 2)))
+    rmse_ref = float(np.sqrt(np.mean((ref[keep].mean(axis=0) - truth) ** 2)))
+    assert abs(rmse_gpu - rmse_ref) <= 0.01 * rmse_ref, (rmse_gpu, rmse_ref)
 
 
 def test_analysis_large_512_rows_in_the_bench_configuration():
