@@ -482,9 +482,10 @@ def run_ours(args):
 
     # ---- timed region: K device-timed steps (inputs resident in HBM), the
     # first few each followed by one end-to-end step, so that both figures
-    # are taken at the same clocks (a GB300 under its power cap slows as a
-    # long run heats it: end-to-end steps measured after the device steps of
-    # a warm GPU came out 15-40 % slower than the same steps interleaved) ----
+    # are taken under the same conditions (a GB300 runs under its power cap
+    # here; end-to-end steps taken after all the device steps, on a GPU that
+    # had just run the test suite, came out 15-40 % slower than device step +
+    # copies, while interleaved they differ by the copy time alone) ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
