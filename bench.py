@@ -309,6 +309,7 @@ def run_batched(args):
                     sigma_obs=p.sigma_obs, obs_op=p.obs_op, seed=p.seed) for p in probs]
     outs = [torch.empty_like(f["prior"]) for f in filters]
     max_n, max_d = max(p.n for p in probs), max(p.d for p in probs)
+    batch_tuning = None
     if gram == "fp32":
         handles = [ensf.Filter(p.n, p.d, gram="fp32", wx="fp32", graph=args.graph) for p in probs]
 
@@ -319,6 +320,8 @@ def run_batched(args):
         prof_handles = handles
     else:
         h = ensf.Filter(max_n, max_d, gram=gram, wx=wx, graph=args.graph)
+        # the k-range per batched Gram work item, timed on these filters
+        batch_tuning = h.autotune_batched(filters, eps)
 
         def one(sd):
             h.analysis_batched([dict(fl, seed=fl["seed"] + sd) for fl in filters], K, eps, outs=outs)
@@ -380,7 +383,7 @@ def run_batched(args):
                        "l2": "working set partly L2-resident (small filters)", "cuda_graph": args.graph,
                        "parallelism": f"{world} independent batch(es), one per GPU"},
             "roofline": roof, "kernels": kern, "gpu_launches": int(sum(v[0] for v in prof.values()) // args.steps),
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "tuning": batch_tuning}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -210,6 +210,21 @@ size_t ensf_batch_workspace_bytes(const ensf_config *cfg, const ensf_instance *i
 ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int count, int K, float eps,
                                   void *workspace, size_t ws_bytes, void *stream);
 
+/* Autotuner of the batched analysis: times short batched analyses (K = 8,
+ * same arguments otherwise; overwrites each instance's `out`) with 8, 16, 32
+ * and 64 k-blocks of 64 state columns per Gram work item (the split-K range
+ * of one 128 x 128 tile) and keeps the fastest in the handle for later
+ * batched analyses.  *kb_chunk and *ms (either may be NULL) receive the
+ * choice and the time of its K = 8 analysis.  Synchronises `stream`; not
+ * while it is being captured (EINVAL).  The workspace must be sized by
+ * ensf_batch_workspace_bytes (which covers every candidate). */
+ensf_status ensf_autotune_batched(ensf_handle *h, const ensf_instance *inst, int count, float eps, void *workspace,
+                                  size_t ws_bytes, int *kb_chunk, float *ms, void *stream);
+
+/* Records the k-range per batched Gram work item without timing (8, 16, 32
+ * or 64 k-blocks; the default is 32).  EINVAL otherwise. */
+ensf_status ensf_set_batch_tuning(ensf_handle *h, int kb_chunk);
+
 /* The analysis with the mini-batch prior score of Eq. 15-16 (J < N members
  * per evaluation): `perm` (device int32 [n]) is a permutation of the forecast
  * members, drawn by the caller; Euler-Maruyama step k uses the J members

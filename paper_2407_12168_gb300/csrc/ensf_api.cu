@@ -177,6 +177,8 @@ struct ensf_handle {
     size_t staging_bytes = 0;
     cudaEvent_t staging_done = nullptr;
     bool staging_pending = false;
+    // batched analyses: k-blocks per Gram work item (ensf_autotune_batched)
+    int batch_kb_chunk = ensf::kBatchKbChunk;
     // (n, d) -> true when ensf_autotune (or ensf_set_tuning) chose to evaluate
     // the noise in the W X epilogue rather than in the Gram's idle warps
     std::map<std::pair<int, int64_t>, bool> noise_inline;
@@ -931,6 +933,7 @@ struct BatchLayout {
     size_t maps_gram = 0, maps_wx = 0, insts = 0, gram_items = 0, rows = 0, wx_items = 0;
     size_t tables_begin = 0, tables_bytes = 0, total = 0;
     int n_gram_items = 0, n_rows = 0, n_wx_items = 0, max_n = 0;
+    int kb_chunk = 0;  // k-blocks per Gram work item
 };
 
 bool batch_ok(const ensf_config *cfg, const ensf_instance *inst, int count) {
@@ -940,8 +943,9 @@ bool batch_ok(const ensf_config *cfg, const ensf_instance *inst, int count) {
     return true;
 }
 
-BatchLayout batch_layout(const ensf_config *cfg, const ensf_instance *inst, int count) {
+BatchLayout batch_layout(const ensf_config *cfg, const ensf_instance *inst, int count, int kb_chunk) {
     BatchLayout B;
+    B.kb_chunk = kb_chunk;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
     const bool gs = cfg->gram == ENSF_PREC_SPLIT_BF16X3, ws = cfg->wx == ENSF_PREC_SPLIT_BF16X3;
@@ -951,7 +955,7 @@ BatchLayout batch_layout(const ensf_config *cfg, const ensf_instance *inst, int 
         BatchLayout::Inst L{};
         L.ldw = (int)round_up(n, 8);
         const int kblocks = (int)((d + 63) / 64);
-        L.splits = (kblocks + ensf::kBatchKbChunk - 1) / ensf::kBatchKbChunk;
+        L.splits = (kblocks + kb_chunk - 1) / kb_chunk;
         L.xbar = take(4 * d);
         L.norms = take(8 * n);
         L.xb_hi = take(2 * n * d);
@@ -1033,7 +1037,9 @@ extern "C" {
 
 size_t ensf_batch_workspace_bytes(const ensf_config *cfg, const ensf_instance *inst, int count) {
     if (!config_ok(cfg) || !batch_ok(cfg, inst, count)) return 0;
-    return batch_layout(cfg, inst, count).total;
+    // sized for the smallest k-range per work item (the most partials and
+    // items), so that every k-range the autotuner may pick fits
+    return batch_layout(cfg, inst, count, ensf::kBatchKbChunkMin).total;
 }
 
 ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int count, int K, float eps,
@@ -1058,7 +1064,7 @@ ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int
     }
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
         return fail(ENSF_EINVAL, "ensf_analysis_batched: workspace must be 256-byte aligned");
-    const BatchLayout B = batch_layout(&h->cfg, inst, count);
+    const BatchLayout B = batch_layout(&h->cfg, inst, count, h->batch_kb_chunk);
     if (ws_bytes < B.total)
         return fail(ENSF_ENOMEM, "ensf_analysis_batched: workspace has %zu bytes, needs %zu", ws_bytes, B.total);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1094,6 +1100,7 @@ ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int
         b.ldw = L.ldw;
         b.d = I.d;
         b.splits = L.splits;
+        b.kb_chunk = B.kb_chunk;
         b.partial = reinterpret_cast<float *>(dev(L.partial));
         b.norms = reinterpret_cast<const double *>(dev(L.norms));
         b.wb_hi = reinterpret_cast<__nv_bfloat16 *>(dev(L.wb_hi));
@@ -1166,6 +1173,59 @@ ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int
     }
     ENSF_CUDA(cudaEventRecord(h->staging_done, s));
     h->staging_pending = true;
+    return ENSF_OK;
+}
+
+ensf_status ensf_set_batch_tuning(ensf_handle *h, int kb_chunk) {
+    if (!h) return fail(ENSF_EINVAL, "ensf_set_batch_tuning: NULL handle");
+    if (kb_chunk != 8 && kb_chunk != 16 && kb_chunk != 32 && kb_chunk != 64)
+        return fail(ENSF_EINVAL, "ensf_set_batch_tuning: kb_chunk must be 8, 16, 32 or 64");
+    h->batch_kb_chunk = kb_chunk;
+    return ENSF_OK;
+}
+
+ensf_status ensf_autotune_batched(ensf_handle *h, const ensf_instance *inst, int count, float eps, void *workspace,
+                                  size_t ws_bytes, int *kb_chunk, float *ms, void *stream) {
+    if (!h) return fail(ENSF_EINVAL, "ensf_autotune_batched: NULL handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(ENSF_EINVAL, "ensf_autotune_batched: the stream is capturing; tune before capture");
+    // time short batched analyses (K = 8) for each k-range per Gram work item,
+    // launched eagerly, in two interleaved passes (best of the two)
+    constexpr int kTuneK = 8;
+    const int cands[] = {8, 16, 32, 64};
+    const unsigned flags = h->cfg.flags;
+    const int before = h->batch_kb_chunk;
+    h->cfg.flags &= ~ENSF_FLAG_CUDA_GRAPH;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ensf_status st = ENSF_OK;
+    float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) st = fail(ENSF_ECUDA, "event");
+    for (int pass = 0; pass < 3 && st == ENSF_OK; ++pass)
+        for (int ci = 0; ci < 4 && st == ENSF_OK; ++ci) {
+            h->batch_kb_chunk = cands[ci];
+            cudaEventRecord(a, s);
+            st = ensf_analysis_batched(h, inst, count, kTuneK, eps, workspace, ws_bytes, stream);
+            cudaEventRecord(b, s);
+            float t = 0.f;
+            if (st == ENSF_OK && (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess))
+                st = fail(ENSF_ECUDA, "ensf_autotune_batched: timing");
+            if (st == ENSF_OK && pass > 0) best_ms[ci] = std::min(best_ms[ci], t);  // pass 0 warms up
+        }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    h->cfg.flags = flags;
+    if (st != ENSF_OK) {
+        h->batch_kb_chunk = before;
+        return st;
+    }
+    int bi = 0;
+    for (int ci = 1; ci < 4; ++ci)
+        if (best_ms[ci] < best_ms[bi]) bi = ci;
+    h->batch_kb_chunk = cands[bi];
+    if (kb_chunk) *kb_chunk = cands[bi];
+    if (ms) *ms = best_ms[bi];
     return ENSF_OK;
 }
 

@@ -1243,8 +1243,8 @@ k_gram_tc_batched(const CUtensorMap *__restrict__ maps, const BGramItem *__restr
     const BInst &I = insts[it.inst];
     const int n = I.n;
     const int kblocks = static_cast<int>((I.d + BK - 1) / BK);
-    const int kb0 = it.split * kBatchKbChunk;
-    const int nkb = min(kblocks, kb0 + kBatchKbChunk) - kb0;
+    const int kb0 = it.split * I.kb_chunk;
+    const int nkb = min(kblocks, kb0 + I.kb_chunk) - kb0;
     const CUtensorMap *m = maps + 4 * it.inst;
     const uint32_t tmem = setup<BN, STAGES>(c, warp);
     if (warp == 0) {

@@ -94,13 +94,15 @@ struct TcWxArgs {
 // maps and parameters live in device memory (the batch workspace); the work
 // is a list of tiles over all instances.
 constexpr int kBatchTileN = 128;   // Gram member tile and W X particle tile of the batched kernels
-constexpr int kBatchKbChunk = 32;  // k-blocks (of 64 state columns) per batched Gram work item
+constexpr int kBatchKbChunk = 32;     // default k-blocks (of 64 state columns) per batched Gram work item
+constexpr int kBatchKbChunkMin = 8;   // smallest such k-range the batched autotuner tries
 
 struct BInst {
     int n;                           // particles = forecast members of this filter
     int ldw;                         // row pitch (elements) of the W and X^T planes: n rounded up to 8
     int64_t d;                       // state dimension
     int splits;                      // split-K slices of this instance's Gram
+    int kb_chunk;                    // k-blocks per slice (the Gram work item's k-range)
     float *partial;                  // [splits][n][n]
     const double *norms;             // [n] |x_j - m|^2
     __nv_bfloat16 *wb_hi, *wb_lo;    // [n][ldw] weights (lo NULL for plain BF16)

@@ -95,6 +95,11 @@ _SIGNATURES = [
     ("ensf_analysis_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EnsfInstance), ctypes.c_int,
                                              ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t,
                                              ctypes.c_void_p]),
+    ("ensf_autotune_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EnsfInstance), ctypes.c_int,
+                                             ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                             ctypes.c_void_p]),
+    ("ensf_set_batch_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ensf_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_void_p, ctypes.c_void_p]),
@@ -306,11 +311,9 @@ class Filter:
                                     _stream_ptr(stream)), "ensf_autotune")
         return {f: getattr(rep, f) for f, _ in EnsfTuning._fields_}
 
-    def analysis_batched(self, filters, K: int, eps: float, outs=None, stream=None):
-        """Batched analysis of independent filters.  ``filters`` is a list of
-        dicts with device tensors ``prior`` [n][d], ``y`` [d], optional ``mask``
-        [d], and ``sigma_obs``, ``obs_op``, ``seed``, ``offset``; returns the
-        list of analysis ensembles."""
+    def _batch_args(self, filters, outs=None):
+        """Instance table, workspace base and size, and the output tensors of
+        a batched call (the inputs are kept alive in the returned tuple)."""
         torch = _torch()
         lib = load()
         insts = (EnsfInstance * len(filters))()
@@ -340,9 +343,32 @@ class Filter:
         if getattr(self, "_batch_ws", None) is None or self._batch_ws.numel() < nbytes + 256:
             self._batch_ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         base = (self._batch_ws.data_ptr() + 255) // 256 * 256
-        _check(lib.ensf_analysis_batched(self._h, insts, len(filters), int(K), float(eps), ctypes.c_void_p(base),
-                                         nbytes, _stream_ptr(stream)), "ensf_analysis_batched")
+        return insts, ctypes.c_void_p(base), nbytes, results, keep
+
+    def analysis_batched(self, filters, K: int, eps: float, outs=None, stream=None):
+        """Batched analysis of independent filters.  ``filters`` is a list of
+        dicts with device tensors ``prior`` [n][d], ``y`` [d], optional ``mask``
+        [d], and ``sigma_obs``, ``obs_op``, ``seed``, ``offset``; returns the
+        list of analysis ensembles."""
+        insts, base, nbytes, results, _keep = self._batch_args(filters, outs)
+        _check(load().ensf_analysis_batched(self._h, insts, len(filters), int(K), float(eps), base, nbytes,
+                                            _stream_ptr(stream)), "ensf_analysis_batched")
         return results
+
+    def autotune_batched(self, filters, eps: float, stream=None) -> dict:
+        """Pick the k-range per Gram work item of batched analyses of these
+        filters (overwrites their outputs); returns the choice and the time
+        of its K = 8 trial analysis."""
+        insts, base, nbytes, _results, _keep = self._batch_args(filters)
+        chunk, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+        _check(load().ensf_autotune_batched(self._h, insts, len(filters), float(eps), base, nbytes,
+                                            ctypes.byref(chunk), ctypes.byref(ms), _stream_ptr(stream)),
+               "ensf_autotune_batched")
+        return {"kb_chunk": chunk.value, "trial_ms_k8": ms.value}
+
+    def set_batch_tuning(self, kb_chunk: int) -> None:
+        """Record the k-range per batched Gram work item (8, 16, 32 or 64)."""
+        _check(load().ensf_set_batch_tuning(self._h, int(kb_chunk)), "ensf_set_batch_tuning")
 
     def weights(self, z, prior, t: float, eps: float, stream=None):
         """Weights w_ij of Eq. 16 at pseudo-time t; returns [n][n_x] FP32."""

@@ -267,10 +267,12 @@ BATCH = [
 ]
 
 
-@pytest.mark.parametrize("path", ["split", "split-bf16"])
-def test_batched_analysis_matches_oracle(path):
+@pytest.mark.parametrize("path,kb_chunk", [("split", 32), ("split-bf16", 32), ("split", 8), ("split-bf16", 64)])
+def test_batched_analysis_matches_oracle(path, kb_chunk):
     """Five filters with uneven N and d in one batched analysis (one launch
-    per stage for all of them): each against the oracle, sampled rows."""
+    per stage for all of them): each against the oracle, sampled rows; with
+    the default k-range per Gram work item and with the smallest and largest
+    the batched autotuner tries (2 to 8 slices of d, or one)."""
     torch = _torch()
     from paper_2407_12168_gb300 import ensf
     gram, wx, tol = PATHS[path]
@@ -278,6 +280,7 @@ def test_batched_analysis_matches_oracle(path):
     probs = [inputs.small_case(seed=c[0], n=c[1], grid=c[2], layers=c[3], K=K, obs_op=c[4], obs_frac=c[5],
                                sigma_obs=c[6]) for c in BATCH]
     f = ensf.Filter(256, 4096, gram=gram, wx=wx)
+    f.set_batch_tuning(kb_chunk)
     filters = [dict(prior=torch.from_numpy(p.prior).cuda(), y=torch.from_numpy(p.y).cuda(),
                     mask=torch.from_numpy(p.mask).cuda() if p.mask is not None else None, sigma_obs=p.sigma_obs,
                     obs_op=p.obs_op, seed=p.seed, offset=3) for p in probs]
@@ -292,6 +295,32 @@ def test_batched_analysis_matches_oracle(path):
         rel, tie, bad = compare_members(got, ref, cond, tol)
         assert not bad.any(), f"{p.name}: " + describe(rel, tie, bad)
         assert tie.sum() <= max(1, len(rows) // 6), f"{p.name}: " + describe(rel, tie, bad)
+
+
+def test_batched_autotuner_choice_is_recorded():
+    """ensf_autotune_batched picks one of the k-ranges and keeps it: a later
+    batched analysis is bitwise the one with that k-range set explicitly;
+    bad k-ranges are rejected."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    probs = [inputs.small_case(seed=c[0], n=c[1], grid=c[2], layers=c[3], K=4, obs_op=c[4], obs_frac=c[5],
+                               sigma_obs=c[6]) for c in BATCH]
+    filters = [dict(prior=torch.from_numpy(p.prior).cuda(), y=torch.from_numpy(p.y).cuda(),
+                    mask=torch.from_numpy(p.mask).cuda() if p.mask is not None else None, sigma_obs=p.sigma_obs,
+                    obs_op=p.obs_op, seed=p.seed) for p in probs]
+    tuned = ensf.Filter(256, 4096, gram="split", wx="bf16")
+    rep = tuned.autotune_batched(filters, 0.05)
+    assert rep["kb_chunk"] in (8, 16, 32, 64) and rep["trial_ms_k8"] > 0
+    a = [o.cpu().numpy() for o in tuned.analysis_batched(filters, 4, 0.05)]
+    fixed = ensf.Filter(256, 4096, gram="split", wx="bf16")
+    fixed.set_batch_tuning(rep["kb_chunk"])
+    b = [o.cpu().numpy() for o in fixed.analysis_batched(filters, 4, 0.05)]
+    assert tuned.status_sync() == 0 and fixed.status_sync() == 0
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    for bad in (0, 12, 128):
+        with pytest.raises(ensf.EnsfError):
+            fixed.set_batch_tuning(bad)
 
 
 def test_batched_graph_matches_eager():
