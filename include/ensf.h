@@ -140,8 +140,11 @@ typedef struct {
     int gram_noise_warps; /* warps of a Gram CTA generating the next step's noise (8 or 4) */
     int gram_fp32_particles; /* 1 (pair tiles only): the Gram reads the FP32 particles and splits
                                 them itself, so the W X step writes no BF16 particle planes */
-    int noise_inline;  /* Philox noise with both stages on the tensor cores: 1 = evaluated in the
-                          W X epilogue, 0 = written a step ahead by the Gram's idle warps */
+    int noise_inline;  /* where the counter-based draws are made when both stages run on the tensor
+                          cores: 0 = written to a slice by the Gram's spare warps while its MMAs
+                          run, 1 = evaluated in the W X epilogue, 2 = written to the slice by a
+                          kernel on a low-priority side stream that runs beside the Gram and the
+                          softmax (the draws are the same in all three) */
     int pdl;           /* 1: the per-step kernels (Gram, row softmax, W X) are launched with
                           programmatic dependent launch (each may start while its predecessor
                           finishes, and waits for it on the device), 0: ordinary launches.
@@ -154,8 +157,10 @@ typedef struct {
  * these operands (same arguments as ensf_analysis, without K) and records the
  * fastest for this (n, d) in the handle; later analyses of that shape use it.
  * When both stages run on the tensor cores with counter-based noise (no noise
- * buffer, no ENSF_FLAG_INLINE_NOISE), it tunes both noise placements and
- * keeps the one with the smaller Gram + softmax + W X time (noise_inline).
+ * buffer, no ENSF_FLAG_INLINE_NOISE), it tunes the shapes with the draws in
+ * the Gram and in the W X epilogue, keeps the one with the smaller Gram +
+ * softmax + W X time, and then compares it with the side-stream placement on
+ * short whole analyses (noise_inline).
  * It then times whole steps with and without programmatic dependent launch
  * (pdl) and keeps the faster.
  * Overwrites `out` and the workspace, synchronises `stream`, and must not be

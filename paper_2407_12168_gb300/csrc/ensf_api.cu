@@ -179,17 +179,16 @@ struct ensf_handle {
     bool staging_pending = false;
     // batched analyses: k-blocks per Gram work item (ensf_autotune_batched)
     int batch_kb_chunk = ensf::kBatchKbChunk;
-    // (n, d) -> true when ensf_autotune (or ensf_set_tuning) chose to evaluate
-    // the noise in the W X epilogue rather than in the Gram's idle warps
-    std::map<std::pair<int, int64_t>, bool> noise_inline;
+    // (n, d) -> where the counter-based draws of an analysis are made, as
+    // chosen by ensf_autotune or ensf_set_tuning (NoisePlace)
+    std::map<std::pair<int, int64_t>, int> noise_place_tuned;
+    // low-priority side stream and its events, for draws made by a kernel that
+    // runs beside the Gram and the softmax (created on first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_free = nullptr, ev_drawn = nullptr;
 
-    // whether the tensor-core W X of an (n, d) analysis evaluates its noise
-    // itself (no pre-generated slice)
-    bool inline_noise(int n, int64_t d) const {
-        if (cfg.flags & ENSF_FLAG_INLINE_NOISE) return true;
-        auto it = noise_inline.find(std::make_pair(n, d));
-        return it != noise_inline.end() && it->second;
-    }
+    int noise_place(int n, int64_t d) const;
+    bool inline_noise(int n, int64_t d) const;
 
     // (n, d) -> whether the per-step kernels (Gram, row softmax, W X) are
     // launched with programmatic dependent launch, as chosen by ensf_autotune
@@ -208,6 +207,21 @@ struct ensf_handle {
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
     int *err() const { return at<int>(L.err); }
 };
+
+// Where the draws xi[k+1] of Euler-Maruyama step k are made (tensor-core W X
+// with the counter-based stream): written to a [n][d] slice by the Gram's
+// spare warps while its MMAs run, evaluated inside the W X epilogue, or
+// written to the slice by a kernel on a low-priority side stream that runs
+// beside the Gram and the softmax (on the SMs they leave idle).
+enum NoisePlace { NOISE_GRAM = 0, NOISE_WX = 1, NOISE_SIDE = 2 };
+
+int ensf_handle::noise_place(int n, int64_t d) const {
+    if (cfg.flags & ENSF_FLAG_INLINE_NOISE) return NOISE_WX;
+    auto it = noise_place_tuned.find(std::make_pair(n, d));
+    return it != noise_place_tuned.end() ? it->second : NOISE_GRAM;
+}
+
+bool ensf_handle::inline_noise(int n, int64_t d) const { return noise_place(n, d) == NOISE_WX; }
 
 namespace {
 
@@ -380,6 +394,9 @@ ensf_status ensf_destroy(ensf_handle *h) {
     if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
     if (h->staging_done) cudaEventDestroy(h->staging_done);
     if (h->staging) cudaFreeHost(h->staging);
+    if (h->ev_free) cudaEventDestroy(h->ev_free);
+    if (h->ev_drawn) cudaEventDestroy(h->ev_drawn);
+    if (h->side) cudaStreamDestroy(h->side);
     ensf::tc_context_destroy(h->tc);
     delete h;
     return ENSF_OK;
@@ -526,10 +543,26 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
     // while the MMAs of step k run; otherwise a separate launch does.
     float *nslice = tc_wx ? h->at<float>(L.noise) : nullptr;
     const bool pregen = tc_wx && !noise->buf && !h->inline_noise(n, d);
+    const bool side = pregen && tc_gram && h->noise_place(n, d) == NOISE_SIDE;
+    if (side && !h->side) {
+        int least = 0, greatest = 0;
+        ENSF_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        ENSF_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, least));
+        ENSF_CUDA(cudaEventCreateWithFlags(&h->ev_free, cudaEventDisableTiming));
+        ENSF_CUDA(cudaEventCreateWithFlags(&h->ev_drawn, cudaEventDisableTiming));
+    }
     for (int k = 0; k < K; ++k) {
         ensf::StepCoef c = step_coef(k, K, eps, sigma_obs, obs_op);
         NoiseRequest nr;
-        if (pregen && tc_gram) {
+        if (side) {
+            // the slice is free once the previous step's W X has read it
+            ENSF_CUDA(cudaEventRecord(h->ev_free, s));
+            ENSF_CUDA(cudaStreamWaitEvent(h->side, h->ev_free, 0));
+            ENSF_LAUNCH(h, P_NOISE, h->side,
+                        ensf::launch_noise_slice(noise->seed, noise->offset, k + 1, n, d, nslice, 4 * h->sms,
+                                                 h->side));
+            ENSF_CUDA(cudaEventRecord(h->ev_drawn, h->side));
+        } else if (pregen && tc_gram) {
             nr.slice = nslice;
             nr.seed = noise->seed;
             nr.offset = noise->offset;
@@ -553,6 +586,7 @@ ensf_status analysis_enqueue(ensf_handle *h, const float *prior, int n, int64_t 
             ensf::TcWxArgs a = wx_args(h, n, d, y, obs_mask, noise, out, c,
                                        step_coef(k + 1, K, eps, sigma_obs, obs_op).alpha, k, x0, nm);
             if (gram_f32) a.zb_hi = a.zb_lo = nullptr;
+            if (side) ENSF_CUDA(cudaStreamWaitEvent(s, h->ev_drawn, 0));
             ENSF_LAUNCH(h, P_WXEM, s, ensf::launch_wx_em_tc(h->tc, a, h->sms, s));
         }
     }
@@ -724,22 +758,61 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         if (st != ENSF_OK) return st;
     } else {
         ensf::TcTuneReport r_slice, r_inline;
-        h->noise_inline[key] = false;
+        h->noise_place_tuned[key] = NOISE_GRAM;
         st = autotune_pass(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, eps, noise, out, s, &r_slice);
         if (st != ENSF_OK) return st;
-        h->noise_inline[key] = true;
+        h->noise_place_tuned[key] = NOISE_WX;
         st = autotune_pass(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, eps, noise, out, s, &r_inline);
         if (st != ENSF_OK) return st;
         const bool inl = r_inline.gram_ms + r_inline.wx_ms < r_slice.gram_ms + r_slice.wx_ms;
-        h->noise_inline[key] = inl;
         r = inl ? r_inline : r_slice;
-        if (!inl) {  // the second pass overwrote the shapes of the first: record them again
-            ensf::GramChoice g{r.gram_bn, r.gram_stages, r.gram_splits, r.gram_bk, r.gram_pair};
-            g.noise_warps = r.gram_noise_warps;
-            g.a_fp32 = r.gram_a_fp32;
-            if (ensf::tc_set_tuning(h->tc, n, n, d, h->cfg.gram == ENSF_PREC_SPLIT_BF16X3, g, r.wx_bn,
-                                    h->cfg.wx == ENSF_PREC_SPLIT_BF16X3, h->cfg.gram == ENSF_PREC_TF32) != cudaSuccess)
-                return fail(ENSF_ECUDA, "ensf_autotune: could not record the chosen launch shapes");
+        // The third placement, draws by a side-stream kernel beside the Gram
+        // and the softmax, takes the Gram shape of the pass without noise and
+        // the W X shape of the pass that reads the slice; it is judged on short
+        // whole analyses against the better of the first two.
+        auto record = [&](const ensf::TcTuneReport &g, int wx_bn) -> bool {
+            ensf::GramChoice c{g.gram_bn, g.gram_stages, g.gram_splits, g.gram_bk, g.gram_pair};
+            c.noise_warps = g.gram_noise_warps;
+            c.a_fp32 = g.gram_a_fp32;
+            return ensf::tc_set_tuning(h->tc, n, n, d, h->cfg.gram == ENSF_PREC_SPLIT_BF16X3, c, wx_bn,
+                                       h->cfg.wx == ENSF_PREC_SPLIT_BF16X3,
+                                       h->cfg.gram == ENSF_PREC_TF32) == cudaSuccess;
+        };
+        auto time_analyses = [&](float *ms) -> ensf_status {
+            constexpr int kTuneK = 6;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            ENSF_CUDA(cudaEventCreate(&e0));
+            ENSF_CUDA(cudaEventCreate(&e1));
+            *ms = 1e30f;
+            ensf_status q = ENSF_OK;
+            for (int rep = 0; rep < 3 && q == ENSF_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                q = analysis_enqueue(h, prior, n, d, y, obs_mask, obs_op, sigma_obs, kTuneK, eps, noise, out, s);
+                cudaEventRecord(e1, s);
+                float t = 0.f;
+                if (q == ENSF_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+                    q = fail(ENSF_ECUDA, "ensf_autotune: timing");
+                if (q == ENSF_OK && rep > 0) *ms = std::min(*ms, t);  // the first run warms up
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return q;
+        };
+        float t_best = 0.f, t_side = 0.f;
+        if (!record(r, r.wx_bn)) return fail(ENSF_ECUDA, "ensf_autotune: could not record the launch shapes");
+        h->noise_place_tuned[key] = inl ? NOISE_WX : NOISE_GRAM;
+        if ((st = time_analyses(&t_best)) != ENSF_OK) return st;
+        if (!record(r_inline, r_slice.wx_bn)) return fail(ENSF_ECUDA, "ensf_autotune: could not record the launch shapes");
+        h->noise_place_tuned[key] = NOISE_SIDE;
+        if ((st = time_analyses(&t_side)) != ENSF_OK) return st;
+        if (t_side < t_best) {
+            r = r_inline;
+            r.wx_bn = r_slice.wx_bn;
+            r.wx_ms = r_slice.wx_ms;
+        } else {
+            if (!record(r, r.wx_bn)) return fail(ENSF_ECUDA, "ensf_autotune: could not record the launch shapes");
+            h->noise_place_tuned[key] = inl ? NOISE_WX : NOISE_GRAM;
         }
     }
     if (r.pdl >= 0) h->pdl_tuned[key] = r.pdl != 0;
@@ -754,7 +827,7 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         report->gram_cta_pair = r.gram_pair;
         report->gram_noise_warps = r.gram_noise_warps;
         report->gram_fp32_particles = r.gram_a_fp32;
-        report->noise_inline = h->inline_noise(n, d) ? 1 : 0;
+        report->noise_inline = h->noise_place(n, d);
         report->pdl = h->use_pdl(n, d) ? 1 : 0;
     }
     return ENSF_OK;
@@ -765,6 +838,8 @@ ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning 
     if (n < 1 || n > h->cfg.max_n || d < 8 || d > h->cfg.max_d || d % 8 != 0)
         return fail(ENSF_EINVAL, "ensf_set_tuning: n or d outside the handle's limits");
     if (!is_tc(h->cfg.gram)) return fail(ENSF_EINVAL, "ensf_set_tuning: the Gram of this handle runs on CUDA cores");
+    if (t->noise_inline < NOISE_GRAM || t->noise_inline > NOISE_SIDE)
+        return fail(ENSF_EINVAL, "ensf_set_tuning: noise_inline must be 0, 1 or 2");
     ensf::GramChoice g;
     g.bn = t->gram_tile_n;
     g.stages = t->gram_stages;
@@ -778,7 +853,7 @@ ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning 
     if (ensf::tc_set_tuning(h->tc, n, n, d, split3, g, is_tc(h->cfg.wx) ? t->wx_tile_n : 0, wx_split,
                             h->cfg.gram == ENSF_PREC_TF32) != cudaSuccess)
         return fail(ENSF_EINVAL, "ensf_set_tuning: no kernel for that launch shape");
-    h->noise_inline[std::make_pair(n, d)] = t->noise_inline != 0;
+    h->noise_place_tuned[std::make_pair(n, d)] = t->noise_inline;
     if (t->pdl == 0 || t->pdl == 1) h->pdl_tuned[std::make_pair(n, d)] = t->pdl == 1;
     return ENSF_OK;
 }

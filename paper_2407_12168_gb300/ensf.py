@@ -285,10 +285,11 @@ class Filter:
     def set_tuning(self, n: int, d: int, gram_tile_n: int, gram_stages: int, gram_k_block: int = 64,
                    gram_splits: int = 0, wx_tile_n: int = 0, gram_cta_pair: int = 0, gram_noise_warps: int = 0,
                    gram_fp32_particles: int = 0, noise_inline: int = 0, pdl: int = -1):
-        """Record tensor-core launch shapes (and the noise placement and
-        whether the step kernels use programmatic dependent launch, ``pdl``
-        1/0, -1 = keep) for analyses of this (n, d) without timing them (e.g.
-        a report saved from ``autotune``)."""
+        """Record tensor-core launch shapes (and the noise placement,
+        ``noise_inline`` 0 = Gram warps, 1 = W X epilogue, 2 = side-stream
+        kernel, and whether the step kernels use programmatic dependent
+        launch, ``pdl`` 1/0, -1 = keep) for analyses of this (n, d) without
+        timing them (e.g. a report saved from ``autotune``)."""
         t = EnsfTuning(gram_tile_n=gram_tile_n, gram_stages=gram_stages, gram_splits=gram_splits,
                        wx_tile_n=wx_tile_n, gram_k_block=gram_k_block, gram_cta_pair=gram_cta_pair,
                        gram_noise_warps=gram_noise_warps, gram_fp32_particles=gram_fp32_particles,

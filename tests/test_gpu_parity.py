@@ -356,7 +356,7 @@ def test_inline_noise_is_bitwise_the_pregenerated_noise():
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("n,pair,inline", [(130, 0, 0), (130, 0, 1), (512, 1, 0)])
+@pytest.mark.parametrize("n,pair,inline", [(130, 0, 0), (130, 0, 1), (130, 0, 2), (512, 1, 0)])
 def test_programmatic_dependent_launch_is_bitwise(n, pair, inline):
     """The step kernels (Gram, row softmax, W X) launched with programmatic
     dependent launch, where each waits on the device for its predecessor,
@@ -392,11 +392,14 @@ def test_recorded_noise_placement_is_bitwise(wx_tile):
     p = inputs.small_case(seed=33, n=130, grid=32, layers=2, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
     from paper_2407_12168_gb300 import ensf
     outs = []
-    for inl in (0, 1):
+    for place in (0, 1, 2):  # Gram warps, W X epilogue, side-stream kernel
         f = ensf.Filter(p.n, p.d, gram="split", wx="bf16")
-        f.set_tuning(p.n, p.d, 128, 3, gram_splits=2, wx_tile_n=wx_tile, noise_inline=inl)
+        f.set_tuning(p.n, p.d, 128, 3, gram_splits=2, wx_tile_n=wx_tile, noise_inline=place)
         outs.append(_gpu_analysis(p, "split", "bf16", filt=f))
     np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    with pytest.raises(ensf.EnsfError):
+        f.set_tuning(p.n, p.d, 128, 3, noise_inline=3)
 
 
 @pytest.mark.parametrize("path,J", [("split", 16), ("split", 32), ("split-bf16", 32), ("split-bf16", 64)])
