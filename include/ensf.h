@@ -173,14 +173,15 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
 /* Records launch shapes for analyses of this (n, d) without timing them,
  * e.g. a report saved from ensf_autotune in another process.  Uses the
  * gram_tile_n, gram_stages, gram_splits (0: the cost model), gram_k_block,
- * wx_tile_n (0: unchanged), noise_inline and pdl (-1: unchanged) fields of `t`.  Valid Gram shapes (tile width,
- * ring depth, k-block) for the split-BF16x3 Gram: (128, 3, 64), (256, 2, 64),
- * (128, 6, 32), (256, 4, 32), (256, 3, 32), and with gram_cta_pair = 1
- * (256, 3, 64) when n is a multiple of 256 (optionally with
- * gram_fp32_particles = 1); for the BF16 Gram: (128, 6, 64),
- * (256, 4, 64), (128, 12, 32), (256, 8, 32); for the TF32 Gram: (128, 6, 32),
- * (256, 4, 32), and with gram_cta_pair = 1 (256, 6, 32) when n is a
- * multiple of 256.  EINVAL for any other shape, for
+ * gram_cta_pair, gram_noise_warps, gram_fp32_particles, wx_tile_n
+ * (0: unchanged), noise_inline (0, 1 or 2) and pdl (-1: unchanged) fields
+ * of `t`.  Valid Gram shapes (tile width, ring depth, k-block) for the
+ * split-BF16x3 Gram: (128, 3, 64), (256, 2, 64), (128, 6, 32), (256, 4, 32),
+ * (256, 3, 32), and with gram_cta_pair = 1 (256, 3, 64) when n is a multiple
+ * of 256 (optionally with gram_fp32_particles = 1); for the BF16 Gram:
+ * (128, 6, 64), (256, 4, 64), (128, 12, 32), (256, 8, 32); for the TF32
+ * Gram: (128, 6, 32), (256, 4, 32), and with gram_cta_pair = 1 (256, 6, 32)
+ * when n is a multiple of 256.  EINVAL for any other shape or placement, for
  * n or d outside the handle's limits, or for a handle whose Gram runs on
  * CUDA cores. */
 ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning *t);
