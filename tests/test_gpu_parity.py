@@ -383,6 +383,27 @@ def test_programmatic_dependent_launch_is_bitwise(n, pair, inline):
         np.testing.assert_array_equal(o_, outs[0])
 
 
+def test_minibatch_launch_forms_are_bitwise():
+    """The mini-batch analysis (windows of J = 32 of 128 members) gives the
+    same bits with the draws made in the Gram's warps, in the W X epilogue or
+    on the side stream, with and without programmatic dependent launch."""
+    torch = _torch()
+    from paper_2407_12168_gb300 import ensf
+    p = inputs.small_case(seed=35, n=128, grid=32, layers=2, K=5, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
+    prior, y = torch.from_numpy(p.prior).cuda(), torch.from_numpy(p.y).cuda()
+    mask = torch.from_numpy(p.mask).cuda()
+    perm = torch.from_numpy(np.random.default_rng(36).permutation(p.n).astype(np.int32)).cuda()
+    outs = []
+    for place, pdl in [(0, 0), (1, 1), (2, 1), (2, 0)]:
+        f = ensf.Filter(p.n, p.d, gram="split", wx="bf16", check_finite=True)
+        f.set_tuning(p.n, p.d, 128, 3, gram_splits=2, wx_tile_n=128, noise_inline=place, pdl=pdl)
+        o_ = f.analysis_minibatch(prior, y, mask, p.sigma_obs, p.K, p.eps, perm, 32, p.obs_op, seed=p.seed)
+        assert f.status_sync() == 0
+        outs.append(o_.cpu().numpy())
+    for o_ in outs[1:]:
+        np.testing.assert_array_equal(o_, outs[0])
+
+
 @pytest.mark.parametrize("wx_tile", [64, 128, 256])
 def test_recorded_noise_placement_is_bitwise(wx_tile):
     """The noise placement recorded for a shape (by ensf_set_tuning here, by
