@@ -505,7 +505,8 @@ def run_ours(args):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    step_each = [a.elapsed_time(b) for a, b in ev]
+    ms = float(sum(step_each))
     if f.status_sync() != 0:
         raise RuntimeError("device error during the benchmark")
     e2e_each = [a.elapsed_time(b) for a, b in ee]
@@ -593,7 +594,10 @@ def run_ours(args):
     gpu_launches = int(sum(v[0] for v in prof.values()))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "ms_each_step": {"median": float(np.median(step_each)), "min": float(min(step_each)),
+                             "max": float(max(step_each))},
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"split-bf16": "bf16x3+bf16 (fp32 acc)", "split": "bf16x3 (fp32 acc)",
                                           "fp32": "f32", "tf32-bf16": "tf32+bf16 (fp32 acc)",
                                           "tf32": "tf32+bf16x3 (fp32 acc)",
