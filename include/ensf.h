@@ -254,15 +254,18 @@ ensf_status ensf_weights(ensf_handle *h, const float *z, int n, const float *pri
  * device allocation, and loops that must never reach an allocation that could
  * synchronise the device.  The paper has no counterpart; this is a property
  * of the library, not of the method.  It needs no handle and no workspace:
- * its scratch (row norms and split-K partial Grams) is one static device
- * array of 2 MiB + 4 KiB that every device loading the library keeps until
- * the process exits.  Limits: 1 <= n, n_x <= 256 (else ENSF_EINVAL with a
- * message in ensf_last_error); d a positive multiple of 8; t in (0, 1].
- * The first call on a device looks up the array's device address (with that
- * device current), so make that first call before any stream capture.  All
- * calls share the array: calls that overlap on the GPU (other streams, other
- * host threads) race on it and must be serialised by the caller.  Each call
- * writes every scratch word it reads, so no state carries between calls. */
+ * its scratch (the forecast mean that centres the Gram operands, the row
+ * norms and the split-K partial Grams) is one static device array of
+ * 4 MiB + 4 KiB that every device loading the library keeps until the
+ * process exits.  The Gram runs on the centred operands z - alpha m and
+ * x_j - m, as in ensf_weights.  Limits: 1 <= n, n_x <= 256 and d a multiple
+ * of 8 in [8, 524288] (else ENSF_EINVAL with a message in ensf_last_error);
+ * t in (0, 1].  The first call on a device looks up the array's device
+ * address (with that device current), so make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.  Each call writes every scratch word it reads, so no state
+ * carries between calls. */
 ensf_status ensf_weights_static(const float *z, int n, const float *prior, int n_x, int64_t d, float t,
                                 float eps, float *w, void *stream);
 
@@ -399,9 +402,19 @@ ensf_status ensf_unet_forward(ensf_unet *u, const float *x, int batch, float *y,
  * parameters (device FP32 [param_count]; grads or loss may be NULL). */
 ensf_status ensf_unet_gradients(ensf_unet *u, const float *x, const float *target, int batch, float *grads,
                                 double *loss, void *stream);
-/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8) on that loss; loss (device) may be NULL. */
+/* One AdamW step on that loss (Loshchilov and Hutter, ICLR 2019, Algorithm 2
+ * with step size 1 and schedule multiplier lr; beta1 0.9, beta2 0.999,
+ * eps 1e-8; t counts the steps since the last ensf_unet_set_params):
+ *   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+ *   w -= lr (m / (1 - beta1^t) / (sqrt(v / (1 - beta2^t)) + eps) + weight_decay w),
+ * on the FP32 master weights, then the BF16 copies are refreshed; loss
+ * (device) may be NULL. */
 ensf_status ensf_unet_train_step(ensf_unet *u, const float *x, const float *target, int batch, float lr,
                                  float weight_decay, double *loss, void *stream);
+/* Read the AdamW state: first and second moments m, v (device FP32
+ * [param_count], same order as the parameters) and, when step != NULL (host),
+ * the number of AdamW steps since the last ensf_unet_set_params. */
+ensf_status ensf_unet_get_moments(ensf_unet *u, float *m, float *v, int64_t *step, void *stream);
 ensf_status ensf_unet_destroy(ensf_unet *u);
 
 /* Wait for `stream` and return the handle's recorded device error, clearing it. */

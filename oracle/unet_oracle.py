@@ -155,6 +155,29 @@ def forward(params, widths, x_nchw, with_cache=False):
     return y
 
 
+def adamw_step(w, g, m, v, step, lr, weight_decay, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One AdamW update in FP64 (Loshchilov and Hutter, "Decoupled Weight
+    Decay Regularization", ICLR 2019, their Algorithm 2 with the step size
+    alpha = 1 and the schedule multiplier eta_t = lr):
+
+        m_t = beta1 m_{t-1} + (1 - beta1) g_t
+        v_t = beta2 v_{t-1} + (1 - beta2) g_t^2
+        m^_t = m_t / (1 - beta1^t),   v^_t = v_t / (1 - beta2^t)
+        w_t = w_{t-1} - lr (m^_t / (sqrt(v^_t) + eps) + weight_decay w_{t-1})
+
+    The weight decay acts on the parameters directly (decoupled from the
+    gradient-based step), not through the gradient as an L2 penalty would.
+    ``step`` is t >= 1, the index of this update.  Returns (w_t, m_t, v_t)."""
+    w = np.asarray(w, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    w_new = w - lr * (m_hat / (np.sqrt(v_hat) + eps) + weight_decay * w)
+    return w_new, m, v
+
+
 def loss_and_grad(params, widths, x_nchw, target_nchw):
     """Mean-squared-error loss and its gradient with respect to the flat
     parameter vector (FP64, hand-written backward pass)."""

@@ -740,6 +740,15 @@ ensf_status ensf_unet_get_params(ensf_unet *u, float *params, void *stream) {
     return ENSF_OK;
 }
 
+ensf_status ensf_unet_get_moments(ensf_unet *u, float *m, float *v, int64_t *step, void *stream) {
+    if (!u || !m || !v) return unet_fail(ENSF_EINVAL, "ensf_unet_get_moments: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    UNET_CUDA(cudaMemcpyAsync(m, u->adam_m, sizeof(float) * u->nparams, cudaMemcpyDeviceToDevice, s));
+    UNET_CUDA(cudaMemcpyAsync(v, u->adam_v, sizeof(float) * u->nparams, cudaMemcpyDeviceToDevice, s));
+    if (step) *step = u->step;
+    return ENSF_OK;
+}
+
 ensf_status ensf_unet_forward(ensf_unet *u, const float *x, int batch, float *y, void *stream) {
     if (!u || !x || !y || batch < 1 || batch > u->cfg.max_batch)
         return unet_fail(ENSF_EINVAL, "ensf_unet_forward: bad arguments");

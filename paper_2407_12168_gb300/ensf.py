@@ -140,6 +140,8 @@ _SIGNATURES = [
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_unet_train_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_float, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ensf_unet_get_moments", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
     ("ensf_unet_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("ensf_status_sync", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -373,14 +375,15 @@ class Filter:
 
     def weights(self, z, prior, t: float, eps: float, stream=None):
         """Weights w_ij of Eq. 16 at pseudo-time t; returns [n][n_x] FP32."""
+        n, n_x, d = _weights_shapes(z, prior)
         torch = _torch()
         _dev(z, torch.float32, "z")
         _dev(prior, torch.float32, "prior")
-        n, d = z.shape
-        n_x = prior.shape[0]
-        w = torch.empty((n, n_x), dtype=torch.float32, device=z.device)
-        _check(load().ensf_weights(self._h, z.data_ptr(), n, prior.data_ptr(), n_x, d, float(t), float(eps),
-                                   w.data_ptr(), _stream_ptr(stream)), "ensf_weights")
+        _same_device(z, prior=prior)
+        with torch.cuda.device(z.device):
+            w = torch.empty((n, n_x), dtype=torch.float32, device=z.device)
+            _check(load().ensf_weights(self._h, z.data_ptr(), n, prior.data_ptr(), n_x, d, float(t), float(eps),
+                                       w.data_ptr(), _stream_ptr(stream)), "ensf_weights")
         return w
 
     def profile_enable(self, on: bool = True) -> None:
@@ -398,17 +401,46 @@ class Filter:
         return int(load().ensf_status_sync(self._h, _stream_ptr(stream)))
 
 
+def _weights_shapes(z, prior, out=None):
+    """(n, n_x, d) of particles z [n][d] against members prior [n_x][d],
+    checked before anything reaches the device: the C side sees only
+    pointers, so a short prior or a small `out` would be read or written out
+    of bounds there."""
+    if getattr(z, "dim", None) is None or getattr(prior, "dim", None) is None:
+        raise TypeError("z and prior must be tensors")
+    if z.dim() != 2 or prior.dim() != 2:
+        raise ValueError(f"z and prior must be 2-D, got {tuple(z.shape)} and {tuple(prior.shape)}")
+    n, d = z.shape
+    n_x = prior.shape[0]
+    if prior.shape[1] != d:
+        raise ValueError(f"prior has {prior.shape[1]} state entries per member, z has {d}")
+    if out is not None:
+        if getattr(out, "dim", None) is None or tuple(out.shape) != (n, n_x):
+            raise ValueError(f"out must have shape {(n, n_x)}, got {tuple(getattr(out, 'shape', ()))}")
+    return int(n), int(n_x), int(d)
+
+
+def _same_device(ref, **others):
+    for name, t in others.items():
+        if t is not None and t.device != ref.device:
+            raise ValueError(f"{name} is on {t.device}, z on {ref.device}")
+
+
 def weights_static(z, prior, t: float, eps: float, out=None, stream=None):
-    """Weights of Eq. 16 (FP32 Gram) through the allocation-free entry point:
-    no handle, no workspace; at most 256 particles and 256 members."""
+    """Weights of Eq. 16 (FP32 Gram on centred operands) through the
+    allocation-free entry point: no handle, no workspace; at most 256
+    particles, 256 members and 524288 state entries.  Runs on z's device."""
+    n, n_x, d = _weights_shapes(z, prior, out)
     torch = _torch()
     _dev(z, torch.float32, "z")
     _dev(prior, torch.float32, "prior")
-    n, d = z.shape
-    n_x = prior.shape[0]
-    w = out if out is not None else torch.empty((n, n_x), dtype=torch.float32, device=z.device)
-    _check(load().ensf_weights_static(z.data_ptr(), n, prior.data_ptr(), n_x, d, float(t), float(eps),
-                                      w.data_ptr(), _stream_ptr(stream)), "ensf_weights_static")
+    if out is not None:
+        _dev(out, torch.float32, "out")
+    _same_device(z, prior=prior, out=out)
+    with torch.cuda.device(z.device):
+        w = out if out is not None else torch.empty((n, n_x), dtype=torch.float32, device=z.device)
+        _check(load().ensf_weights_static(z.data_ptr(), n, prior.data_ptr(), n_x, d, float(t), float(eps),
+                                          w.data_ptr(), _stream_ptr(stream)), "ensf_weights_static")
     return w
 
 
@@ -483,6 +515,16 @@ class UNet:
         out = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
         _check(load().ensf_unet_get_params(self._h, out.data_ptr(), _stream_ptr(stream)), "ensf_unet_get_params")
         return out
+
+    def get_moments(self, stream=None):
+        """AdamW state: (first moments, second moments, steps since set_params)."""
+        torch = _torch()
+        m = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        v = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        step = ctypes.c_int64(0)
+        _check(load().ensf_unet_get_moments(self._h, m.data_ptr(), v.data_ptr(), ctypes.byref(step),
+                                            _stream_ptr(stream)), "ensf_unet_get_moments")
+        return m, v, int(step.value)
 
     def forward(self, x, stream=None):
         torch = _torch()

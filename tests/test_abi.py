@@ -77,3 +77,22 @@ def test_binding_fails_loudly_without_device():
         pytest.skip("a CUDA device is present")
     with pytest.raises(RuntimeError):
         ensf.Filter(4, 64)
+
+
+def test_weights_wrappers_reject_mismatched_shapes_on_the_host():
+    """The weights wrappers check shapes before anything reaches the device:
+    the C side sees only pointers, so a prior with fewer columns than z, or
+    an `out` of the wrong shape, would be read or written out of bounds."""
+    import torch
+    z = torch.zeros((4, 16))
+    with pytest.raises(ValueError, match="state entries"):
+        ensf.weights_static(z, torch.zeros((3, 8)), 0.5, 0.05)
+    with pytest.raises(ValueError, match="2-D"):
+        ensf.weights_static(z, torch.zeros((3, 16, 1)), 0.5, 0.05)
+    with pytest.raises(ValueError, match="2-D"):
+        ensf.weights_static(torch.zeros(16), torch.zeros((3, 16)), 0.5, 0.05)
+    with pytest.raises(ValueError, match="out must have shape"):
+        ensf.weights_static(z, torch.zeros((3, 16)), 0.5, 0.05, out=torch.zeros((4, 2)))
+    with pytest.raises(ValueError, match="state entries"):
+        ensf._weights_shapes(z, torch.zeros((3, 32)))
+    assert ensf._weights_shapes(z, torch.zeros((3, 16)), torch.zeros((4, 3))) == (4, 3, 16)

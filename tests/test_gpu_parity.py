@@ -175,7 +175,9 @@ def test_analysis_sparse_arctan_128_rows(path):
     got = _gpu_analysis(p, gram, wx)[rows]
     rel, tie, bad = compare_members(got, ref, cond, tol)
     assert not bad.any(), describe(rel, tie, bad)
-    assert tie.sum() <= 1, describe(rel, tie, bad)
+    # no sampled member of this workload is ill-conditioned: every one is
+    # held to the per-member tolerance
+    assert tie.sum() == 0, describe(rel, tie, bad)
 
 
 def test_analysis_is_deterministic():
@@ -520,7 +522,9 @@ def test_analysis_large_512_rows_in_the_bench_configuration():
         cond = conditioning(p, ref, rows=rows, prec=_cond_prec(gram, wx))
     rel, tie, bad = compare_members(got, ref, cond, tol)
     assert not bad.any(), describe(rel, tie, bad)
-    assert tie.sum() <= 1, describe(rel, tie, bad)
+    # no sampled member of this workload is ill-conditioned: every one is
+    # held to the per-member tolerance
+    assert tie.sum() == 0, describe(rel, tie, bad)
 
 
 GRAM_SHAPES = {

@@ -62,3 +62,47 @@ def test_unet_training_lowers_the_loss():
     for _ in range(60):
         last = float(net.train_step(x, t, lr=3e-3).item())
     assert last < 0.5 * first
+
+
+def test_adamw_step_matches_oracle():
+    """Two AdamW steps of ensf_unet_train_step against the oracle's FP64
+    AdamW update applied to the same gradients: the FP32 master weights and
+    both moments after each step.  The update (w_t - w_{t-1}) must agree to
+    1e-5 relative; the stored weights then differ from the oracle's only by
+    FP32 rounding of w_t itself."""
+    import torch
+    from paper_2407_12168_gb300 import ensf
+    g = np.random.default_rng(5)
+    params = uo.init_params(WIDTHS, seed=6)
+    params[-(WIDTHS[0] * 2 + 2):] = g.uniform(-0.2, 0.2, WIDTHS[0] * 2 + 2).astype(np.float32)
+    net = ensf.UNet(WIDTHS, 32, 32, max_batch=2)
+    net.set_params(torch.from_numpy(params).cuda())
+    lr, wd = 1e-2, 0.05
+    w_prev = params.astype(np.float64)
+    m_prev = np.zeros_like(w_prev)
+    v_prev = np.zeros_like(w_prev)
+    u32 = np.finfo(np.float32).eps
+    for step in (1, 2):
+        x = g.standard_normal((2, 2, 32, 32)).astype(np.float32)
+        t = (x + 0.3 * g.standard_normal(x.shape)).astype(np.float32)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        # the gradient the step will use (the backward pass is deterministic)
+        grad_a, _ = net.gradients(xd, td)
+        grad_b, _ = net.gradients(xd, td)
+        grad = grad_a.cpu().numpy().astype(np.float64)
+        assert np.array_equal(grad, grad_b.cpu().numpy().astype(np.float64))
+        net.train_step(xd, td, lr=lr, weight_decay=wd)
+        w_gpu = net.get_params().cpu().numpy().astype(np.float64)
+        m_gpu, v_gpu, nsteps = net.get_moments()
+        m_gpu = m_gpu.cpu().numpy().astype(np.float64)
+        v_gpu = v_gpu.cpu().numpy().astype(np.float64)
+        assert nsteps == step
+        w_ref, m_ref, v_ref = uo.adamw_step(w_prev, grad, m_prev, v_prev, step, lr, wd)
+        np.testing.assert_allclose(m_gpu, m_ref, rtol=1e-5, atol=1e-30)
+        np.testing.assert_allclose(v_gpu, v_ref, rtol=1e-5, atol=1e-30)
+        upd_err = np.abs(w_gpu - w_ref)
+        bound = 1e-5 * np.abs(w_ref - w_prev) + 2 * u32 * np.abs(w_ref)
+        worst = int(np.argmax(upd_err - bound))
+        assert np.all(upd_err <= bound), (step, worst, w_prev[worst], w_gpu[worst], w_ref[worst])
+        # continue from the GPU's own FP32 state, as the next kernel step does
+        w_prev, m_prev, v_prev = w_gpu, m_gpu, v_gpu
