@@ -242,6 +242,74 @@ ensf_status ensf_analysis_minibatch(ensf_handle *h, const float *prior, int n, i
                                     const uint8_t *obs_mask, int obs_op, float sigma_obs, int K, float eps,
                                     const ensf_noise *noise, const int *perm, int J, float *out, void *stream);
 
+/* ---- d-sharded analysis -------------------------------------------------
+ * One filter whose state is split along d across ranks (the paper runs the
+ * EnSF of one large state on many GPUs, Sec. III-A.3 and the weak-scaling
+ * study of Sec. IV-B).  Every term of an Euler-Maruyama step but one is local
+ * to a block of state columns: H is elementwise and R diagonal, so the
+ * likelihood score, W X and the update (Eq. 7, 15, 17) need only this rank's
+ * columns.  The exception is the Gram cross term z_i . x_j of the log-kernel
+ * (Eq. 12, 16) and the squared norms |x_j - m|^2, sums over all of d: each
+ * rank computes its columns' share, the ranks exchange them, and every rank
+ * then forms the same weights.  The library holds no communicator: the
+ * caller moves the shares between the calls below (e.g. an all-reduce of the
+ * norms once per analysis and an all-gather of the split-K partial Grams once
+ * per step), and the library never waits for another rank.
+ *
+ * Per analysis, on each rank:
+ *   ensf_shard_prep(h, sh, norms)            this slice's norm shares -> norms [n] FP64
+ *   (caller: norms <- sum over ranks of norms)
+ *   for k = 0 .. K-1:
+ *     ensf_shard_gram(h, sh, k, partial)     this slice's S split-K partial Grams
+ *                                            -> partial [S][n][n] FP32
+ *     (caller: gathered [R*S][n][n] <- the R ranks' partials in rank order)
+ *     ensf_shard_update(h, sh, k, gathered, R*S, norms)
+ *                                            softmax over all R*S partials (fixed order),
+ *                                            then W X + score + update of this slice
+ * The counter-based noise is drawn at global state columns col0 + c, so the
+ * sharded analysis draws exactly the numbers of the unsharded one; with equal
+ * split boundaries (each slice a whole number of the unsharded analysis's
+ * split-K ranges) its Gram partials are the unsharded ones, bit for bit.
+ * The handle's max_d bounds d_local; the other ensf_analysis argument rules
+ * apply to the slice (16-byte alignment, d_local % 8 == 0).  The persistent
+ * small-filter mode does not apply (ENSF_EUNSUPPORTED). */
+typedef struct {
+    const float *prior;        /* [n][d_local] this rank's columns of the forecast ensemble */
+    int n;                     /* ensemble size (the same on every rank)                     */
+    int64_t d_local;           /* columns held by this rank                                  */
+    int64_t col0;              /* global index of the first of them                          */
+    const float *y;            /* [d_local] observations of these columns                    */
+    const uint8_t *obs_mask;   /* [d_local], or NULL = all observed                          */
+    int obs_op;                /* ensf_obs_op                                                */
+    float sigma_obs;           /* > 0                                                        */
+    int K;                     /* Euler-Maruyama steps                                       */
+    float eps;                 /* in (0, 1)                                                  */
+    ensf_noise noise;          /* buf: [K+1][n][d_local] these columns' draws, or NULL: Philox */
+    float *out;                /* [n][d_local] these columns of the particles                */
+} ensf_shard;
+
+/* Number S of split-K partial Grams ensf_shard_gram writes for (n, d_local)
+ * with the handle's current shape for that size (set with ensf_set_tuning to
+ * line the slices up with another run's split boundaries). */
+ensf_status ensf_shard_splits(ensf_handle *h, int n, int64_t d_local, int *splits);
+
+/* Preparation of one analysis on this slice: centre, split planes, the
+ * initial particles (out) and this slice's shares of the FP64 squared norms
+ * |x_j - m|^2, written to norms (device, n doubles, caller-owned). */
+ensf_status ensf_shard_prep(ensf_handle *h, const ensf_shard *sh, double *norms, void *stream);
+
+/* Step k, first half: this slice's split-K partial Grams (z_i - alpha m) .
+ * (x_j - m) to partial (device, [S][n][n] FP32, S from ensf_shard_splits,
+ * 16-byte aligned); also draws the step's noise where the tuning puts it. */
+ensf_status ensf_shard_gram(ensf_handle *h, const ensf_shard *sh, int k, float *partial, void *stream);
+
+/* Step k, second half: weights from all ranks' partials (partials: device
+ * [splits_total][n][n] FP32, summed in index order) and the all-reduced norms
+ * (device, n doubles), then W X, score and update of this slice's particles.
+ * After step K-1, `out` holds this slice of the analysis ensemble. */
+ensf_status ensf_shard_update(ensf_handle *h, const ensf_shard *sh, int k, const float *partials, int splits_total,
+                              const double *norms, void *stream);
+
 /* Normalised weights w_ij of Eq. 16 for given particles z [n][d] at pseudo-
  * time t, against the forecast ensemble prior [n_x][d], written to
  * w [n][n_x] FP32.  Uses the handle's Gram precision; this is the Gram +

@@ -136,6 +136,7 @@ ensf::StepCoef step_coef(int k, int K, double eps, double sigma_obs, int obs_op)
     c.inv_2beta2_d = 1.0 / (2.0 * beta2);
     c.k = k;
     c.obs_op = obs_op;
+    c.col0 = 0;
     return c;
 }
 
@@ -443,15 +444,21 @@ cudaError_t gram_operand(const ensf_handle *h, const float *src, int rows, int64
                                    off_lo ? h->at<__nv_bfloat16>(off_lo) : nullptr, d, s, centre, scale, rowmap);
 }
 
+// norms_out: where the FP64 row norms go (NULL: the handle's own); col0: global
+// index of state column 0 (a d-slice of a sharded state draws its initial
+// particles at global columns).
 ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, int K, float eps, float sigma_obs,
                           int obs_op, const ensf_noise *noise, float *out, cudaStream_t s,
-                          const int *perm = nullptr, bool skip_z_split = false) {
+                          const int *perm = nullptr, bool skip_z_split = false, double *norms_out = nullptr,
+                          int64_t col0 = 0) {
     const Layout &L = h->L;
     const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
     float *xbar = h->at<float>(L.xbar);
+    double *norms = norms_out ? norms_out : h->at<double>(L.norms);
     ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_col_mean(prior, n, d, xbar, s));
-    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, h->at<double>(L.norms), s, xbar, perm));
-    ENSF_LAUNCH(h, P_INIT, s, ensf::launch_init_particles(out, n, d, noise->buf, noise->seed, noise->offset, s));
+    ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, norms, s, xbar, perm));
+    ENSF_LAUNCH(h, P_INIT, s,
+                ensf::launch_init_particles(out, n, d, noise->buf, noise->seed, noise->offset, s, col0));
     if (tc_gram) {
         ENSF_LAUNCH(h, P_SPLIT, s, gram_operand(h, prior, n, d, L.xb_hi, L.xb_lo, xbar, 1.0f, perm, s));
         if (!skip_z_split)  // (the FP32-operand Gram splits the particles itself)
@@ -991,6 +998,162 @@ ensf_status ensf_status_sync(ensf_handle *h, void *stream) {
         ENSF_CUDA(cudaStreamSynchronize(s));
         return fail(static_cast<ensf_status>(word), "device reported %s", ensf_status_string(static_cast<ensf_status>(word)));
     }
+    return ENSF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ d-sharded
+namespace {
+
+ensf_status shard_validate(ensf_handle *h, const ensf_shard *sh, const char *who) {
+    if (!h || !sh) return fail(ENSF_EINVAL, "%s: NULL handle or shard", who);
+    ensf_status st = analysis_validate(h, sh->prior, sh->n, sh->d_local, sh->y, sh->obs_mask, sh->obs_op,
+                                       sh->sigma_obs, sh->K, sh->eps, &sh->noise, sh->out);
+    if (st != ENSF_OK) return st;
+    if (sh->col0 < 0 || sh->col0 > (int64_t(1) << 32) - sh->d_local)
+        return fail(ENSF_EINVAL, "%s: col0=%lld outside [0, 2^32 - d_local]", who, (long long)sh->col0);
+    if ((h->cfg.flags & ENSF_FLAG_PERSISTENT) && !is_tc(h->cfg.gram) && !is_tc(h->cfg.wx) && sh->n <= 128)
+        return fail(ENSF_EUNSUPPORTED, "%s: the persistent small-filter mode runs whole analyses only", who);
+    return ENSF_OK;
+}
+
+int shard_split_count(ensf_handle *h, int n, int64_t d_local) {
+    if (!is_tc(h->cfg.gram)) return simt_splits(n, n, d_local, h->sms);
+    ensf::TcGramArgs a{};
+    a.n = n;
+    a.n_x = n;
+    a.d = d_local;
+    a.split3 = (h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
+    a.tf32 = (h->cfg.gram == ENSF_PREC_TF32);
+    a.partial_cap = h->L.partial_floats;
+    return ensf::tc_gram_split_count(h->tc, a, h->sms);
+}
+
+}  // namespace
+
+extern "C" {
+
+ensf_status ensf_shard_splits(ensf_handle *h, int n, int64_t d_local, int *splits) {
+    if (!h || !splits) return fail(ENSF_EINVAL, "ensf_shard_splits: NULL argument");
+    if (n < 1 || n > h->cfg.max_n || d_local < 8 || d_local > h->cfg.max_d || d_local % 8 != 0)
+        return fail(ENSF_EINVAL, "ensf_shard_splits: n or d_local outside the handle's limits");
+    *splits = shard_split_count(h, n, d_local);
+    return *splits > 0 ? ENSF_OK : fail(ENSF_ECUDA, "ensf_shard_splits: no split plan");
+}
+
+ensf_status ensf_shard_prep(ensf_handle *h, const ensf_shard *sh, double *norms, void *stream) {
+    ensf_status st = shard_validate(h, sh, "ensf_shard_prep");
+    if (st != ENSF_OK) return st;
+    if (!norms || (reinterpret_cast<uintptr_t>(norms) & 7u))
+        return fail(ENSF_EINVAL, "ensf_shard_prep: norms must be an 8-byte aligned device array of n doubles");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool gram_f32 = is_tc(h->cfg.gram) &&
+                          ensf::tc_gram_reads_fp32(h->tc, sh->n, sh->n, sh->d_local,
+                                                   h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
+    return analysis_prep(h, sh->prior, sh->n, sh->d_local, sh->K, sh->eps, sh->sigma_obs, sh->obs_op, &sh->noise,
+                         sh->out, s, nullptr, gram_f32, norms, sh->col0);
+}
+
+ensf_status ensf_shard_gram(ensf_handle *h, const ensf_shard *sh, int k, float *partial, void *stream) {
+    ensf_status st = shard_validate(h, sh, "ensf_shard_gram");
+    if (st != ENSF_OK) return st;
+    if (k < 0 || k >= sh->K) return fail(ENSF_EINVAL, "ensf_shard_gram: step k=%d outside [0, K)", k);
+    if (!aligned16(partial)) return fail(ENSF_EINVAL, "ensf_shard_gram: partial must be 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout &L = h->L;
+    const int n = sh->n;
+    const int64_t d = sh->d_local;
+    const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
+    ensf::StepCoef c = step_coef(k, sh->K, sh->eps, sh->sigma_obs, sh->obs_op);
+    c.col0 = sh->col0;
+    const int S = shard_split_count(h, n, d);
+    // the step's draws: written during the Gram by its spare warps (the side-
+    // stream placement of whole analyses is drawn there too: the same numbers),
+    // by a separate launch for a CUDA-core Gram, or evaluated in the W X epilogue
+    const bool pregen = tc_wx && !sh->noise.buf && !h->inline_noise(n, d);
+    float *nslice = tc_wx ? h->at<float>(L.noise) : nullptr;
+    if (pregen && !tc_gram)
+        ENSF_LAUNCH(h, P_NOISE, s,
+                    ensf::launch_noise_slice(sh->noise.seed, sh->noise.offset, k + 1, n, d, nslice, 1 << 30, s,
+                                             sh->col0));
+    if (!tc_gram) {
+        ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_fp32(sh->out, n, sh->prior, n, d, S, partial, s,
+                                                         h->at<float>(L.xbar), c.alpha));
+        return ENSF_OK;
+    }
+    ensf::TcGramArgs a;
+    a.zb_hi = h->at<__nv_bfloat16>(L.zb_hi);
+    a.zb_lo = L.zb_lo ? h->at<__nv_bfloat16>(L.zb_lo) : nullptr;
+    a.xb_hi = h->at<__nv_bfloat16>(L.xb_hi);
+    a.xb_lo = L.xb_lo ? h->at<__nv_bfloat16>(L.xb_lo) : nullptr;
+    a.n = n;
+    a.n_x = n;
+    a.d = d;
+    a.split3 = (h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
+    a.partial = partial;
+    a.partial_cap = std::min<int64_t>(L.partial_floats, (int64_t)S * n * n);
+    a.err = h->err();
+    a.noise = pregen ? nslice : nullptr;
+    a.seed = sh->noise.seed;
+    a.offset = sh->noise.offset;
+    a.noise_k = k + 1;
+    a.noise_col0 = sh->col0;
+    a.z32 = sh->out;
+    a.centre = h->at<float>(L.xbar);
+    a.alpha = c.alpha;
+    if (h->cfg.gram == ENSF_PREC_TF32) {
+        a.tf32 = true;
+        a.zc32 = h->at<float>(L.zb_hi);
+        a.xc32 = h->at<float>(L.xb_hi);
+    }
+    a.pdl = h->use_pdl(n, d);
+    int splits = 0, ldp = 0;
+    int64_t stride = 0;
+    ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_tc(h->tc, a, h->sms, &splits, &stride, &ldp, s));
+    if (splits != S) return fail(ENSF_ECUDA, "ensf_shard_gram: split plan changed (%d, not %d)", splits, S);
+    return ENSF_OK;
+}
+
+ensf_status ensf_shard_update(ensf_handle *h, const ensf_shard *sh, int k, const float *partials, int splits_total,
+                              const double *norms, void *stream) {
+    ensf_status st = shard_validate(h, sh, "ensf_shard_update");
+    if (st != ENSF_OK) return st;
+    if (k < 0 || k >= sh->K) return fail(ENSF_EINVAL, "ensf_shard_update: step k=%d outside [0, K)", k);
+    if (!aligned16(partials) || !norms || (reinterpret_cast<uintptr_t>(norms) & 7u) || splits_total < 1)
+        return fail(ENSF_EINVAL, "ensf_shard_update: partials (16-byte aligned), norms and splits_total >= 1 needed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout &L = h->L;
+    const int n = sh->n;
+    const int64_t d = sh->d_local;
+    const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
+    ensf::StepCoef c = step_coef(k, sh->K, sh->eps, sh->sigma_obs, sh->obs_op);
+    c.col0 = sh->col0;
+    const float alpha_next = step_coef(k + 1, sh->K, sh->eps, sh->sigma_obs, sh->obs_op).alpha;
+    // the row softmax of Eq. 16 over the gathered partials (every rank the same)
+    __nv_bfloat16 *wb_hi = tc_wx ? h->at<__nv_bfloat16>(L.wb_hi) : nullptr;
+    __nv_bfloat16 *wb_lo = (tc_wx && L.wb_lo) ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
+    ENSF_LAUNCH(h, P_SOFTMAX, s,
+                ensf::launch_softmax_rows(partials, splits_total, (int64_t)n * n, n, n, n, norms, c.alpha_d,
+                                          c.inv_2beta2_d, tc_wx ? nullptr : h->at<float>(L.w), n, wb_hi, wb_lo,
+                                          (int)round_up(n, 8), s, h->use_pdl(n, d)));
+    const bool gram_f32 =
+        tc_gram && ensf::tc_gram_reads_fp32(h->tc, n, n, d, h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
+    if (!tc_wx) {
+        ENSF_LAUNCH(h, P_WXEM, s,
+                    ensf::launch_wx_em_fp32(h->at<float>(L.w), n, sh->prior, n, n, d, sh->out, sh->y, sh->obs_mask,
+                                            sh->noise.buf, sh->noise.seed, sh->noise.offset, c, s));
+        if (tc_gram && !gram_f32)
+            ENSF_LAUNCH(h, P_SPLIT, s,
+                        gram_operand(h, sh->out, n, d, L.zb_hi, L.zb_lo, h->at<float>(L.xbar), alpha_next, nullptr,
+                                     s));
+    } else {
+        ensf::TcWxArgs a = wx_args(h, n, d, sh->y, sh->obs_mask, &sh->noise, sh->out, c, alpha_next, k);
+        if (gram_f32) a.zb_hi = a.zb_lo = nullptr;
+        ENSF_LAUNCH(h, P_WXEM, s, ensf::launch_wx_em_tc(h->tc, a, h->sms, s));
+    }
+    if (k == sh->K - 1 && (h->cfg.flags & ENSF_FLAG_CHECK_FINITE))
+        ENSF_LAUNCH(h, P_CHECK, s, ensf::launch_check_finite(sh->out, (int64_t)n * d, h->err(), s));
     return ENSF_OK;
 }
 

@@ -25,6 +25,9 @@ struct StepCoef {
     double inv_2beta2_d;// 1 / (2 beta_t^2) (double, for the logits)
     int k;              // step index; the step consumes noise slice k + 1
     int obs_op;         // 0 identity, 1 arctan
+    int64_t col0;       // global index of state column 0 of the kernel's operands (the
+                        // noise counter uses global columns: a slice of the state draws
+                        // what the whole state draws there); 0 for a whole state
 };
 
 // Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11): ten

@@ -29,14 +29,15 @@ cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
 }
 
 // ---- CUDA-core kernels (ensf_simt.cu) ----------------------------------
-// z[i][c] <- xi[0][i][c] (noise buffer or Philox stream)
+// z[i][c] <- xi[0][i][c] (noise buffer or Philox stream; the stream is drawn at
+// global column col0 + c)
 cudaError_t launch_init_particles(float *z, int n, int64_t d, const float *noise_buf,
-                                  uint64_t seed, uint32_t offset, cudaStream_t s);
+                                  uint64_t seed, uint32_t offset, cudaStream_t s, int64_t col0 = 0);
 cudaError_t launch_philox_normal(uint64_t seed, uint32_t offset, int k0, int count, int n,
                                  int64_t d, float *out, cudaStream_t s);
-// out[i][c] = xi[k][i][c] (one slice), at most max_blocks blocks of 256 threads
+// out[i][c] = xi[k][i][col0 + c] (one slice), at most max_blocks blocks of 256 threads
 cudaError_t launch_noise_slice(uint64_t seed, uint32_t offset, int k, int n, int64_t d, float *out,
-                               int max_blocks, cudaStream_t s);
+                               int max_blocks, cudaStream_t s, int64_t col0 = 0);
 // out[j] = |x_j - centre|^2 in FP64 (centre may be NULL)
 // (rows: optional row map, row r of the result reads row rows[r] of x)
 cudaError_t launch_row_norms(const float *x, int n, int64_t d, double *out, cudaStream_t s,

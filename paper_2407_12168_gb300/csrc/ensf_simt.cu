@@ -100,14 +100,14 @@ __global__ void k_philox_normal(uint64_t seed, uint32_t offset, int k0, int n, i
 // over (particle quad, column) pairs) so that it can share the SMs with a
 // concurrently running Gram without crowding out its blocks.
 __global__ void __launch_bounds__(256) k_noise_slice(uint64_t seed, uint32_t offset, int k, int n, int64_t d,
-                                                     float *__restrict__ out) {
+                                                     float *__restrict__ out, int64_t col0) {
     const int64_t quads = (n + 3) / 4;
     const int64_t total = quads * d;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int qd = (int)(idx / d);
         const int64_t c = idx - (int64_t)qd * d;
-        float4 v = noise4(seed, offset, k, c, qd);
+        float4 v = noise4(seed, offset, k, c + col0, qd);
         const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_noise_slice(uint64_t seed, uint32_t off
 // z[i][c] <- xi[0][i][c]; one thread per (column c, particle quad).
 __global__ void k_init_particles(float *__restrict__ z, int n, int64_t d,
                                  const float *__restrict__ noise_buf, uint64_t seed,
-                                 uint32_t offset) {
+                                 uint32_t offset, int64_t col0) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int qd = blockIdx.y;
     if (c >= d) return;
@@ -132,7 +132,7 @@ __global__ void k_init_particles(float *__restrict__ z, int n, int64_t d,
             vv[r] = i < n ? noise_buf[(int64_t)i * d + c] : 0.f;
         }
     } else {
-        float4 v = noise4(seed, offset, 0, c, qd);
+        float4 v = noise4(seed, offset, 0, c + col0, qd);
         vv[0] = v.x; vv[1] = v.y; vv[2] = v.z; vv[3] = v.w;
     }
 #pragma unroll
@@ -269,7 +269,7 @@ k_wx_em_fp32(const float *__restrict__ w, int ldw, const float *__restrict__ x, 
             for (int r = 0; r < 4; ++r)
                 xi[r][q] = (ib + r < n) ? noise_buf[((int64_t)(cf.k + 1) * n + ib + r) * d + c + q] : 0.f;
         } else {
-            float4 v = noise4(seed, offset, cf.k + 1, c + q, ib >> 2);
+            float4 v = noise4(seed, offset, cf.k + 1, c + q + cf.col0, ib >> 2);
             xi[0][q] = v.x; xi[1][q] = v.y; xi[2][q] = v.z; xi[3][q] = v.w;
         }
     }
@@ -489,9 +489,9 @@ cudaError_t launch_relax_spread(const float *prior, float *z, int n, int64_t d, 
 
 // ===========================================================================
 cudaError_t launch_init_particles(float *z, int n, int64_t d, const float *noise_buf,
-                                  uint64_t seed, uint32_t offset, cudaStream_t s) {
+                                  uint64_t seed, uint32_t offset, cudaStream_t s, int64_t col0) {
     dim3 grid((unsigned)((d + 255) / 256), (unsigned)((n + 3) / 4));
-    k_init_particles<<<grid, 256, 0, s>>>(z, n, d, noise_buf, seed, offset);
+    k_init_particles<<<grid, 256, 0, s>>>(z, n, d, noise_buf, seed, offset, col0);
     return cudaGetLastError();
 }
 
@@ -503,11 +503,11 @@ cudaError_t launch_philox_normal(uint64_t seed, uint32_t offset, int k0, int cou
 }
 
 cudaError_t launch_noise_slice(uint64_t seed, uint32_t offset, int k, int n, int64_t d, float *out,
-                               int max_blocks, cudaStream_t s) {
+                               int max_blocks, cudaStream_t s, int64_t col0) {
     const int64_t total = (int64_t)((n + 3) / 4) * d;
     int64_t blocks = (total + 255) / 256;
     if (blocks > max_blocks) blocks = max_blocks;
-    k_noise_slice<<<(unsigned)blocks, 256, 0, s>>>(seed, offset, k, n, d, out);
+    k_noise_slice<<<(unsigned)blocks, 256, 0, s>>>(seed, offset, k, n, d, out, col0);
     return cudaGetLastError();
 }
 

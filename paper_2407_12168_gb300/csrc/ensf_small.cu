@@ -117,6 +117,7 @@ __device__ StepCoef step_coef_dev(int k, int K, double eps, float inv_r, int obs
     c.inv_2beta2_d = __ddiv_rn(1.0, __dmul_rn(2.0, beta2));
     c.k = k;
     c.obs_op = obs_op;
+    c.col0 = 0;
     return c;
 }
 

@@ -381,6 +381,7 @@ struct GramParams {
     uint32_t offset;
     int noise_k;
     int64_t d;
+    int64_t noise_col0;  // global index of state column 0 (noise counters use global columns)
     int noise_warp0;   // first warp that generates noise (2: warps 2-9, 6: warps 6-9)
     // FP32-operand form: A = z - alpha m split in the kernel (centre m, [d])
     float alpha;
@@ -404,8 +405,8 @@ __device__ __forceinline__ void gram_noise_share(const GramParams &p) {
     for (int qd = 0; qd < quads; ++qd) {
         for (int64_t col = c0 + et; col < c1; col += 2 * kStride) {
             const int64_t col2 = col + kStride;
-            const float4 v = noise4(p.seed, p.offset, p.noise_k, col, qd);
-            const float4 v2 = col2 < c1 ? noise4(p.seed, p.offset, p.noise_k, col2, qd) : v;
+            const float4 v = noise4(p.seed, p.offset, p.noise_k, col + p.noise_col0, qd);
+            const float4 v2 = col2 < c1 ? noise4(p.seed, p.offset, p.noise_k, col2 + p.noise_col0, qd) : v;
             const float vv[4] = {v.x, v.y, v.z, v.w}, vv2[4] = {v2.x, v2.y, v2.z, v2.w};
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -1192,7 +1193,7 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
                     // xi[k+1][i0 .. i0+15][c]: four Philox blocks of four particles each
 #pragma unroll
                     for (int e4 = 0; e4 < 4; ++e4) {
-                        const float4 v = noise4(p.seed, p.offset, cf.k + 1, c, (i0 >> 2) + e4);
+                        const float4 v = noise4(p.seed, p.offset, cf.k + 1, c + cf.col0, (i0 >> 2) + e4);
                         xi[e4 * 4 + 0] = v.x;
                         xi[e4 * 4 + 1] = v.y;
                         xi[e4 * 4 + 2] = v.z;
@@ -1600,6 +1601,30 @@ GramChoice default_gram_choice(const TcGramArgs &a) {
     return g;
 }
 
+// Split-K plan of a Gram launch with shape choice ch: the k-block width, the
+// k-blocks per split and the number of splits that hold work (returned).
+int gram_split_plan(const TcGramArgs &a, const GramChoice &ch, int sms, int *kblocks, int *kb_per_split) {
+    int KB, BN;
+    if (a.tf32) {
+        const bool pair = ch.pair && a.n % kPairTile == 0 && a.n_x % kPairTile == 0;
+        KB = 32;
+        BN = (pair || ch.bn != 128) ? 256 : 128;
+    } else {
+        const bool pair = ch.pair && a.split3 && a.n % kPairTile == 0 && a.n_x % kPairTile == 0;
+        BN = pair ? kPairTile : ch.bn;
+        KB = pair ? BK : (ch.bk == 32 ? 32 : BK);
+    }
+    const int mt = (a.n + BM - 1) / BM, nt = (a.n_x + BN - 1) / BN;
+    const int kb = static_cast<int>((a.d + KB - 1) / KB);
+    const int64_t per_split = static_cast<int64_t>(a.n) * a.n_x;
+    int S = ch.splits > 0 ? ch.splits : choose_splits(mt * nt, kb, sms, per_split, a.partial_cap);
+    S = std::max(1, std::min<int>(S, static_cast<int>(std::min<int64_t>(kb, a.partial_cap / per_split))));
+    const int kbps = (kb + S - 1) / S;
+    *kblocks = kb;
+    *kb_per_split = kbps;
+    return (kb + kbps - 1) / kbps;  // splits that hold work
+}
+
 cudaError_t gram_launch_tf32(TcContext *ctx, const TcGramArgs &a, int sms, const GramChoice &ch, int *splits,
                              int64_t *part_stride, int *ldp, cudaStream_t s) {
     constexpr int KB = 32;  // 32 FP32 = one 128-byte swizzle row
@@ -1616,18 +1641,15 @@ cudaError_t gram_launch_tf32(TcContext *ctx, const TcGramArgs &a, int sms, const
     GramParams p;
     p.n = a.n;
     p.n_x = a.n_x;
-    p.kblocks = static_cast<int>((a.d + KB - 1) / KB);
     const int64_t per_split = static_cast<int64_t>(a.n) * a.n_x;
-    int S = ch.splits > 0 ? ch.splits : choose_splits(mt * nt, p.kblocks, sms, per_split, a.partial_cap);
-    S = std::max(1, std::min<int>(S, static_cast<int>(std::min<int64_t>(p.kblocks, a.partial_cap / per_split))));
-    p.kb_per_split = (p.kblocks + S - 1) / S;
-    S = (p.kblocks + p.kb_per_split - 1) / p.kb_per_split;
+    int S = gram_split_plan(a, ch, sms, &p.kblocks, &p.kb_per_split);
     p.partial = a.partial;
     p.err = a.err;
     p.noise = a.noise;
     p.seed = a.seed;
     p.offset = a.offset;
     p.noise_k = a.noise_k;
+    p.noise_col0 = a.noise_col0;
     p.pdl = a.pdl;
     p.d = a.d;
     p.noise_warp0 = ch.noise_warps == 4 ? 6 : 2;
@@ -1670,18 +1692,15 @@ cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const Gram
     GramParams p;
     p.n = a.n;
     p.n_x = a.n_x;
-    p.kblocks = static_cast<int>((a.d + KB - 1) / KB);
     const int64_t per_split = static_cast<int64_t>(a.n) * a.n_x;
-    int S = ch.splits > 0 ? ch.splits : choose_splits(mt * nt, p.kblocks, sms, per_split, a.partial_cap);
-    S = std::max(1, std::min<int>(S, static_cast<int>(std::min<int64_t>(p.kblocks, a.partial_cap / per_split))));
-    p.kb_per_split = (p.kblocks + S - 1) / S;
-    S = (p.kblocks + p.kb_per_split - 1) / p.kb_per_split;  // splits that hold work
+    int S = gram_split_plan(a, ch, sms, &p.kblocks, &p.kb_per_split);
     p.partial = a.partial;
     p.err = a.err;
     p.noise = a.noise;
     p.seed = a.seed;
     p.offset = a.offset;
     p.noise_k = a.noise_k;
+    p.noise_col0 = a.noise_col0;
     p.pdl = a.pdl;
     p.d = a.d;
     // the FP32 form's warps 2-9 split A and warps 10-15 generate the noise
@@ -1723,6 +1742,18 @@ cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *sp
         if (it != ctx->gram_tuned.end()) ch = it->second;
     }
     return gram_launch(ctx, a, sms, ch, splits, part_stride, ldp, s);
+}
+
+int tc_gram_split_count(TcContext *ctx, const TcGramArgs &a, int sms) {
+    if (!ctx) return 0;
+    GramChoice ch = default_gram_choice(a);
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        auto it = ctx->gram_tuned.find(std::make_tuple(a.n, a.n_x, a.d, a.split3));
+        if (it != ctx->gram_tuned.end()) ch = it->second;
+    }
+    int kb = 0, kbps = 0;
+    return gram_split_plan(a, ch, sms, &kb, &kbps);
 }
 
 cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStream_t s) {

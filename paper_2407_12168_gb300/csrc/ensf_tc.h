@@ -53,6 +53,7 @@ struct TcGramArgs {
     uint64_t seed;
     uint32_t offset;
     int noise_k;
+    int64_t noise_col0 = 0;              // global column of column 0 (noise counters are global)
     // the FP32 particles [n][d] and the centre, for the form that splits
     // z - alpha * centre itself (NULL: only the BF16 planes are available)
     const float *z32 = nullptr;
@@ -156,6 +157,9 @@ cudaError_t launch_selftest_mbar_wait(int *err, cudaStream_t s);
 // True when the tuned Gram for this shape reads the FP32 particles (the W X
 // epilogue then need not write the BF16 particle planes).
 bool tc_gram_reads_fp32(TcContext *ctx, int n, int n_x, int64_t d, bool split3);
+// Number of split-K partial Grams launch_gram_tc writes for these arguments
+// (with the shape recorded for them, or the default one).
+int tc_gram_split_count(TcContext *ctx, const TcGramArgs &a, int sms);
 cudaError_t tc_autotune(TcContext *ctx, const TcGramArgs *g, const TcWxArgs *w, int sms, cudaStream_t s,
                         TcTuneReport *rep, AfterGram after_gram = nullptr, void *after_ctx = nullptr);
 

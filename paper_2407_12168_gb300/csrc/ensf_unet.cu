@@ -306,14 +306,17 @@ __global__ void k_unpad_grad(const float *__restrict__ c, int Co, int K9, int Kp
     g[i] = c[(i / K9) * Kp + i % K9];
 }
 
+// AdamW on the FP32 master weights.  The coefficients arrive from the host,
+// where 1 - beta and the bias corrections 1 - beta^t are formed in double and
+// rounded once (1 - fl32(0.999) would be 1.3e-5 away from 0.001).
 __global__ void k_adamw(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
-                        float *__restrict__ v, int64_t count, float lr, float b1, float b2, float eps, float wd,
-                        float c1, float c2) {
+                        float *__restrict__ v, int64_t count, float lr, float b1, float b2, float omb1, float omb2,
+                        float eps, float wd, float c1, float c2) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + omb1 * gi;
+    const float vi = b2 * v[i] + omb2 * gi * gi;
     m[i] = mi;
     v[i] = vi;
     w[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
@@ -780,10 +783,11 @@ ensf_status ensf_unet_train_step(ensf_unet *u, const float *x, const float *targ
     if (st != ENSF_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     u->step += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - (float)std::pow(b1, (double)u->step), c2 = 1.f - (float)std::pow(b2, (double)u->step);
-    k_adamw<<<nb(u->nparams), 256, 0, s>>>(u->params, u->grads, u->adam_m, u->adam_v, u->nparams, lr, b1, b2, 1e-8f,
-                                          weight_decay, c1, c2);
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - std::pow(b1, (double)u->step)), c2 = (float)(1.0 - std::pow(b2, (double)u->step));
+    k_adamw<<<nb(u->nparams), 256, 0, s>>>(u->params, u->grads, u->adam_m, u->adam_v, u->nparams, lr, (float)b1,
+                                          (float)b2, (float)(1.0 - b1), (float)(1.0 - b2), 1e-8f, weight_decay, c1,
+                                          c2);
     UNET_LAUNCH();
     return repack(u, s);
 }

@@ -43,6 +43,13 @@ class EnsfInstance(ctypes.Structure):
                 ("noise", EnsfNoise), ("out", ctypes.c_void_p)]
 
 
+class EnsfShard(ctypes.Structure):
+    _fields_ = [("prior", ctypes.c_void_p), ("n", ctypes.c_int), ("d_local", ctypes.c_int64),
+                ("col0", ctypes.c_int64), ("y", ctypes.c_void_p), ("obs_mask", ctypes.c_void_p),
+                ("obs_op", ctypes.c_int), ("sigma_obs", ctypes.c_float), ("K", ctypes.c_int),
+                ("eps", ctypes.c_float), ("noise", EnsfNoise), ("out", ctypes.c_void_p)]
+
+
 class EnsfProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double)]
@@ -100,6 +107,14 @@ _SIGNATURES = [
                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                              ctypes.c_void_p]),
     ("ensf_set_batch_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("ensf_shard_splits", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    ("ensf_shard_prep", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EnsfShard), ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    ("ensf_shard_gram", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EnsfShard), ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    ("ensf_shard_update", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EnsfShard), ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_void_p, ctypes.c_void_p]),
@@ -283,6 +298,77 @@ class Filter:
                                               perm.data_ptr(), int(J), out.data_ptr(), _stream_ptr(stream)),
                "ensf_analysis_minibatch")
         return out
+
+    # ---- d-sharded analysis: this handle runs one slice of the state ----
+    def shard(self, prior, y, mask, sigma_obs: float, K: int, eps: float, col0: int, obs_op: int = OBS_IDENTITY,
+              seed: int = 0, offset: int = 0, noise=None, out=None):
+        """Descriptor of this rank's slice (columns col0 .. col0 + d_local - 1
+        of the state) for shard_prep / shard_gram / shard_update; the tensors
+        are kept alive in it."""
+        torch = _torch()
+        _dev(prior, torch.float32, "prior")
+        n, d_local = prior.shape
+        _dev(y, torch.float32, "y")
+        if tuple(y.shape) != (d_local,):
+            raise ValueError(f"y must have shape {(d_local,)}")
+        if mask is not None:
+            _dev(mask, torch.uint8, "mask")
+            if tuple(mask.shape) != (d_local,):
+                raise ValueError(f"mask must have shape {(d_local,)}")
+        if noise is not None:
+            _dev(noise, torch.float32, "noise")
+            if tuple(noise.shape) != (K + 1, n, d_local):
+                raise ValueError(f"noise must have shape {(K + 1, n, d_local)}")
+        if out is None:
+            out = torch.empty_like(prior)
+        _dev(out, torch.float32, "out")
+        if tuple(out.shape) != (n, d_local):
+            raise ValueError(f"out must have shape {(n, d_local)}")
+        desc = EnsfShard(prior.data_ptr(), n, d_local, int(col0), y.data_ptr(),
+                         mask.data_ptr() if mask is not None else None, int(obs_op), float(sigma_obs), int(K),
+                         float(eps),
+                         EnsfNoise(noise.data_ptr() if noise is not None else None, int(seed) & (2 ** 64 - 1),
+                                   int(offset) & 0xFFFFFFFF), out.data_ptr())
+        desc._keep = (prior, y, mask, noise, out)
+        desc.out_tensor = out
+        return desc
+
+    def shard_splits(self, n: int, d_local: int) -> int:
+        """Split-K partial Grams per step that shard_gram writes for (n, d_local)."""
+        S = ctypes.c_int(0)
+        _check(load().ensf_shard_splits(self._h, int(n), int(d_local), ctypes.byref(S)), "ensf_shard_splits")
+        return int(S.value)
+
+    def shard_prep(self, desc, norms, stream=None):
+        """Preparation of this slice; writes its shares of the FP64 norms to ``norms`` [n]."""
+        torch = _torch()
+        _dev(norms, torch.float64, "norms")
+        if norms.numel() != desc.n:
+            raise ValueError(f"norms must hold {desc.n} doubles")
+        _check(load().ensf_shard_prep(self._h, ctypes.byref(desc), norms.data_ptr(), _stream_ptr(stream)),
+               "ensf_shard_prep")
+
+    def shard_gram(self, desc, k: int, partial, stream=None):
+        """Step k: this slice's split-K partial Grams into ``partial`` [S][n][n] FP32."""
+        torch = _torch()
+        _dev(partial, torch.float32, "partial")
+        if partial.dim() != 3 or tuple(partial.shape[1:]) != (desc.n, desc.n) or \
+                partial.shape[0] != self.shard_splits(desc.n, desc.d_local):
+            raise ValueError("partial must be [S][n][n] with S = shard_splits(n, d_local)")
+        _check(load().ensf_shard_gram(self._h, ctypes.byref(desc), int(k), partial.data_ptr(), _stream_ptr(stream)),
+               "ensf_shard_gram")
+
+    def shard_update(self, desc, k: int, partials, norms, stream=None):
+        """Step k: weights from every rank's partials ([R*S][n][n], rank
+        order) and the summed norms, then W X + score + update of this slice."""
+        torch = _torch()
+        _dev(partials, torch.float32, "partials")
+        _dev(norms, torch.float64, "norms")
+        if partials.dim() != 3 or tuple(partials.shape[1:]) != (desc.n, desc.n) or norms.numel() != desc.n:
+            raise ValueError("partials must be [splits][n][n] and norms [n]")
+        _check(load().ensf_shard_update(self._h, ctypes.byref(desc), int(k), partials.data_ptr(),
+                                        int(partials.shape[0]), norms.data_ptr(), _stream_ptr(stream)),
+               "ensf_shard_update")
 
     def set_tuning(self, n: int, d: int, gram_tile_n: int, gram_stages: int, gram_k_block: int = 64,
                    gram_splits: int = 0, wx_tile_n: int = 0, gram_cta_pair: int = 0, gram_noise_warps: int = 0,
