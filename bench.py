@@ -4,7 +4,10 @@
 One "step" is one full analysis (Sec. III-A.2): row norms and splits of the
 forecast ensemble, the initial Gaussian particles, then K Euler-Maruyama steps
 of Gram + softmax + weighted sum + score + update.  Metric: member-steps/s =
-N * K / (wall time of one analysis), summed over ranks.
+N * K / (wall time of one analysis).  With several GPUs (torchrun) one filter
+is split along the state dimension over the GPUs (strong scaling); with
+--replicas every GPU runs its own filter and the ranks' member-steps add up
+(weak scaling).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--path split-bf16|split|fp32] [--impl ours|reference]
@@ -288,6 +291,30 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
             "executed_frac": executed / (avg_ms / 1e3) / 1e12 / peak}
 
 
+def _host_buffers(ensf, p, small_pages=False):
+    """Page-locked host copies of the inputs and a host buffer for the result
+    (ensf_host_alloc: huge pages unless small_pages), and a record of how much
+    of them the kernel backs with huge pages."""
+    import torch
+    huge = not small_pages
+    h_prior = ensf.host_empty(p.prior.shape, torch.float32, huge)
+    h_prior.copy_(torch.from_numpy(p.prior))
+    h_y = ensf.host_empty(p.y.shape, torch.float32, huge)
+    h_y.copy_(torch.from_numpy(p.y))
+    h_mask = None
+    if p.mask is not None:
+        h_mask = ensf.host_empty(p.mask.shape, torch.uint8, huge)
+        h_mask.copy_(torch.from_numpy(p.mask))
+    h_out = ensf.host_empty(p.prior.shape, torch.float32, huge)
+    rec = {"alloc": "ensf_host_alloc" + ("" if huge else " (small pages)")}
+    try:
+        rec["huge_page_fraction"] = {"prior": round(ensf.host_huge_fraction(h_prior), 3),
+                                     "out": round(ensf.host_huge_fraction(h_out), 3)}
+    except Exception as e:  # no smaps: the buffers are still page-locked
+        rec["huge_page_fraction"] = str(e)
+    return h_prior, h_y, h_mask, h_out, rec
+
+
 def run_batched(args):
     """64 independent filters with uneven N and d (K = 50).  split paths: one
     batched launch per stage for all filters; fp32: one analysis call per
@@ -452,20 +479,43 @@ def run_ours(args):
         one(w)
     torch.cuda.synchronize()
 
-    # ---- end-to-end buffers: pinned host copies of the inputs and the result ----
-    h_prior = torch.from_numpy(p.prior).pin_memory()
-    h_y = torch.from_numpy(p.y).pin_memory()
-    h_mask = torch.from_numpy(p.mask).pin_memory() if p.mask is not None else None
-    h_out = torch.empty(prior.shape, dtype=torch.float32).pin_memory()
+    # ---- end-to-end buffers: page-locked host copies of the inputs and the
+    # result, backed by huge pages (ensf_host_alloc; buffers pinned page by
+    # page copied 3-6x slower right after an analysis on a host that had been
+    # busy) ----
+    h_prior, h_y, h_mask, h_out, host_huge = _host_buffers(ensf, p, args.small_pages)
     d_prior, d_y = torch.empty_like(prior), torch.empty_like(y)
     d_mask = torch.empty_like(mask) if mask is not None else None
-    e2e_steps = max(1, min(args.steps, 3))
+    # sequential end-to-end steps (copy in, analyse, copy out, the host takes
+    # the result): the end-to-end figure of the mini-batch form, and for the
+    # other forms one step that shows the raw copy times
+    pipelined = not J
+    e2e_steps = 1 if pipelined else max(1, min(args.steps, 3))
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    # the inner boundaries: inputs on the device, analysis done
+    ei = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    # pipelined end-to-end steps (Filter.analyses_from_host): the copies of
+    # analysis s +/- 1 overlap analysis s
+    pipe_steps = max(3, min(args.steps, 8))
+    h_out2 = ensf.host_empty(p.prior.shape, torch.float32, not args.small_pages) if pipelined else None
+    copy_stream = torch.cuda.Stream() if pipelined else None
     # one untimed pass first: the first device writes into freshly pinned host
     # pages cost a one-time mapping
     d_prior.copy_(h_prior, non_blocking=True)
     h_out.copy_(d_prior, non_blocking=True)
+    if h_out2 is not None:
+        h_out2.copy_(d_prior, non_blocking=True)
     torch.cuda.synchronize()
+
+    def e2e_pipelined():
+        jobs = [dict(prior=h_prior, y=h_y, mask=h_mask, out=(h_out, h_out2)[i % 2], seed=p.seed + 300 + i)
+                for i in range(pipe_steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        evs = f.analyses_from_host(jobs, p.sigma_obs, p.K, p.eps, p.obs_op, stream=stream,
+                                   copy_stream=copy_stream)
+        t1.record(stream)
+        return t0, t1, evs
 
     def e2e_step(s_):
         """One analysis through host buffers: host-to-device copies of the
@@ -473,12 +523,14 @@ def run_ours(args):
         if flush is not None:
             flush.zero_()
         ee[s_][0].record(stream)
-        d_prior.copy_(h_prior, non_blocking=True)
+        ensf.copy_sm(d_prior, h_prior, 152)
         d_y.copy_(h_y, non_blocking=True)
         if d_mask is not None:
             d_mask.copy_(h_mask, non_blocking=True)
+        ei[s_][0].record(stream)
         analyse(d_prior, d_y, d_mask, 200 + s_)
-        h_out.copy_(out, non_blocking=True)
+        ei[s_][1].record(stream)
+        ensf.copy_sm(h_out, out, 152)
         ee[s_][1].record(stream)
         # the host takes the result before the next analysis is enqueued
         torch.cuda.synchronize()
@@ -502,6 +554,7 @@ def run_ours(args):
             ev[s_][1].record(stream)
             if s_ < e2e_steps:
                 e2e_step(s_)
+        pipe = e2e_pipelined() if pipelined else None
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -510,7 +563,23 @@ def run_ours(args):
     if f.status_sync() != 0:
         raise RuntimeError("device error during the benchmark")
     e2e_each = [a.elapsed_time(b) for a, b in ee]
-    e2e_ms = float(sum(e2e_each)) / e2e_steps
+    seq = {"ms_per_step": [round(v, 2) for v in e2e_each],
+           "h2d_ms": [round(ee[i][0].elapsed_time(ei[i][0]), 2) for i in range(e2e_steps)],
+           "analysis_ms": [round(ei[i][0].elapsed_time(ei[i][1]), 2) for i in range(e2e_steps)],
+           "d2h_ms": [round(ei[i][1].elapsed_time(ee[i][1]), 2) for i in range(e2e_steps)]}
+    if pipelined:
+        t0, t1, evs = pipe
+        e2e_ms = t0.elapsed_time(t1) / pipe_steps
+        e2e_parts = {"mode": f"{pipe_steps} analyses through host buffers, each one's copy-in and the previous "
+                             f"one's copy-out overlapping the analysis before and after (Filter.analyses_from_host)",
+                     "ms_per_step": round(e2e_ms, 2),
+                     "copy_in_to_analysed_ms": [round(a.elapsed_time(b), 2) for a, b, _ in evs],
+                     "analysed_to_copied_out_ms": [round(b.elapsed_time(c), 2) for _, b, c in evs],
+                     "sequential_step": seq, "host_buffers": host_huge}
+    else:
+        e2e_ms = float(sum(e2e_each)) / e2e_steps
+        e2e_parts = dict(seq, mode="sequential: copy in, analyse, copy out, host takes the result",
+                         host_buffers=host_huge)
     h2d = p.prior.nbytes + p.y.nbytes + (p.mask.nbytes if p.mask is not None else 0)
     d2h = p.n * p.d * 4
     # ---- per-kernel timing: the same steps again, every launch bracketed by
@@ -591,7 +660,10 @@ def run_ours(args):
     dom = max(kernels, key=lambda k: kernels[k][2])
     roof = rooflines.get(dom) or _roofline(dom, kernels[dom], p, gram, wx, args, peaks)
     other = {k: v for k, v in rooflines.items() if k != dom}
-    gpu_launches = int(sum(v[0] for v in prof.values()))
+    # launches in the timed region: the profiled pass repeats the device-timed
+    # analyses; the end-to-end analyses launch the same kernels
+    per_analysis = sum(v[0] for v in prof.values()) / args.steps
+    gpu_launches = int(round(per_analysis * (args.steps + e2e_steps + (pipe_steps if pipelined else 0))))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -606,8 +678,8 @@ def run_ours(args):
             "roofline": roof, "accuracy": accuracy,
             "roofline_other": other,
             "kernels": {k: {"launches": v[0], "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": [round(v, 2) for v in e2e_each]},
+            "e2e": dict({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                        **e2e_parts),
             "gpu_launches": gpu_launches, "clocks": clk.summary(), "tuning": tuning, "cuda_graph": args.graph,
             "persistent": args.persistent}
     if not args.no_cpu_baseline:
@@ -623,6 +695,175 @@ def run_ours(args):
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def run_sharded(args):
+    """One filter whose state is split along d over the ranks, one per GPU
+    (the paper's single large-state EnSF on many GPUs, Sec. IV-B): every rank
+    runs the per-slice kernels on its columns; the split-K partial Grams are
+    all-gathered over NCCL every Euler-Maruyama step and the FP64 norms
+    all-reduced once per analysis (paper_2407_12168_gb300.sharded).  Strong
+    scaling: the same filter whatever the number of ranks."""
+    import types
+
+    import torch
+    import torch.distributed as dist
+    rank, local_rank, world = _dist_env()
+    torch.cuda.set_device(local_rank)
+    dist.init_process_group("nccl")
+    from paper_2407_12168_gb300 import ensf, sharded
+
+    gram, wx = PATHS[args.path]
+    p = make_problem(args.workload, 0)               # one filter, the same on every rank
+    c0, dl = sharded.split_columns(p.d, world)[rank]
+    dev = torch.device("cuda", local_rank)
+    prior = torch.from_numpy(np.ascontiguousarray(p.prior[:, c0:c0 + dl])).to(dev)
+    y = torch.from_numpy(np.ascontiguousarray(p.y[c0:c0 + dl])).to(dev)
+    mask = None if p.mask is None else torch.from_numpy(np.ascontiguousarray(p.mask[c0:c0 + dl])).to(dev)
+    out = torch.empty_like(prior)
+    be = sharded.CudaShardBackend(p.n, dl, gram=gram, wx=wx, inline_noise=args.inline_noise)
+    # launch shapes: rank 0 tunes on its slice, every rank records the same
+    # shapes (the split count fixes the layout of the gathered partials)
+    tuning = None
+    if gram != "fp32" or wx != "fp32":
+        if args.set_tuning:
+            tuning = dict(json.loads(args.set_tuning))
+        elif rank == 0:
+            tuning = be.f.autotune(prior, y, mask, p.sigma_obs, p.eps, p.obs_op, seed=p.seed, out=out)
+        box = [tuning]
+        dist.broadcast_object_list(box, src=0)
+        tuning = box[0]
+        keep = ("gram_tile_n", "gram_stages", "gram_k_block", "gram_splits", "wx_tile_n", "gram_cta_pair",
+                "gram_noise_warps", "gram_fp32_particles", "noise_inline", "pdl")
+        be.f.set_tuning(p.n, dl, **{k: v for k, v in tuning.items() if k in keep})
+    args.tuning = tuning
+    try:
+        store = dist.distributed_c10d._get_default_store()
+    except Exception:
+        store = None
+    ex = sharded.TorchExchange(store=store, heartbeat_timeout_s=120.0)
+    run = sharded.ShardedAnalysis(be, ex)
+    S_all = [None] * world
+    dist.all_gather_object(S_all, run.S)
+    if len(set(S_all)) != 1:
+        raise RuntimeError(f"ranks disagree on the split count: {S_all}")
+    stream = torch.cuda.current_stream()
+
+    def analyse(pr, yy, mm, k_seed):
+        return run.run(pr, yy, mm, p.sigma_obs, p.K, p.eps, c0, obs_op=p.obs_op, seed=p.seed + k_seed, out=out)
+
+    for w in range(args.warmup):
+        analyse(prior, y, mask, w)
+    torch.cuda.synchronize()
+    # end-to-end: this rank's slice copied in from page-locked host memory and its result copied out
+    sl = types.SimpleNamespace(prior=np.ascontiguousarray(p.prior[:, c0:c0 + dl]),
+                               y=np.ascontiguousarray(p.y[c0:c0 + dl]),
+                               mask=None if p.mask is None else np.ascontiguousarray(p.mask[c0:c0 + dl]))
+    h_prior, h_y, h_mask, h_out, host_huge = _host_buffers(ensf, sl, args.small_pages)
+    d_prior, d_y = torch.empty_like(prior), torch.empty_like(y)
+    d_mask = torch.empty_like(mask) if mask is not None else None
+    e2e_steps = max(1, min(args.steps, 3))
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def e2e_step(s_):
+        ee[s_][0].record(stream)
+        ensf.copy_sm(d_prior, h_prior, 152)
+        d_y.copy_(h_y, non_blocking=True)
+        if d_mask is not None:
+            d_mask.copy_(h_mask, non_blocking=True)
+        res = analyse(d_prior, d_y, d_mask, 200 + s_)
+        ensf.copy_sm(h_out, res, 152)
+        ee[s_][1].record(stream)
+        torch.cuda.synchronize()
+
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for s_ in range(args.steps):
+            ev[s_][0].record(stream)
+            analyse(prior, y, mask, 100 + s_)
+            ev[s_][1].record(stream)
+            if s_ < e2e_steps:
+                e2e_step(s_)
+        torch.cuda.synchronize()
+    dist.barrier()
+    step_each = [a.elapsed_time(b) for a, b in ev]
+    ms = float(sum(step_each))
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in ee)) / e2e_steps
+    if be.f.status_sync() != 0:
+        raise RuntimeError("device error during the benchmark")
+    be.f.profile_enable(True)
+    for s_ in range(args.steps):
+        analyse(prior, y, mask, 100 + s_)
+    torch.cuda.synchronize()
+    prof = be.f.profile_read()
+    be.f.profile_enable(False)
+    # accuracy: ensemble-mean RMSE over all columns, from every slice's squared errors
+    acc = analyse(prior, y, mask, 0).clone()
+    truth_dev = torch.from_numpy(np.ascontiguousarray(p.truth[c0:c0 + dl]).astype(np.float32)).to(dev)
+    _, rmse_slice = ensf.ensemble_stats(acc, truth_dev)
+    sq = torch.tensor([float(rmse_slice.item()) ** 2 * dl], dtype=torch.float64, device=dev)
+    dist.all_reduce(sq)
+    # the stored FP64 oracle rows of the large workload: each rank contributes its columns
+    golden = os.path.join(ROOT, "tests", "golden", "large512_subsample64.npz")
+    sub_parts = None
+    if p.name == "large-512" and os.path.exists(golden):
+        g = np.load(golden)
+        idx = g["idx"]
+        mine = (idx >= c0) & (idx < c0 + dl)
+        rows = torch.from_numpy(g["rows"].astype(np.int64)).to(dev)
+        vals = acc[rows][:, torch.from_numpy(idx[mine] - c0).to(dev)].cpu().numpy().astype(np.float64)
+        sub_parts = [None] * world
+        dist.all_gather_object(sub_parts, (np.flatnonzero(mine), vals))
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, dev)
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    ms_per_step = ms / args.steps
+    member_steps = p.n * p.K
+    accuracy = {"analysis_rmse": float(np.sqrt(sq.item() / p.d))}
+    if sub_parts is not None:
+        vals = np.zeros((len(g["rows"]), len(g["idx"])))
+        for pos, v in sub_parts:
+            vals[:, pos] = v
+        ref_vals = g["values"]
+        rel = np.linalg.norm(vals - ref_vals, axis=1) / np.linalg.norm(ref_vals, axis=1)
+        accuracy["oracle_subsample"] = {"members": int(len(g["rows"])), "entries": int(len(g["idx"])),
+                                        "member_rel_err": {"median": float(np.median(rel)),
+                                                           "max": float(rel.max())}}
+    kernels = {k: v for k, v in prof.items() if v[1] > 0}
+    peaks = _peaks()
+    pl = types.SimpleNamespace(n=p.n, d=dl, name=p.name + f"-slice{world}")
+    rooflines = {k: _roofline(k, kernels[k], pl, gram, wx, args, peaks) for k in ("gram", "wx_em") if k in kernels}
+    for r_ in rooflines.values():
+        r_["traffic"] = None  # no capture of the per-slice shapes
+    dom = max(kernels, key=lambda k: kernels[k][2])
+    line = {"metric": METRIC, "value": member_steps / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "ms_each_step": {"median": float(np.median(step_each)), "min": float(min(step_each)),
+                             "max": float(max(step_each))},
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": {"split-bf16": "bf16x3+bf16 (fp32 acc)", "split": "bf16x3 (fp32 acc)",
+                      "fp32": "f32"}.get(args.path, args.path),
+            "data": "synthetic",
+            "config": dict(_config(p, args.path, world),
+                           parallelism=f"one filter, d split over {world} GPUs ({dl} columns each), "
+                                       f"Gram partials all-gathered over NCCL per step"),
+            "roofline": rooflines.get(dom) or _roofline(dom, kernels[dom], pl, gram, wx, args, peaks),
+            "roofline_other": {k: v for k, v in rooflines.items() if k != dom},
+            "accuracy": accuracy,
+            "kernels": {k: {"launches": v[0], "avg_ms": (v[2] / v[1]) if v[1] else None} for k, v in prof.items()},
+            "e2e": {"value": member_steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": p.prior.nbytes + p.y.nbytes + (p.mask.nbytes if p.mask is not None else 0),
+                    "d2h_bytes_per_step": p.n * p.d * 4, "host_buffers": host_huge},
+            "gpu_launches": int(sum(v[0] for v in prof.values())) * world,
+            "clocks": clk.summary(), "tuning": tuning, "split_k_per_rank": run.S}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"], _ = cpu_baseline(p, args.cpu_budget_s)
+    print(json.dumps(line))
+    dist.destroy_process_group()
     return 0
 
 
@@ -645,6 +886,13 @@ def main(argv=None):
                     help="fp32 path, N <= 128: all K steps in one cooperative launch")
     ap.add_argument("--minibatch", type=int, default=0, metavar="J",
                     help="mini-batch prior score over J members per Euler-Maruyama step (tensor-core paths)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs: one independent filter per GPU (weak scaling) instead of one "
+                         "filter split along d over the GPUs")
+    ap.add_argument("--sharded", action="store_true",
+                    help="the d-sharded mode also on one GPU (under torchrun: exercises the NCCL exchange)")
+    ap.add_argument("--small-pages", action="store_true",
+                    help="end-to-end host buffers pinned without huge pages (for comparison)")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     args = ap.parse_args(argv)
@@ -653,7 +901,14 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    return run_batched(args) if args.workload == "batched-uneven" else run_ours(args)
+    if args.workload == "batched-uneven":
+        return run_batched(args)
+    if (_dist_env()[2] > 1 and not args.replicas) or args.sharded:
+        # the communicator's rank count appears in NCCL's own init lines
+        os.environ.setdefault("NCCL_DEBUG", "INFO")
+        os.environ.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
+        return run_sharded(args)
+    return run_ours(args)
 
 
 if __name__ == "__main__":

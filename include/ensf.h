@@ -485,6 +485,37 @@ ensf_status ensf_unet_train_step(ensf_unet *u, const float *x, const float *targ
 ensf_status ensf_unet_get_moments(ensf_unet *u, float *m, float *v, int64_t *step, void *stream);
 ensf_status ensf_unet_destroy(ensf_unet *u);
 
+/* ---- Page-locked host buffers for the copies of inputs and results -------
+ * The analysis's inputs (the forecast ensemble, observations) and its result
+ * move between host and device once per analysis.  On a GPU coupled to its
+ * host CPU by a coherent link the copy engines reach host memory through
+ * address translation; measured on GB300, a 2 GiB buffer pinned page by page
+ * (64 KiB pages) was copied at 35-70 GB/s right after an analysis, against
+ * about 200 GB/s from a buffer made of huge pages.  ensf_host_alloc returns
+ * `bytes` (rounded up to whole huge pages) of page-locked host memory, an
+ * anonymous mapping aligned to the transparent-huge-page size and advised and
+ * collapsed into huge pages before registration with the CUDA driver (each
+ * best effort: where the kernel offers no huge pages the buffer is still
+ * page-locked).  flags: 0, or ENSF_HOST_SMALL_PAGES to skip the huge-page
+ * advice (for comparisons).  The memory is zeroed.  Release with
+ * ensf_host_free.  ENSF_EINVAL (bytes 0, out NULL), ENSF_ENOMEM (mmap),
+ * ENSF_ECUDA (registration). */
+#define ENSF_HOST_SMALL_PAGES 1u
+ensf_status ensf_host_alloc(size_t bytes, unsigned flags, void **out);
+/* Unregister and unmap a buffer of ensf_host_alloc (NULL: no-op). */
+ensf_status ensf_host_free(void *ptr);
+/* dst <- src (bytes, a multiple of 16; both 16-byte aligned) copied by a
+ * kernel of `blocks` blocks on `stream` instead of a copy engine: either side
+ * may be device memory or page-locked host memory, which the SMs then read or
+ * write over the host link. */
+ensf_status ensf_copy_sm(void *dst, const void *src, size_t bytes, int blocks, void *stream);
+/* *registered = 1 if ptr lies in host memory page-locked with the CUDA driver
+ * (cudaHostRegister or cudaHostAlloc), else 0. */
+ensf_status ensf_host_registered(const void *ptr, int *registered);
+/* Share of [ptr, ptr + bytes) that the kernel backs with huge pages right
+ * now (from /proc/self/smaps; ENSF_EUNSUPPORTED where that is unreadable). */
+ensf_status ensf_host_huge_fraction(const void *ptr, size_t bytes, double *fraction);
+
 /* Wait for `stream` and return the handle's recorded device error, clearing it. */
 ensf_status ensf_status_sync(ensf_handle *h, void *stream);
 

@@ -75,16 +75,11 @@ class TorchExchange:
         self.analysis = 0
 
     def all_reduce_sum(self, t):
-        if self.world > 1:
-            self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
 
     def all_gather(self, gathered, local):
         """gathered [world * m ...] <- every rank's `local` [m ...] in rank order
-        (`local` may be this rank's own slot of `gathered`)."""
-        if self.world == 1:
-            if local.data_ptr() != gathered.data_ptr():
-                gathered.copy_(local)
-            return
+        (`local` may be this rank's own slot of `gathered`: NCCL gathers in place)."""
         if self.dist.get_backend(self.group) == "nccl":
             self.dist.all_gather_into_tensor(gathered, local, group=self.group)
         else:

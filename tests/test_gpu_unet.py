@@ -98,11 +98,26 @@ def test_adamw_step_matches_oracle():
         v_gpu = v_gpu.cpu().numpy().astype(np.float64)
         assert nsteps == step
         w_ref, m_ref, v_ref = uo.adamw_step(w_prev, grad, m_prev, v_prev, step, lr, wd)
-        np.testing.assert_allclose(m_gpu, m_ref, rtol=1e-5, atol=1e-30)
-        np.testing.assert_allclose(v_gpu, v_ref, rtol=1e-5, atol=1e-30)
+        # 1e-5 relative, plus the rounding of the kernel's own FP32 sums: where
+        # beta1 m + (1 - beta1) g nearly cancels, a few units in the last place
+        # of its two terms exceed 1e-5 of the small result
+        m_round = 4 * u32 * (0.9 * np.abs(m_prev) + 0.1 * np.abs(grad))
+        v_round = 4 * u32 * (0.999 * v_prev + 0.001 * grad * grad)
+        for name, got, want, rnd in (("m", m_gpu, m_ref, m_round), ("v", v_gpu, v_ref, v_round)):
+            err = np.abs(got - want)
+            bnd = 1e-5 * np.abs(want) + rnd
+            worst = int(np.argmax(err - bnd))
+            assert np.all(err <= bnd), (step, name, worst, got[worst], want[worst])
+        c1, c2 = 1.0 - 0.9 ** step, 1.0 - 0.999 ** step
+        dw = w_ref - w_prev
+        # the update to 1e-5, beyond what the moment rounding above and the
+        # FP32 evaluation of the update and of w itself carry
+        m_part = lr * (m_round / c1) / (np.sqrt(v_ref / c2) + 1e-8)
+        bound = 1e-5 * np.abs(dw) + 8 * u32 * np.abs(dw) + 2 * u32 * np.abs(w_ref) + m_part
         upd_err = np.abs(w_gpu - w_ref)
-        bound = 1e-5 * np.abs(w_ref - w_prev) + 2 * u32 * np.abs(w_ref)
         worst = int(np.argmax(upd_err - bound))
         assert np.all(upd_err <= bound), (step, worst, w_prev[worst], w_gpu[worst], w_ref[worst])
+        # and the bound is tight: most updates agree far below it
+        assert np.median(upd_err / np.maximum(np.abs(dw), 1e-30)) < 1e-5
         # continue from the GPU's own FP32 state, as the next kernel step does
         w_prev, m_prev, v_prev = w_gpu, m_gpu, v_gpu
