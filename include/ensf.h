@@ -74,6 +74,10 @@ typedef enum {
                                       the instantiated graph is kept in the handle and updated in
                                       place when only scalars or pointers change.  Ignored on the
                                       legacy default stream and inside a caller's own capture. */
+#define ENSF_FLAG_WX_UNSTAGED 16u  /* tensor-core BF16 W X with the noise evaluated in its epilogue:
+                                      use the epilogue that reads and writes the particles with
+                                      per-thread global accesses instead of the TMA-staged one (the
+                                      same arithmetic and results; kept for comparison) */
 #define ENSF_FLAG_PERSISTENT 8u    /* FP32 precisions and n <= 128: the K Euler-Maruyama steps run in
                                       one cooperative launch (one block per SM, three bounded grid
                                       barriers per step) instead of three launches per step; for

@@ -508,6 +508,7 @@ ensf::TcWxArgs wx_args(ensf_handle *h, int n, int64_t d, const float *y, const u
     a.coef = c;
     a.err = h->err();
     a.pdl = h->use_pdl(n, d);
+    a.staged = !(h->cfg.flags & ENSF_FLAG_WX_UNSTAGED);
     return a;
 }
 

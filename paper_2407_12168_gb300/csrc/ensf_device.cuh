@@ -73,21 +73,24 @@ __device__ __forceinline__ float4 noise4(uint64_t seed, uint32_t offset, int k, 
 }
 
 // Likelihood score term mask * H'(z) (y - H(z)) / sigma_obs^2 (Eq. 5).
+// Every rounding is spelled out (no contraction left to the compiler), so
+// all kernels that share these functions compute bit-identical particles.
 __device__ __forceinline__ float lik_score(int op, float z, float y, float inv_r) {
     if (op == 1) {
-        float dh = 1.0f / (1.0f + z * z);
-        return dh * (y - atanf(z)) * inv_r;
+        const float dh = __fdiv_rn(1.0f, __fmaf_rn(z, z, 1.0f));
+        return __fmul_rn(__fmul_rn(dh, __fsub_rn(y, atanf(z))), inv_r);
     }
-    return (y - z) * inv_r;
+    return __fmul_rn(__fsub_rn(y, z), inv_r);
 }
 
 // One Euler-Maruyama step of the reverse-time SDE (Eq. 7) with the posterior
 // score of Eq. 17, given u = sum_j w_ij x_j (the weighted forecast mean),
 // g = the likelihood score (0 where unobserved) and the noise draw xi.
 __device__ __forceinline__ float em_update(const StepCoef &c, float z, float u, float g, float xi) {
-    float s_prior = -(z - c.alpha * u) * c.inv_beta2;   // Eq. 15 with sum_j w_ij = 1
-    float s = s_prior + c.h * g;                       // Eq. 17
-    return z - c.dt * (c.b * z - c.sigma2 * s) + c.noise_scale * xi;
+    const float s_prior = __fmul_rn(__fmaf_rn(c.alpha, u, -z), c.inv_beta2);  // -(z - alpha u) / beta^2, Eq. 15
+    const float s = __fmaf_rn(c.h, g, s_prior);                                // Eq. 17
+    const float drift = __fmaf_rn(c.b, z, -__fmul_rn(c.sigma2, s));            // b z - sigma^2 s
+    return __fmaf_rn(c.noise_scale, xi, __fmaf_rn(-c.dt, drift, z));          // Eq. 7
 }
 
 
@@ -114,12 +117,49 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float v) {
     lo = __fadd_rn(lo, err);
 }
 
+// Double-float arithmetic: a value carried as an unevaluated FP32 sum hi + lo
+// (about 48 significant bits; Dekker 1971, Knuth's TwoSum).  The _rn
+// intrinsics keep the compiler from contracting or reordering the steps.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_norm(float hi, float lo) {  // |hi| >= |lo| not required
+    const float s = __fadd_rn(hi, lo);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(lo, bb));
+    return DF{s, err};
+}
+
+// a + b (TwoSum of the high parts, low parts added to the error term)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = df_norm(a.hi, b.hi);
+    return df_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+// a * b (exact product of the high parts by FMA, cross terms added)
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_norm(p, e);
+}
+
+// A double input (the FP64 norms, the host's coefficients) split into two
+// floats as it is read; everything after this runs in FP32.
+__device__ __forceinline__ DF df_from(double v) {
+    const float h = __double2float_rn(v);
+    return DF{h, __double2float_rn(v - static_cast<double>(h))};
+}
+
 // sum_{s0 <= s < s1} p[s * stride], ascending s, as a compensated FP32 sum
-// returned in FP64 (error of order s1 - s0 squared times 2^-48 relative to
-// sum |p|; FP64 units are few on this part, FP32 ones are not).  The loads
-// go out eight at a time, also for a short tail: the partials sit in L2 and
-// each load waits on it.
-__device__ __forceinline__ double sum_partials(const float *__restrict__ p, int64_t stride, int s0, int s1) {
+// (error of order (s1 - s0)^2 2^-48 relative to sum |p|; FP64 units are few
+// on this part, FP32 ones are not).  The loads go out eight at a time, also
+// for a short tail: the partials sit in L2 and each load waits on it.
+__device__ __forceinline__ DF sum_partials(const float *__restrict__ p, int64_t stride, int s0, int s1) {
     float hi = 0.f, lo = 0.f;
     for (int s = s0; s < s1; s += 8) {
         float v[8];
@@ -129,14 +169,32 @@ __device__ __forceinline__ double sum_partials(const float *__restrict__ p, int6
         for (int q = 0; q < 8; ++q)
             if (s + q < s1) df_add(hi, lo, v[q]);
     }
-    return (double)hi + (double)lo;
+    return df_norm(hi, lo);
+}
+
+// Log-kernel of Eq. 12 in its expanded form, l = (2 alpha G - alpha^2 |x|^2) / (2 beta^2)
+// (the row constant -|z|^2 / (2 beta^2) cancels in the softmax), in double-float.
+struct LogitCoef {
+    DF two_alpha, alpha_sq, inv_2beta2;
+};
+
+__device__ __forceinline__ LogitCoef logit_coef(double alpha, double inv_2beta2) {
+    const DF a = df_from(alpha);
+    return LogitCoef{DF{2.f * a.hi, 2.f * a.lo}, df_mul(a, a), df_from(inv_2beta2)};
+}
+
+__device__ __forceinline__ DF logit(const LogitCoef &k, DF g, double norm) {
+    const DF t = df_add(df_mul(k.two_alpha, g), df_neg(df_mul(k.alpha_sq, df_from(norm))));
+    return df_mul(t, k.inv_2beta2);
 }
 
 // One row i of the softmax of Eq. 16 from split-K partial Grams (read through
 // L2 only: they may come from other blocks of the same launch; block of NT
-// threads; lg = n_x doubles of shared memory, red = NT doubles):
+// threads; lg = n_x doubles of shared memory, red = NT doubles, both used as
+// pairs of floats):
 //   G_ij = sum_s partial[s][i][j]  (fixed order: deterministic),
-//   l_ij = (2 alpha G_ij - alpha^2 |x_j|^2) / (2 beta^2), w_ij = softmax_j(l_ij).
+//   l_ij = (2 alpha G_ij - alpha^2 |x_j|^2) / (2 beta^2), w_ij = softmax_j(l_ij),
+// all in FP32, the sums and the logits compensated (double-float).
 // Writes FP32 w and/or the BF16 split w = w_hi + w_lo.  When the row is short,
 // `groups` threads share a column j, each summing a fixed range of splits
 // (the group sums are then added in group order: deterministic).
@@ -146,18 +204,21 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
                                             const double *__restrict__ norms, double alpha,
                                             double inv_2beta2, float *__restrict__ w, int ldw,
                                             __nv_bfloat16 *__restrict__ w_hi,
-                                            __nv_bfloat16 *__restrict__ w_lo, int ldwb, double *lg,
-                                            double *red) {
+                                            __nv_bfloat16 *__restrict__ w_lo, int ldwb, double *lg_raw,
+                                            double *red_raw) {
+    DF *lg = reinterpret_cast<DF *>(lg_raw);
+    DF *red = reinterpret_cast<DF *>(red_raw);
+    float *redf = reinterpret_cast<float *>(red_raw);
     const int tid = threadIdx.x;
+    const LogitCoef kc = logit_coef(alpha, inv_2beta2);
     const int groups = n_x >= NT ? 1 : min(NT / n_x, splits);
     const int per = (splits + groups - 1) / groups;
-    double lmax = -DBL_MAX;
+    float lmax = -FLT_MAX;
     if (groups == 1) {
         for (int j = tid; j < n_x; j += NT) {
-            const double g = sum_partials(partial + (int64_t)i * ldp + j, part_stride, 0, splits);
-            double l = (2.0 * alpha * g - alpha * alpha * norms[j]) * inv_2beta2;
+            const DF l = logit(kc, sum_partials(partial + (int64_t)i * ldp + j, part_stride, 0, splits), norms[j]);
             lg[j] = l;
-            lmax = fmax(lmax, l);
+            lmax = fmaxf(lmax, l.hi);
         }
     } else {
         const int j = tid % n_x, grp = tid / n_x;
@@ -167,37 +228,39 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
         }
         __syncthreads();
         if (tid < n_x) {
-            double g = 0.0;
-            for (int q = 0; q < groups; ++q) g += red[q * n_x + tid];
-            double l = (2.0 * alpha * g - alpha * alpha * norms[tid]) * inv_2beta2;
+            DF g = red[tid];
+            for (int q = 1; q < groups; ++q) g = df_add(g, red[q * n_x + tid]);
+            const DF l = logit(kc, g, norms[tid]);
             lg[tid] = l;
-            lmax = l;
+            lmax = l.hi;
         }
         __syncthreads();
     }
-    red[tid] = lmax;
+    redf[tid] = lmax;
     __syncthreads();
     for (int s = NT / 2; s > 0; s >>= 1) {
-        if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
+        if (tid < s) redf[tid] = fmaxf(redf[tid], redf[tid + s]);
         __syncthreads();
     }
-    const double m = red[0];
+    const float m = redf[0];
     __syncthreads();
-    double sum = 0.0;
+    float sh = 0.f, sl = 0.f;
     for (int j = tid; j < n_x; j += NT) {
-        double e = (double)expf((float)(lg[j] - m));
-        lg[j] = e;
-        sum += e;
+        const DF l = lg[j];
+        const DF dl = df_norm(__fsub_rn(l.hi, m), l.lo);  // l.hi - m is exact where it matters (near the max)
+        const float e = expf(__fadd_rn(dl.hi, dl.lo));
+        lg[j].hi = e;
+        df_add(sh, sl, e);
     }
-    red[tid] = sum;
+    red[tid] = df_norm(sh, sl);
     __syncthreads();
     for (int s = NT / 2; s > 0; s >>= 1) {
-        if (tid < s) red[tid] += red[tid + s];
+        if (tid < s) red[tid] = df_add(red[tid], red[tid + s]);
         __syncthreads();
     }
-    const double inv = 1.0 / red[0];
+    const float inv = __frcp_rn(__fadd_rn(red[0].hi, red[0].lo));
     for (int j = tid; j < n_x; j += NT) {
-        float wv = (float)(lg[j] * inv);
+        const float wv = __fmul_rn(lg[j].hi, inv);
         if (w) w[(int64_t)i * ldw + j] = wv;
         if (w_hi) {
             __nv_bfloat16 hi = __float2bfloat16_rn(wv);

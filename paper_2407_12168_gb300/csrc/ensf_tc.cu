@@ -1229,6 +1229,263 @@ k_wx_em_tc(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CU
     }
 }
 
+// ------------------------------------------- W X + EM, TMA-staged epilogue
+// The persistent tile loop of k_wx_em_tc (tiles of U^T = X^T W^T: 128 state
+// columns x BN particles, two TMEM accumulators), with the particle state
+// moved through shared memory by TMA instead of per-thread global accesses.
+// The four epilogue warps that share a quarter of the tile's particles work
+// in chunks of 16 particles x 128 state columns: one thread of the four warps
+// loads the chunk of z (FP32) into a staging buffer with TMA (the next chunk's
+// load overlaps this chunk's arithmetic), each thread updates its column of
+// the chunk in place and writes the BF16 planes of the next Gram beside it,
+// and the same thread stores the chunk back with TMA.  The step's noise is
+// evaluated in the epilogue from the counter-based stream.  Per element an
+// epilogue thread thus issues three or four shared-memory accesses at fixed
+// offsets and no address arithmetic, which leaves the issue slots the noise
+// needs.  The arithmetic is that of k_wx_em_tc (bitwise).
+constexpr int kStgRows = 16;    // particles per staged chunk
+constexpr int kStgCols = BM;    // state columns per staged chunk (the tile's MMA rows)
+
+template <int BN, int STAGES>
+struct WxStagedPlan {
+    static constexpr int kA = BM * BK * 2;  // X^T rows (state columns)
+    static constexpr int kB = BN * BK * 2;  // W rows (particles)
+    static constexpr int kStage = kA + kB;
+    static constexpr int kStgZ = kStgRows * kStgCols * 4;   // FP32 z chunk
+    static constexpr int kStgH = kStgRows * kStgCols * 2;   // one BF16 plane chunk
+    static constexpr int kStgBuf = kStgZ + 2 * kStgH;
+    static constexpr int kStgOff = kStage * STAGES;
+    static constexpr int kBarOff = kStgOff + 4 * 2 * kStgBuf;  // four particle quarters, double-buffered
+    static constexpr int kBytes = kBarOff + 512 + 1024;
+    static_assert(kBytes <= 227 * 1024, "shared memory plan too large");
+    static_assert(BN == 64 || BN == 128 || BN == 256, "BN");
+};
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kWxThreads, 1)
+k_wx_em_staged(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CUtensorMap w_hi,
+               const __grid_constant__ CUtensorMap z_map, const __grid_constant__ CUtensorMap zh_map,
+               const __grid_constant__ CUtensorMap zl_map, WxParams p) {
+    pdl_wait();  // reads the weights of the row softmax
+    pdl_launch_dependents();
+    using P = WxStagedPlan<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*reinterpret_cast<volatile int *>(p.err) != 0) return;  // an earlier launch failed: skip
+
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    uint8_t *tiles = smem_raw + pad;
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;   // [2] accumulator ready
+    uint64_t *tempty = tfull + 2;       // [2] accumulator drained
+    uint64_t *zfull = tempty + 2;       // [4 quarters][2 buffers] staged z chunk landed
+    uint64_t *zdone = zfull + 8;        // [4 quarters][2 buffers] chunk updated by its 128 threads
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(zdone + 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], kEpiWarps);
+        }
+        for (int b = 0; b < 8; ++b) {
+            mbar_init(&zfull[b], 1);
+            mbar_init(&zdone[b], 128);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kWxTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int total = p.m_tiles * p.n_tiles;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0, issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int m0 = (t / p.n_tiles) * BM, n0 = (t % p.n_tiles) * BN;
+                for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) { ok = false; break; }
+                    const uint32_t st = smem_u32(tiles + s * P::kStage);
+                    mbar_expect_tx(&full[s], P::kStage);
+                    tma_load_2d(st, &xt_hi, &full[s], kb * BK, m0);
+                    tma_load_2d(st + P::kA, &w_hi, &full[s], kb * BK, n0);
+                    issued = it + 1;
+                }
+            }
+            if (*abort_flag) {
+                const uint64_t t0 = globaltimer();
+                for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i) {
+                    const int s = i % STAGES;
+                    while (!mbar_try_wait(&full[s], (i / STAGES) & 1) && globaltimer() - t0 < kTimeoutNs) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int it = 0, lt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++lt) {
+                const int slot = lt & 1;
+                const uint32_t use = lt >> 1;
+                if (!mbar_wait(&tempty[slot], (use & 1u) ^ 1u, abort_flag, p.err)) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + slot * 256;
+                for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(tiles + s * P::kStage);
+                    const uint32_t b = a + P::kA;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(acc, desc_sw128(a + kk * 32), desc_sw128(b + kk * 32), idesc,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[slot]);
+            }
+        }
+    } else {
+        const int ew = warp - 2;            // 0 .. kEpiWarps-1
+        const int q = warp & 3;             // TMEM lane quarter this warp may read
+        const int part = ew >> 2;           // which quarter of the BN particle columns
+        const bool leader = (ew & 3) == 0 && lane == 0;
+        constexpr int kCols = BN / 4;       // particle columns per quarter
+        constexpr int kChunks = kCols / kStgRows;
+        const int cl = q * 32 + lane;       // this thread's state column within the tile
+        const StepCoef &cf = p.coef;
+        uint8_t *stg = tiles + P::kStgOff + part * 2 * P::kStgBuf;
+        uint64_t *zf = zfull + part * 2;
+        uint64_t *zd = zdone + part * 2;
+        const bool planes = p.zb_hi != nullptr;
+        const bool lo_plane = p.zb_lo != nullptr;
+        // the chunk sequence of this quarter runs across the tiles of this CTA
+        auto chunk_origin = [&](int g, int &x, int &y) {
+            const int t = blockIdx.x + (g / kChunks) * gridDim.x;
+            x = (t / p.n_tiles) * BM;
+            y = (t % p.n_tiles) * BN + part * kCols + (g % kChunks) * kStgRows;
+        };
+        auto issue_load = [&](int g) {
+            int x, y;
+            chunk_origin(g, x, y);
+            uint64_t *bar = &zf[g & 1];
+            mbar_expect_tx(bar, P::kStgZ);
+            tma_load_2d(smem_u32(stg + (g & 1) * P::kStgBuf), &z_map, bar, x, y);
+        };
+        const int my_tiles = blockIdx.x < total ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        const int n_chunks = my_tiles * kChunks;
+        if (leader && n_chunks > 0) issue_load(0);
+        int g = 0, lt = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++lt) {
+            const int slot = lt & 1;
+            const uint32_t use = lt >> 1;
+            const int m0 = (t / p.n_tiles) * BM, n0 = (t % p.n_tiles) * BN;
+            // every wait's outcome is made warp-uniform: the TMEM loads are warp-collective
+            if (!__all_sync(0xffffffffu, mbar_wait(&tfull[slot], use & 1u, abort_flag, p.err))) break;
+            tc_fence_after();
+            const int64_t c = static_cast<int64_t>(m0) + cl;  // this thread's state column
+            const bool cok = c < p.d;
+            const float yc = cok ? p.y[c] : 0.f;
+            const bool obs = cok && (p.mask == nullptr || p.mask[c] != 0);
+            const float shift = (cok && p.centre) ? __fmul_rn(p.alpha_next, p.centre[c]) : 0.f;
+#pragma unroll 1
+            for (int ch = 0; ch < kChunks; ++ch, ++g) {
+                const int buf = g & 1;
+                if (leader && g + 1 < n_chunks) {
+                    bulk_wait_read_all();  // the store of chunk g - 1 has left that buffer
+                    issue_load(g + 1);
+                }
+                const int cc = part * kCols + ch * kStgRows;  // accumulator column = particle within tile
+                float u[16];
+                tmem_ld16(tmem + slot * 256 + (static_cast<uint32_t>(q * 32) << 16) + cc, u);
+                if (!__all_sync(0xffffffffu, mbar_wait(&zf[buf], (g >> 1) & 1u, abort_flag, p.err))) {
+                    ok = false;
+                    break;
+                }
+                float *zs = reinterpret_cast<float *>(stg + buf * P::kStgBuf);
+                __nv_bfloat16 *hs = reinterpret_cast<__nv_bfloat16 *>(stg + buf * P::kStgBuf + P::kStgZ);
+                __nv_bfloat16 *ls = hs + kStgRows * kStgCols;
+                const int i0 = n0 + cc;
+                float xi[16];
+#pragma unroll
+                for (int e4 = 0; e4 < 4; ++e4) {
+                    const float4 v = noise4(p.seed, p.offset, cf.k + 1, c + cf.col0, (i0 >> 2) + e4);
+                    xi[e4 * 4 + 0] = v.x;
+                    xi[e4 * 4 + 1] = v.y;
+                    xi[e4 * 4 + 2] = v.z;
+                    xi[e4 * 4 + 3] = v.w;
+                }
+#pragma unroll
+                for (int e = 0; e < kStgRows; ++e) {
+                    const float zv = zs[e * kStgCols + cl];
+                    const float gl = obs ? lik_score(cf.obs_op, zv, yc, cf.inv_r) : 0.f;
+                    const float zn = em_update(cf, zv, u[e], gl, xi[e]);
+                    zs[e * kStgCols + cl] = zn;
+                    if (planes) {
+                        const float zc = __fsub_rn(zn, shift);  // rounded as the FP32-operand Gram rounds it
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
+                        hs[e * kStgCols + cl] = hi;
+                        if (lo_plane) ls[e * kStgCols + cl] = __float2bfloat16_rn(zc - __bfloat162float(hi));
+                    }
+                }
+                // the chunk's shared-memory writes, visible to the TMA store, then
+                // counted on the chunk's barrier; the leader alone waits (bounded)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&zd[buf]);
+                if (leader) {
+                    if (!mbar_wait(&zd[buf], (g >> 1) & 1u, abort_flag, p.err)) {
+                        ok = false;
+                    } else if (i0 < p.n) {  // (a chunk wholly past the last particle stores nothing)
+                        tma_store_2d(&z_map, smem_u32(zs), m0, i0);
+                        if (planes) tma_store_2d(&zh_map, smem_u32(hs), m0, i0);
+                        if (lo_plane) tma_store_2d(&zl_map, smem_u32(ls), m0, i0);
+                        bulk_commit();
+                    }
+                }
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[slot]);
+        }
+        if (leader) bulk_wait_all();  // the stores have read shared memory and landed
+        (void)ok;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kWxTmemCols);
+    }
+}
+
 // ================================================================ batched
 // Gram tile of one instance; maps / parameters / k-range from device tables.
 template <int BN, int STAGES, bool SPLIT>
@@ -1527,6 +1784,27 @@ cudaError_t make_map_f32(const TcContext *ctx, CUtensorMap *m, const float *base
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 2-D tensor map without swizzle for the staged W X epilogue: rows x cols of
+// `esize`-byte elements (cols contiguous, pitch = cols), box = kStgCols
+// columns x kStgRows rows, zero fill beyond the edges (loads) and clipping
+// (stores).
+cudaError_t make_map_stage(const TcContext *ctx, CUtensorMap *m, const void *base, int esize, int64_t cols,
+                           int64_t rows) {
+    if (!base) {
+        memset(m, 0, sizeof(*m));
+        return cudaSuccess;
+    }
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * esize};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kStgCols), static_cast<cuuint32_t>(kStgRows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = ctx->encode(m, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                             const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <class K>
 cudaError_t set_smem(K kernel, int bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1567,6 +1845,19 @@ cudaError_t run_wx(const CUtensorMap (&maps)[4], WxParams p, int sms, cudaStream
     const int total = p.m_tiles * p.n_tiles;
     const int grid = total < sms ? total : sms;
     return launch_k(kern, dim3(grid), dim3(kWxThreads), P::kBytes, s, p.pdl, maps[0], maps[1], maps[2], maps[3], p);
+}
+
+template <int BN, int STAGES>
+cudaError_t run_wx_staged(const CUtensorMap &xt, const CUtensorMap &w, const CUtensorMap (&stg)[3], WxParams p,
+                          int sms, cudaStream_t s) {
+    using P = WxStagedPlan<BN, STAGES>;
+    auto kern = k_wx_em_staged<BN, STAGES>;
+    cudaError_t e = set_smem(kern, P::kBytes);
+    if (e != cudaSuccess) return e;
+    p.n_tiles = (p.n + BN - 1) / BN;
+    const int total = p.m_tiles * p.n_tiles;
+    const int grid = total < sms ? total : sms;
+    return launch_k(kern, dim3(grid), dim3(kWxThreads), P::kBytes, s, p.pdl, xt, w, stg[0], stg[1], stg[2], p);
 }
 
 // Split count minimising (waves) x (k-blocks per split + epilogue cost), with
@@ -1798,6 +2089,16 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
     p.err = a.err;
     p.pdl = a.pdl;
     const bool inl = a.noise == nullptr;  // no slice: Philox in the epilogue
+    if (!split && inl && a.zc32 == nullptr && a.staged) {
+        // in-epilogue noise with BF16 W X: the TMA-staged epilogue
+        CUtensorMap stg[3];
+        if ((e = make_map_stage(ctx, &stg[0], a.z, 4, a.d, a.n)) != cudaSuccess) return e;
+        if ((e = make_map_stage(ctx, &stg[1], a.zb_hi, 2, a.d, a.n)) != cudaSuccess) return e;
+        if ((e = make_map_stage(ctx, &stg[2], a.zb_lo, 2, a.d, a.n)) != cudaSuccess) return e;
+        if (BN == 256) return run_wx_staged<256, 2>(maps[0], maps[2], stg, p, sms, s);
+        if (BN == 128) return run_wx_staged<128, 3>(maps[0], maps[2], stg, p, sms, s);
+        return run_wx_staged<64, 4>(maps[0], maps[2], stg, p, sms, s);
+    }
     if (split) {
         if (BN == 256) return inl ? run_wx<256, 2, true, true>(maps, p, sms, s) : run_wx<256, 2, true, false>(maps, p, sms, s);
         if (BN == 128) return inl ? run_wx<128, 3, true, true>(maps, p, sms, s) : run_wx<128, 3, true, false>(maps, p, sms, s);

@@ -77,6 +77,7 @@ struct TcWxArgs {
     float *z;                            // particles [n][d], updated in place
     __nv_bfloat16 *zb_hi, *zb_lo;        // split copies of the updated particles (NULL: skip)
     float *zc32 = nullptr;               // or the FP32 centred particles (TF32 Gram), NULL: skip
+    bool staged = true;                  // in-epilogue noise, BF16: the TMA-staged epilogue
     const float *y;
     const uint8_t *mask;
     const float *noise;                  // xi[k+1] as a [n][d] slice (pre-generated), or NULL:

@@ -23,6 +23,7 @@ FLAG_CHECK_FINITE = 1
 FLAG_CUDA_GRAPH = 2
 FLAG_PERSISTENT = 8
 FLAG_INLINE_NOISE = 4
+FLAG_WX_UNSTAGED = 16
 
 PREC_TF32 = 3
 PRECISIONS = {"fp32": PREC_FP32, "split": PREC_SPLIT_BF16X3, "bf16": PREC_BF16, "tf32": PREC_TF32}
@@ -233,12 +234,13 @@ class Filter:
 
     def __init__(self, max_n: int, max_d: int, gram: str = "fp32", wx: str = "fp32",
                  check_finite: bool = False, graph: bool = False, inline_noise: bool = False,
-                 persistent: bool = False):
+                 persistent: bool = False, wx_unstaged: bool = False):
         torch = _torch()
         lib = load()
         self.cfg = EnsfConfig(int(max_n), int(max_d), PRECISIONS[gram], PRECISIONS[wx],
                               (FLAG_CHECK_FINITE if check_finite else 0) | (FLAG_CUDA_GRAPH if graph else 0)
-                              | (FLAG_INLINE_NOISE if inline_noise else 0) | (FLAG_PERSISTENT if persistent else 0))
+                              | (FLAG_INLINE_NOISE if inline_noise else 0) | (FLAG_PERSISTENT if persistent else 0)
+                              | (FLAG_WX_UNSTAGED if wx_unstaged else 0))
         nbytes = lib.ensf_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise ValueError("invalid EnSF configuration")

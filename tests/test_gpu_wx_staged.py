@@ -1,0 +1,71 @@
+"""The TMA-staged W X epilogue (particles moved through shared memory by TMA,
+noise evaluated in the epilogue) against the epilogue that reads and writes
+the particles with per-thread global accesses: the same arithmetic, so whole
+analyses must agree bit for bit -- on ragged shapes (N not a multiple of the
+16-particle chunk or of the tile, d not a multiple of the 128-column tile),
+for every particle-plane layout the next Gram may need (BF16 hi + lo for
+the split Gram, hi only for the BF16 Gram, none for a CUDA-core Gram) and
+every W X tile width -- and match the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_2407_12168_gb300 import inputs
+
+from .parity_util import compare_members, conditioning, describe, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (seed, n, grid, layers, K, obs_op, obs_frac, sigma)
+    (71, 70, 44, 1, 6, 1, 0.6, 0.4),     # n: 4 chunks + a ragged 6; d = 1936: a ragged 128-column tile
+    (72, 256, 32, 2, 5, 0, 1.0, 0.6),    # whole 256-particle tiles
+    (73, 300, 20, 2, 4, 1, 0.5, 0.4),    # a second, ragged particle tile; d = 800
+    (74, 33, 64, 2, 5, 1, 0.25, 0.3),    # n = 33, d = 8192
+]
+
+
+def _run(p, gram, wx, unstaged, wx_tile=0):
+    import torch
+    from paper_2407_12168_gb300 import ensf
+    f = ensf.Filter(p.n, p.d, gram=gram, wx=wx, inline_noise=True, wx_unstaged=unstaged, check_finite=True)
+    if wx_tile and gram != "fp32":
+        f.set_tuning(p.n, p.d, 128 if p.n <= 128 else 256, 3 if p.n <= 128 else 2, wx_tile_n=wx_tile,
+                     noise_inline=1)
+    out = f.analysis(torch.from_numpy(p.prior).cuda(), torch.from_numpy(p.y).cuda(),
+                     None if p.mask is None else torch.from_numpy(p.mask).cuda(), p.sigma_obs, p.K, p.eps,
+                     p.obs_op, seed=p.seed, offset=p.offset)
+    assert f.status_sync() == 0
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("gram", ["split", "bf16", "fp32"])
+def test_staged_epilogue_is_bitwise_the_unstaged_one(case, gram):
+    seed, n, grid, layers, K, obs_op, frac, sigma = case
+    p = inputs.small_case(seed=seed, n=n, grid=grid, layers=layers, K=K, obs_op=obs_op, obs_frac=frac,
+                          sigma_obs=sigma)
+    a = _run(p, gram, "bf16", unstaged=False)
+    b = _run(p, gram, "bf16", unstaged=True)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("wx_tile", [64, 128, 256])
+def test_staged_epilogue_tile_widths(wx_tile):
+    p = inputs.small_case(seed=75, n=140, grid=36, layers=2, K=4, obs_op=1, obs_frac=0.5, sigma_obs=0.4)
+    a = _run(p, "split", "bf16", unstaged=False, wx_tile=wx_tile)
+    b = _run(p, "split", "bf16", unstaged=True, wx_tile=wx_tile)
+    assert np.array_equal(a, b)
+
+
+def test_staged_epilogue_matches_oracle():
+    p = inputs.small_case(seed=76, n=70, grid=44, layers=1, K=10, obs_op=1, obs_frac=0.6, sigma_obs=0.4)
+    ref = run_oracle(p)
+    got = _run(p, "split", "bf16", unstaged=False)
+    cond = conditioning(p, ref, prec="bf16")
+    rel, tie, bad = compare_members(got, ref, cond, 1e-2)
+    assert not bad.any(), describe(rel, tie, bad)
+    assert tie.sum() <= 1, describe(rel, tie, bad)
+    _, r_ref = o.mean_rmse(ref, p.truth)
+    _, r_got = o.mean_rmse(got, p.truth)
+    assert r_got == pytest.approx(r_ref, rel=1e-2)
