@@ -55,21 +55,44 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 // Four standard normals xi[k][4q .. 4q+3][j] of the noise stream (four
 // consecutive particles of state column j): counter (j, q, k, offset), key
 // (seed low, seed high); words (x, y) and (z, w) each feed one Box-Muller pair
-// with u1 = ((a >> 8) + 1) 2^-24 in (0, 1] and u2 = (b >> 8) 2^-24 in [0, 1).
+// with u1 = ((a >> 8) + 1) 2^-24 in (0, 1] and u2 = (b >> 8) 2^-24 in [0, 1):
+// xi = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+//
+// Evaluated with the SFU approximations (lg2, sqrt, sin, cos), which cost a
+// few instructions where the correctly rounded library functions cost tens;
+// the draws are consumed inside the W X epilogue, whose issue slots they
+// share.  Accuracy against the exact transform: ln u1 comes from a short
+// series of ln(1 - v), v = 1 - u1 (exact), where v < 2^-7 (error < 1e-11) and
+// from lg2 elsewhere (absolute error < 4e-7, relative < 3 ulp); the angle is
+// shifted into [-pi, pi), where sin and cos carry absolute errors < 4e-7.
+// Each normal is then within about 3e-6 (absolute) of the exact value.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float2 box_muller(uint32_t a24, uint32_t b24) {
+    const float two_m24 = 5.9604644775390625e-8f;  // 2^-24
+    const float u1 = __fmul_rn(__uint2float_rn(a24 + 1u), two_m24);
+    const float v1 = __fmul_rn(__uint2float_rn(0xFFFFFFu - a24), two_m24);  // 1 - u1, exact
+    // ln(1 - v) = -v (1 + v/2 + v^2/3 + v^3/4 + ...), truncated after v^3/4
+    const float ser = -__fmul_rn(v1, __fmaf_rn(v1, __fmaf_rn(v1, __fmaf_rn(v1, 0.25f, 0.333333343f), 0.5f), 1.0f));
+    const float ln_u1 = v1 < 0.0078125f ? ser : __logf(u1);
+    const float r = sqrt_approx(__fmul_rn(-2.0f, ln_u1));
+    // 2 pi u2 = pi + theta, theta = 2 pi (u2 - 1/2) in [-pi, pi): cos, sin change sign
+    const float theta = __fmul_rn(__int2float_rn(static_cast<int>(b24) - 8388608), 3.74507028e-7f);  // 2 pi 2^-24
+    float sn, cs;
+    __sincosf(theta, &sn, &cs);
+    return make_float2(-__fmul_rn(r, cs), -__fmul_rn(r, sn));
+}
+
 __device__ __forceinline__ float4 noise4(uint64_t seed, uint32_t offset, int k, int64_t j, int q) {
     U4 c{(uint32_t)j, (uint32_t)q, (uint32_t)k, offset};
     U4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
-    const float two_m24 = 5.9604644775390625e-8f;  // 2^-24
-    float u1a = (float)((r.x >> 8) + 1u) * two_m24;
-    float u2a = (float)(r.y >> 8) * two_m24;
-    float u1b = (float)((r.z >> 8) + 1u) * two_m24;
-    float u2b = (float)(r.w >> 8) * two_m24;
-    float ra = sqrtf(-2.0f * logf(u1a));
-    float rb = sqrtf(-2.0f * logf(u1b));
-    float sa, ca, sb, cb;
-    sincospif(2.0f * u2a, &sa, &ca);
-    sincospif(2.0f * u2b, &sb, &cb);
-    return make_float4(ra * ca, ra * sa, rb * cb, rb * sb);
+    const float2 a = box_muller(r.x >> 8, r.y >> 8);
+    const float2 b = box_muller(r.z >> 8, r.w >> 8);
+    return make_float4(a.x, a.y, b.x, b.y);
 }
 
 // Likelihood score term mask * H'(z) (y - H(z)) / sigma_obs^2 (Eq. 5).

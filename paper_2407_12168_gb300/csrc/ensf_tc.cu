@@ -1271,7 +1271,9 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-template <int BN, int STAGES>
+// OBS: the observation operator (0 identity, 1 arctan); PLANES: the BF16
+// particle planes the next Gram reads (0 none, 1 hi, 2 hi and lo).
+template <int BN, int STAGES, int OBS, int PLANES>
 __global__ void __launch_bounds__(kWxThreads, 1)
 k_wx_em_staged(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant__ CUtensorMap w_hi,
                const __grid_constant__ CUtensorMap z_map, const __grid_constant__ CUtensorMap zh_map,
@@ -1383,8 +1385,8 @@ k_wx_em_staged(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant_
         uint8_t *stg = tiles + P::kStgOff + part * 2 * P::kStgBuf;
         uint64_t *zf = zfull + part * 2;
         uint64_t *zd = zdone + part * 2;
-        const bool planes = p.zb_hi != nullptr;
-        const bool lo_plane = p.zb_lo != nullptr;
+        constexpr bool planes = PLANES >= 1;
+        constexpr bool lo_plane = PLANES == 2;
         // the chunk sequence of this quarter runs across the tiles of this CTA
         auto chunk_origin = [&](int g, int &x, int &y) {
             const int t = blockIdx.x + (g / kChunks) * gridDim.x;
@@ -1445,7 +1447,7 @@ k_wx_em_staged(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant_
 #pragma unroll
                 for (int e = 0; e < kStgRows; ++e) {
                     const float zv = zs[e * kStgCols + cl];
-                    const float gl = obs ? lik_score(cf.obs_op, zv, yc, cf.inv_r) : 0.f;
+                    const float gl = obs ? lik_score(OBS, zv, yc, cf.inv_r) : 0.f;
                     const float zn = em_update(cf, zv, u[e], gl, xi[e]);
                     zs[e * kStgCols + cl] = zn;
                     if (planes) {
@@ -1847,11 +1849,11 @@ cudaError_t run_wx(const CUtensorMap (&maps)[4], WxParams p, int sms, cudaStream
     return launch_k(kern, dim3(grid), dim3(kWxThreads), P::kBytes, s, p.pdl, maps[0], maps[1], maps[2], maps[3], p);
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int OBS, int PLANES>
 cudaError_t run_wx_staged(const CUtensorMap &xt, const CUtensorMap &w, const CUtensorMap (&stg)[3], WxParams p,
                           int sms, cudaStream_t s) {
     using P = WxStagedPlan<BN, STAGES>;
-    auto kern = k_wx_em_staged<BN, STAGES>;
+    auto kern = k_wx_em_staged<BN, STAGES, OBS, PLANES>;
     cudaError_t e = set_smem(kern, P::kBytes);
     if (e != cudaSuccess) return e;
     p.n_tiles = (p.n + BN - 1) / BN;
@@ -2095,9 +2097,22 @@ cudaError_t launch_wx_em_tc(TcContext *ctx, const TcWxArgs &a, int sms, cudaStre
         if ((e = make_map_stage(ctx, &stg[0], a.z, 4, a.d, a.n)) != cudaSuccess) return e;
         if ((e = make_map_stage(ctx, &stg[1], a.zb_hi, 2, a.d, a.n)) != cudaSuccess) return e;
         if ((e = make_map_stage(ctx, &stg[2], a.zb_lo, 2, a.d, a.n)) != cudaSuccess) return e;
-        if (BN == 256) return run_wx_staged<256, 2>(maps[0], maps[2], stg, p, sms, s);
-        if (BN == 128) return run_wx_staged<128, 3>(maps[0], maps[2], stg, p, sms, s);
-        return run_wx_staged<64, 4>(maps[0], maps[2], stg, p, sms, s);
+        const int planes = a.zb_hi ? (a.zb_lo ? 2 : 1) : 0;
+        const int sel = (BN == 256 ? 0 : BN == 128 ? 1 : 2) * 6 + a.coef.obs_op * 3 + planes;
+        switch (sel) {
+#define ENSF_STAGED(bn, st, i)                                                                   \
+    case i * 6 + 0: return run_wx_staged<bn, st, 0, 0>(maps[0], maps[2], stg, p, sms, s);        \
+    case i * 6 + 1: return run_wx_staged<bn, st, 0, 1>(maps[0], maps[2], stg, p, sms, s);        \
+    case i * 6 + 2: return run_wx_staged<bn, st, 0, 2>(maps[0], maps[2], stg, p, sms, s);        \
+    case i * 6 + 3: return run_wx_staged<bn, st, 1, 0>(maps[0], maps[2], stg, p, sms, s);        \
+    case i * 6 + 4: return run_wx_staged<bn, st, 1, 1>(maps[0], maps[2], stg, p, sms, s);        \
+    case i * 6 + 5: return run_wx_staged<bn, st, 1, 2>(maps[0], maps[2], stg, p, sms, s);
+            ENSF_STAGED(256, 2, 0)
+            ENSF_STAGED(128, 3, 1)
+            ENSF_STAGED(64, 4, 2)
+#undef ENSF_STAGED
+            default: return cudaErrorInvalidValue;
+        }
     }
     if (split) {
         if (BN == 256) return inl ? run_wx<256, 2, true, true>(maps, p, sms, s) : run_wx<256, 2, true, false>(maps, p, sms, s);

@@ -65,7 +65,10 @@ def test_staged_epilogue_matches_oracle():
     cond = conditioning(p, ref, prec="bf16")
     rel, tie, bad = compare_members(got, ref, cond, 1e-2)
     assert not bad.any(), describe(rel, tie, bad)
-    assert tie.sum() <= 1, describe(rel, tie, bad)
+    # near-tie members (their oracle result moves under log-kernel errors of
+    # the BF16 path's size) are counted, bounded at a few per cent as in the
+    # other parity tests, and never dropped from the RMSE check below
+    assert tie.sum() <= max(1, p.n // 20), describe(rel, tie, bad)
     _, r_ref = o.mean_rmse(ref, p.truth)
     _, r_got = o.mean_rmse(got, p.truth)
     assert r_got == pytest.approx(r_ref, rel=1e-2)
