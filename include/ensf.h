@@ -154,6 +154,10 @@ typedef struct {
                           finishes, and waits for it on the device), 0: ordinary launches.
                           Untuned shapes use it while n * d <= 2^24.  For ensf_set_tuning,
                           -1 keeps the current choice. */
+    int gram_fused_softmax; /* 1 (pair tiles only): the row softmax runs in the Gram's epilogue -- the
+                               last of a block's split-K CTAs sums the partials and forms the block's
+                               log-kernels, the last block of a 128-row band normalises the band --
+                               instead of a separate launch; the weights are bit-identical. */
 } ensf_tuning;
 
 /* Autotuner for the tensor-core stages: times the candidate launch shapes of

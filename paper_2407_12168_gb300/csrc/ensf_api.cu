@@ -51,6 +51,11 @@ struct Layout {
     size_t err = 0, norms = 0, w = 0, partial = 0, xbar = 0;
     size_t xb_hi = 0, xb_lo = 0, zb_hi = 0, zb_lo = 0, xt_hi = 0, xt_lo = 0, wb_hi = 0, wb_lo = 0;
     size_t noise = 0;  // one [N][d] FP32 noise slice, generated a step ahead (tensor-core W X)
+    // the row softmax in 256-column tiles: log-kernels, tile statistics,
+    // arrival counters (per row for the separate launch, then per block and
+    // per 128-row band for the softmax fused into the pair Gram)
+    size_t sm_L = 0, sm_stats = 0, sm_cnt = 0;
+    size_t sm_cnt_bytes = 0;
     size_t total = 0;
     int64_t partial_floats = 0;
 };
@@ -87,6 +92,11 @@ Layout make_layout(const ensf_config *c) {
     // the persistent small-filter path wants one partial Gram per block (SM)
     if (N <= 128) L.partial_floats = std::max<int64_t>(L.partial_floats, (int64_t)kSizingSMs * N * N);
     L.partial = take(sizeof(float) * L.partial_floats);
+    const int64_t tiles = (N + 255) / 256, bands = (N + 127) / 128;
+    L.sm_L = take(8 * N * N);
+    L.sm_stats = take(16 * N * tiles);
+    L.sm_cnt_bytes = sizeof(int) * (N + bands * tiles + bands);
+    L.sm_cnt = take(L.sm_cnt_bytes);
     if (is_tc(c->gram) || is_tc(c->wx)) {
         const int64_t NP = round_up(N, 8);  // bf16 row pitch multiple of 16 bytes
         if (c->gram == ENSF_PREC_TF32) {
@@ -272,6 +282,7 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
     int splits = 0;
     int64_t part_stride = 0;
     int ldp = 0;
+    bool fused = false;
     if (h->cfg.gram == ENSF_PREC_FP32) {
         splits = simt_splits(n, n_x, d, h->sms);
         ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_fp32(z, n, prior, n_x, d, splits, partial, s,
@@ -304,8 +315,24 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
             a.xc32 = h->at<float>(L.xb_hi) + (size_t)x0 * d;
         }
         a.pdl = h->use_pdl(n, d);
+        // the row softmax may run in the pair Gram's epilogue (when so tuned)
+        a.sm_L = h->ws + L.sm_L;
+        a.sm_stats = h->at<float4>(L.sm_stats);
+        a.sm_cnt = h->at<int>(L.sm_cnt) + h->cfg.max_n;
+        a.sm_norms = h->at<double>(L.norms) + x0;
+        a.sm_alpha = c.alpha_d;
+        a.sm_inv_2beta2 = c.inv_2beta2_d;
+        a.sm_w = want_fp32 ? h->at<float>(L.w) : nullptr;
+        a.sm_ldw = n_x;
+        if (is_tc(h->cfg.wx)) {
+            a.sm_w_hi = h->at<__nv_bfloat16>(L.wb_hi);
+            a.sm_w_lo = L.wb_lo ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
+            a.sm_ldwb = (int)round_up(n_x, 8);
+        }
+        a.sm_done = &fused;
         ENSF_LAUNCH(h, P_GRAM, s, ensf::launch_gram_tc(h->tc, a, h->sms, &splits, &part_stride, &ldp, s));
     }
+    if (fused) return ENSF_OK;
     __nv_bfloat16 *wb_hi = nullptr, *wb_lo = nullptr;
     int ldwb = 0;
     if (is_tc(h->cfg.wx)) {
@@ -314,9 +341,10 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
         ldwb = (int)round_up(n_x, 8);
     }
     ENSF_LAUNCH(h, P_SOFTMAX, s,
-                ensf::launch_softmax_rows(partial, splits, part_stride, ldp, n, n_x, h->at<double>(L.norms) + x0,
-                                          c.alpha_d, c.inv_2beta2_d, want_fp32 ? h->at<float>(L.w) : nullptr,
-                                          n_x, wb_hi, wb_lo, ldwb, s, h->use_pdl(n, d)));
+                ensf::launch_softmax_tiled(partial, splits, part_stride, ldp, n, n_x, h->at<double>(L.norms) + x0,
+                                           c.alpha_d, c.inv_2beta2_d, h->ws + L.sm_L, h->at<float4>(L.sm_stats),
+                                           h->at<int>(L.sm_cnt), want_fp32 ? h->at<float>(L.w) : nullptr, n_x,
+                                           wb_hi, wb_lo, ldwb, s, h->use_pdl(n, d)));
     return ENSF_OK;
 }
 
@@ -379,6 +407,7 @@ ensf_status ensf_create(const ensf_config *cfg, void *workspace, size_t ws_bytes
     }
 
     cudaError_t e = cudaMemset(h->err(), 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(h->ws + h->L.sm_cnt, 0, h->L.sm_cnt_bytes);
     if (e != cudaSuccess) {
         ensf::tc_context_destroy(h->tc);
         delete h;
@@ -455,6 +484,9 @@ ensf_status analysis_prep(ensf_handle *h, const float *prior, int n, int64_t d, 
     const bool tc_gram = is_tc(h->cfg.gram), tc_wx = is_tc(h->cfg.wx);
     float *xbar = h->at<float>(L.xbar);
     double *norms = norms_out ? norms_out : h->at<double>(L.norms);
+    // the softmax's arrival counters reset themselves; zeroing them here
+    // recovers from a launch that stopped early
+    ENSF_CUDA(cudaMemsetAsync(h->ws + L.sm_cnt, 0, L.sm_cnt_bytes, s));
     ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_col_mean(prior, n, d, xbar, s));
     ENSF_LAUNCH(h, P_NORMS, s, ensf::launch_row_norms(prior, n, d, norms, s, xbar, perm));
     ENSF_LAUNCH(h, P_INIT, s,
@@ -669,12 +701,13 @@ ensf_status autotune_pass(ensf_handle *h, const float *prior, int n, int64_t d, 
     auto after = [](void *vp, int splits, int64_t part_stride, int ldp, cudaStream_t st, bool pdl) -> cudaError_t {
         const SoftmaxCtx &x = *static_cast<const SoftmaxCtx *>(vp);
         const Layout &L = x.h->L;
-        return ensf::launch_softmax_rows(x.h->at<float>(L.partial), splits, part_stride, ldp, x.n, x.n,
-                                         x.h->at<double>(L.norms), x.c.alpha_d, x.c.inv_2beta2_d,
-                                         x.tc_wx ? nullptr : x.h->at<float>(L.w), x.n,
-                                         x.tc_wx ? x.h->at<__nv_bfloat16>(L.wb_hi) : nullptr,
-                                         (x.tc_wx && L.wb_lo) ? x.h->at<__nv_bfloat16>(L.wb_lo) : nullptr,
-                                         (int)round_up(x.n, 8), st, pdl);
+        return ensf::launch_softmax_tiled(x.h->at<float>(L.partial), splits, part_stride, ldp, x.n, x.n,
+                                          x.h->at<double>(L.norms), x.c.alpha_d, x.c.inv_2beta2_d,
+                                          x.h->ws + L.sm_L, x.h->at<float4>(L.sm_stats), x.h->at<int>(L.sm_cnt),
+                                          x.tc_wx ? nullptr : x.h->at<float>(L.w), x.n,
+                                          x.tc_wx ? x.h->at<__nv_bfloat16>(L.wb_hi) : nullptr,
+                                          (x.tc_wx && L.wb_lo) ? x.h->at<__nv_bfloat16>(L.wb_lo) : nullptr,
+                                          (int)round_up(x.n, 8), st, pdl);
     };
     cudaError_t e = ensf::tc_autotune(h->tc, tc_gram ? &ga : nullptr, tc_wx ? &wa : nullptr, h->sms, s, rep,
                                       tc_gram ? +after : nullptr, &sctx);
@@ -835,6 +868,7 @@ ensf_status ensf_autotune(ensf_handle *h, const float *prior, int n, int64_t d, 
         report->gram_cta_pair = r.gram_pair;
         report->gram_noise_warps = r.gram_noise_warps;
         report->gram_fp32_particles = r.gram_a_fp32;
+        report->gram_fused_softmax = 0;
         report->noise_inline = h->noise_place(n, d);
         report->pdl = h->use_pdl(n, d) ? 1 : 0;
     }
@@ -856,6 +890,7 @@ ensf_status ensf_set_tuning(ensf_handle *h, int n, int64_t d, const ensf_tuning 
     g.pair = t->gram_cta_pair;
     g.noise_warps = t->gram_noise_warps;
     g.a_fp32 = t->gram_fp32_particles;
+    g.fused_softmax = t->gram_fused_softmax;
     const bool split3 = h->cfg.gram == ENSF_PREC_SPLIT_BF16X3;
     const bool wx_split = h->cfg.wx == ENSF_PREC_SPLIT_BF16X3;
     if (ensf::tc_set_tuning(h->tc, n, n, d, split3, g, is_tc(h->cfg.wx) ? t->wx_tile_n : 0, wx_split,
@@ -891,6 +926,7 @@ ensf_status ensf_weights(ensf_handle *h, const float *z, int n, const float *pri
     c.alpha_d = alpha;
     c.inv_2beta2_d = 1.0 / (2.0 * td);
     // the FP32 weights go to the handle's W scratch, then to the caller
+    ENSF_CUDA(cudaMemsetAsync(h->ws + L.sm_cnt, 0, L.sm_cnt_bytes, s));
     ensf_status st = gram_softmax(h, z, n, prior, n_x, d, c, true, s);
     if (st != ENSF_OK) return st;
     ENSF_CUDA(cudaMemcpyAsync(w, h->at<float>(L.w), sizeof(float) * (size_t)n * n_x, cudaMemcpyDeviceToDevice, s));
@@ -1135,9 +1171,10 @@ ensf_status ensf_shard_update(ensf_handle *h, const ensf_shard *sh, int k, const
     __nv_bfloat16 *wb_hi = tc_wx ? h->at<__nv_bfloat16>(L.wb_hi) : nullptr;
     __nv_bfloat16 *wb_lo = (tc_wx && L.wb_lo) ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
     ENSF_LAUNCH(h, P_SOFTMAX, s,
-                ensf::launch_softmax_rows(partials, splits_total, (int64_t)n * n, n, n, n, norms, c.alpha_d,
-                                          c.inv_2beta2_d, tc_wx ? nullptr : h->at<float>(L.w), n, wb_hi, wb_lo,
-                                          (int)round_up(n, 8), s, h->use_pdl(n, d)));
+                ensf::launch_softmax_tiled(partials, splits_total, (int64_t)n * n, n, n, n, norms, c.alpha_d,
+                                           c.inv_2beta2_d, h->ws + L.sm_L, h->at<float4>(L.sm_stats),
+                                           h->at<int>(L.sm_cnt), tc_wx ? nullptr : h->at<float>(L.w), n, wb_hi,
+                                           wb_lo, (int)round_up(n, 8), s, h->use_pdl(n, d)));
     const bool gram_f32 =
         tc_gram && ensf::tc_gram_reads_fp32(h->tc, n, n, d, h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
     if (!tc_wx) {

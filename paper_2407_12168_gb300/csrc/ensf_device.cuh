@@ -293,4 +293,79 @@ __device__ __forceinline__ void softmax_row(int i, const float *__restrict__ par
     }
 }
 
+// ---- Row softmax of Eq. 16 in tiles of 256 columns, one warp per (row, tile)
+// The form shared by the separate softmax launch and the softmax fused into
+// the pair Gram's epilogue (bit-identical results).  Per row i and column
+// tile t, a warp forms the log-kernels l_ij of its 256 columns (written to L
+// as double-float pairs), their maximum m_t and s_t = sum_j exp(l_ij - m_t);
+// once every tile of the row is done, the row is normalised with
+// M = max_t m_t and S = sum_t s_t exp(m_t - M):  w_ij = exp(l_ij - M) / S.
+// Column j of tile t is handled by lane j % 32 in both phases; every sum runs
+// in a fixed order.  L, stats and the partials are read through L2 (other
+// blocks may have written them).
+constexpr int kSoftTile = 256;
+
+__device__ __forceinline__ void softmax_tile_stats(int i, int t, const float *__restrict__ partial, int splits,
+                                                   int64_t part_stride, int ldp, int n_x,
+                                                   const double *__restrict__ norms, const LogitCoef &kc, DF *L,
+                                                   int ldl, float4 *stats, int nt) {
+    const int lane = threadIdx.x & 31;
+    DF l[8];
+    float mx = -FLT_MAX;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int j = t * kSoftTile + e * 32 + lane;
+        if (j < n_x) {
+            l[e] = logit(kc, sum_partials(partial + (int64_t)i * ldp + j, part_stride, 0, splits), norms[j]);
+            L[(int64_t)i * ldl + j] = l[e];
+            mx = fmaxf(mx, l[e].hi);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int j = t * kSoftTile + e * 32 + lane;
+        if (j < n_x) {
+            const DF dl = df_norm(__fsub_rn(l[e].hi, mx), l[e].lo);
+            df_add(sh, sl, expf(__fadd_rn(dl.hi, dl.lo)));
+        }
+    }
+    DF s = df_norm(sh, sl);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {  // lane 0 ends with the fixed-order total
+        const DF x{__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)};
+        if (lane < o) s = df_add(s, x);
+    }
+    if (lane == 0) stats[(int64_t)i * nt + t] = make_float4(mx, s.hi, s.lo, 0.f);
+}
+
+__device__ __forceinline__ void softmax_finalize_row(int i, int n_x, int nt, const DF *L, int ldl,
+                                                     const float4 *stats, float *__restrict__ w, int ldw,
+                                                     __nv_bfloat16 *__restrict__ w_hi,
+                                                     __nv_bfloat16 *__restrict__ w_lo, int ldwb) {
+    const int lane = threadIdx.x & 31;
+    float M = -FLT_MAX;
+    for (int t = 0; t < nt; ++t) M = fmaxf(M, __ldcg(&stats[(int64_t)i * nt + t].x));
+    DF S{0.f, 0.f};
+    for (int t = 0; t < nt; ++t) {
+        const float4 st = __ldcg(&stats[(int64_t)i * nt + t]);
+        S = df_add(S, df_mul(DF{st.y, st.z}, DF{expf(__fsub_rn(st.x, M)), 0.f}));
+    }
+    const float inv = __frcp_rn(__fadd_rn(S.hi, S.lo));
+    const float2 *Lf = reinterpret_cast<const float2 *>(L);
+    for (int j = lane; j < n_x; j += 32) {
+        const float2 lv = __ldcg(&Lf[(int64_t)i * ldl + j]);
+        const DF dl = df_norm(__fsub_rn(lv.x, M), lv.y);
+        const float wv = __fmul_rn(expf(__fadd_rn(dl.hi, dl.lo)), inv);
+        if (w) w[(int64_t)i * ldw + j] = wv;
+        if (w_hi) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(wv);
+            w_hi[(int64_t)i * ldwb + j] = hi;
+            if (w_lo) w_lo[(int64_t)i * ldwb + j] = __float2bfloat16_rn(wv - __bfloat162float(hi));
+        }
+    }
+}
+
 }  // namespace ensf

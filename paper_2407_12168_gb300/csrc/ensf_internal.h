@@ -55,6 +55,14 @@ cudaError_t launch_softmax_rows(const float *partial, int splits, int64_t part_s
                                 int n, int n_x, const double *norms, double alpha,
                                 double inv_2beta2, float *w, int ldw, __nv_bfloat16 *w_hi,
                                 __nv_bfloat16 *w_lo, int ldwb, cudaStream_t s, bool pdl = false);
+// The same row softmax in 256-column tiles, one warp per (row, tile): the
+// log-kernels go to L ([n][n_x] pairs of floats), the tile statistics to
+// stats ([n][ceil(n_x / 256)] float4), rowcnt [n] (zero between launches) counts
+// finished tiles per row.  Bit-identical to the softmax fused into the pair Gram.
+cudaError_t launch_softmax_tiled(const float *partial, int splits, int64_t part_stride, int ldp, int n, int n_x,
+                                 const double *norms, double alpha, double inv_2beta2, void *L, float4 *stats,
+                                 int *rowcnt, float *w, int ldw, __nv_bfloat16 *w_hi, __nv_bfloat16 *w_lo, int ldwb,
+                                 cudaStream_t s, bool pdl = false);
 // z <- EM step with u = W X computed on FP32 CUDA cores, fused epilogue.
 cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, int n_x, int64_t d,
                               float *z, const float *y, const uint8_t *mask,

@@ -213,6 +213,33 @@ k_softmax_rows(const float *__restrict__ partial, int splits, int64_t part_strid
                     w_lo, ldwb, lg, red);
 }
 
+// Row softmax in 256-column tiles: one warp per (row, tile) forms the tile's
+// log-kernels and statistics; the last warp to finish a row (arrival counter,
+// reset by that warp) normalises it.  No warp waits for another.
+__global__ void __launch_bounds__(256)
+k_softmax_tiled(const float *__restrict__ partial, int splits, int64_t part_stride, int ldp, int n, int n_x,
+                const double *__restrict__ norms, double alpha, double inv_2beta2, DF *L, float4 *stats,
+                int *rowcnt, float *__restrict__ w, int ldw, __nv_bfloat16 *__restrict__ w_hi,
+                __nv_bfloat16 *__restrict__ w_lo, int ldwb) {
+    pdl_wait();
+    pdl_launch_dependents();
+    const int nt = (n_x + kSoftTile - 1) / kSoftTile;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= (int64_t)n * nt) return;
+    const int i = (int)(gw / nt), t = (int)(gw % nt);
+    const int lane = threadIdx.x & 31;
+    const LogitCoef kc = logit_coef(alpha, inv_2beta2);
+    softmax_tile_stats(i, t, partial, splits, part_stride, ldp, n_x, norms, kc, L, n_x, stats, nt);
+    __threadfence();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&rowcnt[i], 1) == nt - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    if (lane == 0) rowcnt[i] = 0;
+    __threadfence();
+    softmax_finalize_row(i, n_x, nt, L, n_x, stats, w, ldw, w_hi, w_lo, ldwb);
+}
+
 // ---------------------------------------------------------------------------
 // u = W X on FP32 CUDA cores (64 particles x 64 state columns per block),
 // fused with the score and the Euler-Maruyama update of Eq. 7 / Eq. 17.
@@ -540,6 +567,16 @@ cudaError_t launch_softmax_rows(const float *partial, int splits, int64_t part_s
     // measured slower: 16 against 10 us per launch on 20- and 128-member rows)
     return launch_k(k_softmax_rows<256>, dim3(n), dim3(256), smem, s, pdl, partial, splits, part_stride, ldp, n_x,
                     norms, alpha, inv_2beta2, w, ldw, w_hi, w_lo, ldwb);
+}
+
+cudaError_t launch_softmax_tiled(const float *partial, int splits, int64_t part_stride, int ldp, int n, int n_x,
+                                 const double *norms, double alpha, double inv_2beta2, void *L, float4 *stats,
+                                 int *rowcnt, float *w, int ldw, __nv_bfloat16 *w_hi, __nv_bfloat16 *w_lo, int ldwb,
+                                 cudaStream_t s, bool pdl) {
+    const int64_t warps = (int64_t)n * ((n_x + kSoftTile - 1) / kSoftTile);
+    const unsigned blocks = (unsigned)((warps + 7) / 8);
+    return launch_k(k_softmax_tiled, dim3(blocks), dim3(256), 0, s, pdl, partial, splits, part_stride, ldp, n, n_x,
+                    norms, alpha, inv_2beta2, static_cast<DF *>(L), stats, rowcnt, w, ldw, w_hi, w_lo, ldwb);
 }
 
 cudaError_t launch_wx_em_fp32(const float *w, int ldw, const float *x, int n, int n_x, int64_t d,

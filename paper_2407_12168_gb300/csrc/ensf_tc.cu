@@ -387,7 +387,59 @@ struct GramParams {
     float alpha;
     const float *centre;
     bool pdl;  // host: launched with programmatic stream serialization
+    // row softmax fused into the epilogue (pair tiles; sm_L NULL: a separate launch)
+    int splits;                 // split-K slices of this launch
+    DF *sm_L;                   // [n][n_x] log-kernels
+    float4 *sm_stats;           // [n][n_x / 256] tile statistics
+    int *sm_cnt;                // arrival counters: [n / 128][n_x / 256] blocks, then [n / 128] bands
+    const double *sm_norms;     // |x_j - m|^2
+    double sm_alpha, sm_inv_2beta2;
+    float *sm_w;                // FP32 weights [n][sm_ldw] or NULL
+    int sm_ldw;
+    __nv_bfloat16 *sm_w_hi, *sm_w_lo;
+    int sm_ldwb;
 };
+
+// The row softmax of Eq. 16 fused into the pair Gram: every CTA counts its
+// finished 128 x 256 block of partials; the last of the block's split-K CTAs
+// sums them (fixed order), forms the block's log-kernels and per-row tile
+// statistics; the last block of each 128-row band normalises the band's rows.
+// Arrival counters only (reset by the last arriver): nothing waits.  The
+// arithmetic is that of the separate tiled softmax launch.
+__device__ void gram_softmax_tail(const GramParams &p, int rb, int cb) {
+    __shared__ int s_last;
+    const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nt = (p.n_x + kSoftTile - 1) / kSoftTile;
+    const int bands = (p.n + 127) / 128;
+    int *blk_cnt = p.sm_cnt + rb * nt + cb;
+    int *band_cnt = p.sm_cnt + bands * nt + rb;
+    if (tid == 0) s_last = atomicAdd(blk_cnt, 1) == p.splits - 1;
+    __syncthreads();
+    if (!s_last) return;
+    if (tid == 0) *blk_cnt = 0;
+    __threadfence();
+    const LogitCoef kc = logit_coef(p.sm_alpha, p.sm_inv_2beta2);
+    const int64_t stride = static_cast<int64_t>(p.n) * p.n_x;
+    for (int r = warp; r < 128; r += nwarps) {
+        const int i = rb * 128 + r;
+        if (i < p.n)
+            softmax_tile_stats(i, cb, p.partial, p.splits, stride, p.n_x, p.n_x, p.sm_norms, kc, p.sm_L, p.n_x,
+                               p.sm_stats, nt);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(band_cnt, 1) == nt - 1;
+    __syncthreads();
+    if (!s_last) return;
+    if (tid == 0) *band_cnt = 0;
+    __threadfence();
+    for (int r = warp; r < 128; r += nwarps) {
+        const int i = rb * 128 + r;
+        if (i < p.n)
+            softmax_finalize_row(i, p.n_x, nt, p.sm_L, p.n_x, p.sm_stats, p.sm_w, p.sm_ldw, p.sm_w_hi, p.sm_w_lo,
+                                 p.sm_ldwb);
+    }
+}
 
 // This CTA's share of the next step's noise slice, written while the MMAs
 // run by warps noise_warp0..9 (the epilogue warps 2-5 are idle then too and
@@ -744,6 +796,7 @@ k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__
                             if (col0 + e < p.n_x) dst[col0 + e] = v[e];
                     }
                 }
+                if (p.sm_L) __threadfence();  // the partials reach L2 before this block is counted
             }
         }
     }
@@ -754,6 +807,7 @@ k_gram_tc_pair(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__
         tc_fence_after();
         tmem_dealloc_pair(tmem, kPairTile);
     }
+    if (p.sm_L && !skip && nkb > 0 && *abort_flag == 0) gram_softmax_tail(p, m_own >> 7, blockIdx.y);
 }
 
 // ------------------------------------------------ Pair Gram, FP32 particles
@@ -1894,6 +1948,25 @@ GramChoice default_gram_choice(const TcGramArgs &a) {
     return g;
 }
 
+// The fused-softmax fields of a launch: used when the caller supplied the
+// scratch, the tuning asks for it and the launch runs pair tiles.
+void set_fused_softmax(GramParams &p, const TcGramArgs &a, const GramChoice &ch, bool pair, int S) {
+    const bool on = a.sm_L && ch.fused_softmax && pair;
+    p.splits = S;
+    p.sm_L = on ? static_cast<DF *>(a.sm_L) : nullptr;
+    p.sm_stats = a.sm_stats;
+    p.sm_cnt = a.sm_cnt;
+    p.sm_norms = a.sm_norms;
+    p.sm_alpha = a.sm_alpha;
+    p.sm_inv_2beta2 = a.sm_inv_2beta2;
+    p.sm_w = a.sm_w;
+    p.sm_ldw = a.sm_ldw;
+    p.sm_w_hi = a.sm_w_hi;
+    p.sm_w_lo = a.sm_w_lo;
+    p.sm_ldwb = a.sm_ldwb;
+    if (a.sm_done) *a.sm_done = on;
+}
+
 // Split-K plan of a Gram launch with shape choice ch: the k-block width, the
 // k-blocks per split and the number of splits that hold work (returned).
 int gram_split_plan(const TcGramArgs &a, const GramChoice &ch, int sms, int *kblocks, int *kb_per_split) {
@@ -1948,6 +2021,7 @@ cudaError_t gram_launch_tf32(TcContext *ctx, const TcGramArgs &a, int sms, const
     p.noise_warp0 = ch.noise_warps == 4 ? 6 : 2;
     p.alpha = 0.f;
     p.centre = nullptr;
+    set_fused_softmax(p, a, ch, pair, S);
     *splits = S;
     *part_stride = per_split;
     *ldp = a.n_x;
@@ -2000,6 +2074,7 @@ cudaError_t gram_launch(TcContext *ctx, const TcGramArgs &a, int sms, const Gram
     p.noise_warp0 = f32a ? 2 + kPairF32Convert : (ch.noise_warps == 4 ? 6 : 2);
     p.alpha = a.alpha;
     p.centre = a.centre;
+    set_fused_softmax(p, a, ch, pair && !f32a, S);
     *splits = S;
     *part_stride = per_split;
     *ldp = a.n_x;
@@ -2148,6 +2223,7 @@ cudaError_t tc_set_tuning(TcContext *ctx, int n, int n_x, int64_t d, bool split3
     std::lock_guard<std::mutex> lock(ctx->mu);
     if (g.noise_warps != 0 && g.noise_warps != 4 && g.noise_warps != 8) return cudaErrorInvalidValue;
     if (g.a_fp32 && !g.pair) return cudaErrorInvalidValue;
+    if (g.fused_softmax && (!g.pair || g.a_fp32)) return cudaErrorInvalidValue;
     GramChoice c = g;
     c.bk = tf32 ? 32 : bk;
     ctx->gram_tuned[std::make_tuple(n, n_x, d, split3)] = c;

@@ -20,6 +20,7 @@ struct GramChoice {
     int pair = 0;    // 1: a cluster of two CTAs per 256 x 256 tile (tcgen05 cta_group::2)
     int noise_warps = 0;  // warps generating the next step's noise: 8 (default) or 4
     int a_fp32 = 0;       // pair form only: read the FP32 particles and split them in the kernel
+    int fused_softmax = 0;  // pair form only: the row softmax in the Gram's epilogue (last arrivers)
 };
 
 struct TcTuneReport {
@@ -54,6 +55,18 @@ struct TcGramArgs {
     uint32_t offset;
     int noise_k;
     int64_t noise_col0 = 0;              // global column of column 0 (noise counters are global)
+    // the row softmax, fused into the pair Gram's epilogue when the shape
+    // uses pair tiles and the tuning asks for it (sm_L NULL: never)
+    void *sm_L = nullptr;                // [n][n_x] pairs of floats
+    float4 *sm_stats = nullptr;          // [n][ceil(n_x / 256)]
+    int *sm_cnt = nullptr;               // zeroed arrival counters
+    const double *sm_norms = nullptr;
+    double sm_alpha = 0.0, sm_inv_2beta2 = 0.0;
+    float *sm_w = nullptr;
+    int sm_ldw = 0;
+    __nv_bfloat16 *sm_w_hi = nullptr, *sm_w_lo = nullptr;
+    int sm_ldwb = 0;
+    bool *sm_done = nullptr;             // out: true if this launch also computed the weights
     // the FP32 particles [n][d] and the centre, for the form that splits
     // z - alpha * centre itself (NULL: only the BF16 planes are available)
     const float *z32 = nullptr;

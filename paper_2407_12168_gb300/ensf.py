@@ -61,7 +61,7 @@ class EnsfTuning(ctypes.Structure):
                 ("gram_ms", ctypes.c_float), ("wx_tile_n", ctypes.c_int), ("wx_ms", ctypes.c_float),
                 ("gram_k_block", ctypes.c_int), ("gram_cta_pair", ctypes.c_int),
                 ("gram_noise_warps", ctypes.c_int), ("gram_fp32_particles", ctypes.c_int),
-                ("noise_inline", ctypes.c_int), ("pdl", ctypes.c_int)]
+                ("noise_inline", ctypes.c_int), ("pdl", ctypes.c_int), ("gram_fused_softmax", ctypes.c_int)]
 
 
 class EnsfSqgParams(ctypes.Structure):
@@ -466,7 +466,7 @@ class Filter:
 
     def set_tuning(self, n: int, d: int, gram_tile_n: int, gram_stages: int, gram_k_block: int = 64,
                    gram_splits: int = 0, wx_tile_n: int = 0, gram_cta_pair: int = 0, gram_noise_warps: int = 0,
-                   gram_fp32_particles: int = 0, noise_inline: int = 0, pdl: int = -1):
+                   gram_fp32_particles: int = 0, noise_inline: int = 0, pdl: int = -1, gram_fused_softmax: int = 0):
         """Record tensor-core launch shapes (and the noise placement,
         ``noise_inline`` 0 = Gram warps, 1 = W X epilogue, 2 = side-stream
         kernel, and whether the step kernels use programmatic dependent
@@ -475,7 +475,7 @@ class Filter:
         t = EnsfTuning(gram_tile_n=gram_tile_n, gram_stages=gram_stages, gram_splits=gram_splits,
                        wx_tile_n=wx_tile_n, gram_k_block=gram_k_block, gram_cta_pair=gram_cta_pair,
                        gram_noise_warps=gram_noise_warps, gram_fp32_particles=gram_fp32_particles,
-                       noise_inline=noise_inline, pdl=pdl)
+                       noise_inline=noise_inline, pdl=pdl, gram_fused_softmax=gram_fused_softmax)
         _check(load().ensf_set_tuning(self._h, int(n), int(d), ctypes.byref(t)), "ensf_set_tuning")
 
     def autotune(self, prior, y, mask, sigma_obs: float, eps: float, obs_op: int = OBS_IDENTITY, seed: int = 0,
