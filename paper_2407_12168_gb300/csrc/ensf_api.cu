@@ -1252,7 +1252,7 @@ BatchLayout batch_layout(const ensf_config *cfg, const ensf_instance *inst, int 
     }
     B.tables_begin = off;
     B.maps_gram = take(128 * 4 * (size_t)count);
-    B.maps_wx = take(128 * 4 * (size_t)count);
+    B.maps_wx = take(128 * 8 * (size_t)count);  // W X operands (4), staging maps of z and its planes (3), unused
     B.insts = take(sizeof(ensf::BInst) * count);
     B.gram_items = take(sizeof(ensf::BGramItem) * B.n_gram_items);
     B.rows = take(sizeof(ensf::BRow) * B.n_rows);
@@ -1291,6 +1291,9 @@ ensf_status batch_enqueue(ensf_handle *h, const ensf_instance *inst, int count, 
     }
     const void *maps_gram = at(B.maps_gram), *maps_wx = at(B.maps_wx);
     const ensf::BInst *binst = reinterpret_cast<const ensf::BInst *>(at(B.insts));
+    // the TMA-staged W X epilogue: BF16 W X with every filter on the counter-based noise
+    bool staged = !wsp && !(h->cfg.flags & ENSF_FLAG_WX_UNSTAGED);
+    for (int i = 0; i < count && staged; ++i) staged = inst[i].noise.buf == nullptr;
     for (int k = 0; k < K; ++k) {
         ensf::StepCoef c = step_coef(k, K, eps, 1.0, 0);
         ENSF_LAUNCH(h, P_GRAM, s,
@@ -1302,7 +1305,7 @@ ensf_status batch_enqueue(ensf_handle *h, const ensf_instance *inst, int count, 
         ENSF_LAUNCH(h, P_WXEM, s,
                     ensf::launch_wx_em_tc_batched(maps_wx, reinterpret_cast<const ensf::BWxItem *>(at(B.wx_items)),
                                                   B.n_wx_items, binst, wsp, c, step_coef(k + 1, K, eps, 1.0, 0).alpha,
-                                                  h->err(), h->sms, s));
+                                                  h->err(), h->sms, s, staged));
     }
     return ENSF_OK;
 }
@@ -1394,7 +1397,7 @@ ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int
         b.obs_op = I.obs_op;
         bi[i] = b;
         char *mg = tab(B.maps_gram) + 512 * (size_t)i;
-        char *mw = tab(B.maps_wx) + 512 * (size_t)i;
+        char *mw = tab(B.maps_wx) + 1024 * (size_t)i;
         cudaError_t e = cudaSuccess;
         if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mg + 0, b.zb_hi, I.d, I.n, I.d, 128);
         if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mg + 128, b.zb_lo, I.d, I.n, I.d, 128);
@@ -1404,6 +1407,10 @@ ensf_status ensf_analysis_batched(ensf_handle *h, const ensf_instance *inst, int
         if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mw + 128, wsp ? dev(L.xt_lo) : nullptr, I.n, I.d, L.ldw, 128);
         if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mw + 256, b.wb_hi, I.n, I.n, L.ldw, T);
         if (e == cudaSuccess) e = ensf::tc_encode_map(h->tc, mw + 384, b.wb_lo, I.n, I.n, L.ldw, T);
+        if (e == cudaSuccess) e = ensf::tc_encode_stage_map(h->tc, mw + 512, I.out, 4, I.d, I.n);
+        if (e == cudaSuccess) e = ensf::tc_encode_stage_map(h->tc, mw + 640, b.zb_hi, 2, I.d, I.n);
+        if (e == cudaSuccess) e = ensf::tc_encode_stage_map(h->tc, mw + 768, b.zb_lo, 2, I.d, I.n);
+        if (e == cudaSuccess) e = ensf::tc_encode_stage_map(h->tc, mw + 896, nullptr, 4, I.d, I.n);
         if (e != cudaSuccess) return cuda_fail(e, "tensor map encoding");
         const int mt = (I.n + T - 1) / T;
         for (int m = 0; m < mt; ++m)

@@ -1489,6 +1489,7 @@ k_wx_em_staged(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant_
                 __nv_bfloat16 *hs = reinterpret_cast<__nv_bfloat16 *>(stg + buf * P::kStgBuf + P::kStgZ);
                 __nv_bfloat16 *ls = hs + kStgRows * kStgCols;
                 const int i0 = n0 + cc;
+                if (i0 < p.n) {  // (a chunk wholly past the last particle is neither computed nor stored)
                 float xi[16];
 #pragma unroll
                 for (int e4 = 0; e4 < 4; ++e4) {
@@ -1510,6 +1511,7 @@ k_wx_em_staged(const __grid_constant__ CUtensorMap xt_hi, const __grid_constant_
                         hs[e * kStgCols + cl] = hi;
                         if (lo_plane) ls[e * kStgCols + cl] = __float2bfloat16_rn(zc - __bfloat162float(hi));
                     }
+                }
                 }
                 // the chunk's shared-memory writes, visible to the TMA store, then
                 // counted on the chunk's barrier; the leader alone waits (bounded)
@@ -1644,7 +1646,7 @@ k_wx_em_tc_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__restri
             for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
                 const BWxItem w = items[t];
                 const int kblocks = (insts[w.inst].n + BK - 1) / BK;
-                const CUtensorMap *m = maps + 4 * w.inst;
+                const CUtensorMap *m = maps + 8 * w.inst;  // eight maps per filter
                 for (int kb = 0; kb < kblocks; ++kb, ++it_count) {
                     const int s = it_count % STAGES;
                     const uint32_t ph = (it_count / STAGES) & 1;
@@ -1763,6 +1765,231 @@ k_wx_em_tc_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__restri
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[slot]);
         }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kWxTmemCols);
+    }
+}
+
+// Batched W X + EM with the TMA-staged epilogue of k_wx_em_staged, over the
+// tile list of all filters (BN = kBatchTileN particles per item).  The
+// filter's maps sit at maps[8 inst + ...]: 0, 2 the W X operands (X^T, W),
+// 4, 5, 6 the staging maps of z (FP32) and of its BF16 hi and lo planes.  The
+// noise is the counter-based stream of each filter (no caller buffers).
+__global__ void __launch_bounds__(kWxThreads, 1)
+k_wx_em_staged_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__restrict__ items, int n_items,
+                       const BInst *__restrict__ insts, StepCoef cf, float alpha_next, int *err) {
+    constexpr int BN = kBatchTileN, STAGES = 3;
+    using P = WxStagedPlan<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*reinterpret_cast<volatile int *>(err) != 0) return;
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    uint8_t *tiles = smem_raw + pad;
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *zfull = tempty + 2;
+    uint64_t *zdone = zfull + 8;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(zdone + 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], kEpiWarps);
+        }
+        for (int b = 0; b < 8; ++b) {
+            mbar_init(&zfull[b], 1);
+            mbar_init(&zdone[b], 128);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kWxTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0, issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
+                const BWxItem w = items[t];
+                const int kblocks = (insts[w.inst].n + BK - 1) / BK;
+                const CUtensorMap *m = maps + 8 * w.inst;
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err)) { ok = false; break; }
+                    const uint32_t st = smem_u32(tiles + s * P::kStage);
+                    mbar_expect_tx(&full[s], P::kStage);
+                    tma_load_2d(st, m + 0, &full[s], kb * BK, w.m0);
+                    tma_load_2d(st + P::kA, m + 2, &full[s], kb * BK, w.n0);
+                    issued = it + 1;
+                }
+            }
+            if (*abort_flag) {
+                const uint64_t t0 = globaltimer();
+                for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i) {
+                    const int s = i % STAGES;
+                    while (!mbar_try_wait(&full[s], (i / STAGES) & 1) && globaltimer() - t0 < kTimeoutNs) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int it = 0, lt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x, ++lt) {
+                const int slot = lt & 1;
+                const uint32_t use = lt >> 1;
+                const int kblocks = (insts[items[t].inst].n + BK - 1) / BK;
+                if (!mbar_wait(&tempty[slot], (use & 1u) ^ 1u, abort_flag, err)) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + slot * 256;
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&full[s], ph, abort_flag, err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(tiles + s * P::kStage);
+                    const uint32_t b = a + P::kA;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(acc, desc_sw128(a + kk * 32), desc_sw128(b + kk * 32), idesc,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[slot]);
+            }
+        }
+    } else {
+        const int ew = warp - 2;
+        const int q = warp & 3;
+        const int part = ew >> 2;
+        const bool leader = (ew & 3) == 0 && lane == 0;
+        constexpr int kMaxChunks = BN / kStgRows;   // 16-particle chunks of an item
+        const int cl = q * 32 + lane;
+        uint8_t *stg = tiles + P::kStgOff + part * 2 * P::kStgBuf;
+        uint64_t *zf = zfull + part * 2;
+        uint64_t *zd = zdone + part * 2;
+        // An item's chunks that hold particles go round-robin to the four
+        // groups of epilogue warps (chunk j to group j % 4), so that items of
+        // small filters keep every group busy.
+        auto chunks_of = [&](int t) -> int {
+            const BWxItem w = items[t];
+            const int live = min(kMaxChunks, (insts[w.inst].n - w.n0 + kStgRows - 1) / kStgRows);
+            return live > part ? (live - part - 1) / 4 + 1 : 0;
+        };
+        // the cursor of this group's next chunk to load: item nt, local chunk nc
+        int nt = blockIdx.x, nc = 0;
+        auto skip_empty = [&]() {
+            while (nt < n_items && nc >= chunks_of(nt)) {
+                nt += gridDim.x;
+                nc = 0;
+            }
+        };
+        int loads = 0;  // chunks this group has loaded (the buffer and phase of a load)
+        auto issue_next = [&]() {
+            skip_empty();
+            if (nt >= n_items) return;
+            const BWxItem w = items[nt];
+            const int y = w.n0 + (part + 4 * nc) * kStgRows;
+            uint64_t *bar = &zf[loads & 1];
+            mbar_expect_tx(bar, P::kStgZ);
+            tma_load_2d(smem_u32(stg + (loads & 1) * P::kStgBuf), maps + 8 * w.inst + 4, bar, w.m0, y);
+            ++loads;
+            ++nc;
+        };
+        if (leader) issue_next();
+        int g = 0, lt = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x, ++lt) {
+            const int slot = lt & 1;
+            const uint32_t use = lt >> 1;
+            const BWxItem w = items[t];
+            const BInst &I = insts[w.inst];
+            const CUtensorMap *m = maps + 8 * w.inst;
+            if (!__all_sync(0xffffffffu, mbar_wait(&tfull[slot], use & 1u, abort_flag, err))) break;
+            tc_fence_after();
+            const int64_t c = static_cast<int64_t>(w.m0) + cl;
+            const bool cok = c < I.d;
+            const float yc = cok ? I.y[c] : 0.f;
+            const bool obs = cok && (I.mask == nullptr || I.mask[c] != 0);
+            const float shift = cok ? __fmul_rn(alpha_next, I.centre[c]) : 0.f;
+            const bool lo_plane = I.zb_lo != nullptr;
+            const int mine = chunks_of(t);
+#pragma unroll 1
+            for (int ch = 0; ch < mine; ++ch, ++g) {
+                const int buf = g & 1;
+                if (leader) {
+                    bulk_wait_read_all();  // the store of this group's previous chunk has left that buffer
+                    issue_next();
+                }
+                const int cc = (part + 4 * ch) * kStgRows;  // accumulator column = particle within the item
+                float u[16];
+                tmem_ld16(tmem + slot * 256 + (static_cast<uint32_t>(q * 32) << 16) + cc, u);
+                if (!__all_sync(0xffffffffu, mbar_wait(&zf[buf], (g >> 1) & 1u, abort_flag, err))) {
+                    ok = false;
+                    break;
+                }
+                float *zs = reinterpret_cast<float *>(stg + buf * P::kStgBuf);
+                __nv_bfloat16 *hs = reinterpret_cast<__nv_bfloat16 *>(stg + buf * P::kStgBuf + P::kStgZ);
+                __nv_bfloat16 *ls = hs + kStgRows * kStgCols;
+                const int i0 = w.n0 + cc;
+                float xi[16];
+#pragma unroll
+                for (int e4 = 0; e4 < 4; ++e4) {
+                    const float4 v = noise4(I.seed, I.offset, cf.k + 1, c, (i0 >> 2) + e4);
+                    xi[e4 * 4 + 0] = v.x;
+                    xi[e4 * 4 + 1] = v.y;
+                    xi[e4 * 4 + 2] = v.z;
+                    xi[e4 * 4 + 3] = v.w;
+                }
+#pragma unroll
+                for (int e = 0; e < kStgRows; ++e) {
+                    const float zv = zs[e * kStgCols + cl];
+                    const float gl = obs ? lik_score(I.obs_op, zv, yc, I.inv_r) : 0.f;
+                    const float zn = em_update(cf, zv, u[e], gl, xi[e]);
+                    zs[e * kStgCols + cl] = zn;
+                    const float zc = __fsub_rn(zn, shift);
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
+                    hs[e * kStgCols + cl] = hi;
+                    if (lo_plane) ls[e * kStgCols + cl] = __float2bfloat16_rn(zc - __bfloat162float(hi));
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&zd[buf]);
+                if (leader) {
+                    if (!mbar_wait(&zd[buf], (g >> 1) & 1u, abort_flag, err)) {
+                        ok = false;
+                    } else {
+                        tma_store_2d(m + 4, smem_u32(zs), w.m0, i0);
+                        tma_store_2d(m + 5, smem_u32(hs), w.m0, i0);
+                        if (lo_plane) tma_store_2d(m + 6, smem_u32(ls), w.m0, i0);
+                        bulk_commit();
+                    }
+                }
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[slot]);
+        }
+        if (leader) bulk_wait_all();
+        (void)ok;
     }
     tc_fence_before();
     __syncthreads();
@@ -2112,6 +2339,11 @@ cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *sp
     return gram_launch(ctx, a, sms, ch, splits, part_stride, ldp, s);
 }
 
+cudaError_t tc_encode_stage_map(TcContext *ctx, void *out128, const void *base, int esize, int64_t cols,
+                                int64_t rows) {
+    return make_map_stage(ctx, static_cast<CUtensorMap *>(out128), base, esize, cols, rows);
+}
+
 int tc_gram_split_count(TcContext *ctx, const TcGramArgs &a, int sms) {
     if (!ctx) return 0;
     GramChoice ch = default_gram_choice(a);
@@ -2298,10 +2530,17 @@ cudaError_t launch_softmax_batched(const BRow *rows, int n_rows, const BInst *in
 
 cudaError_t launch_wx_em_tc_batched(const void *maps, const BWxItem *items, int n_items, const BInst *insts,
                                     bool split, const StepCoef &cf, float alpha_next, int *err, int sms,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, bool staged) {
     if (n_items <= 0) return cudaSuccess;
     const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
     const int grid = n_items < sms ? n_items : sms;
+    if (staged && !split) {
+        using P = WxStagedPlan<kBatchTileN, 3>;
+        cudaError_t e = set_smem(k_wx_em_staged_batched, P::kBytes);
+        if (e != cudaSuccess) return e;
+        k_wx_em_staged_batched<<<grid, kWxThreads, P::kBytes, s>>>(m, items, n_items, insts, cf, alpha_next, err);
+        return cudaGetLastError();
+    }
     if (split) {
         using P = WxPlan<kBatchTileN, 3, true>;
         auto kern = k_wx_em_tc_batched<kBatchTileN, 3, true>;

@@ -144,9 +144,15 @@ cudaError_t launch_gram_tc_batched(const void *maps, const BGramItem *items, int
                                    bool split3, int *err, cudaStream_t s);
 cudaError_t launch_softmax_batched(const BRow *rows, int n_rows, const BInst *insts, int max_n, double alpha,
                                    double inv_2beta2, cudaStream_t s);
+// staged: BF16 W X with the TMA-staged epilogue (maps: 8 per filter, the
+// staging maps of z and its planes at 4, 5, 6; Philox noise only)
 cudaError_t launch_wx_em_tc_batched(const void *maps, const BWxItem *items, int n_items, const BInst *insts,
                                     bool split, const StepCoef &cf, float alpha_next, int *err, int sms,
-                                    cudaStream_t s);
+                                    cudaStream_t s, bool staged = false);
+// Host: the staging tensor map of the staged W X epilogue (rows x cols of
+// esize-byte elements, 128 x 16 boxes, no swizzle) into `out` (NULL base: zeroed).
+cudaError_t tc_encode_stage_map(TcContext *ctx, void *out128, const void *base, int esize, int64_t cols,
+                                int64_t rows);
 
 cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *splits,
                            int64_t *part_stride, int *ldp, cudaStream_t s);

@@ -72,3 +72,26 @@ def test_staged_epilogue_matches_oracle():
     _, r_ref = o.mean_rmse(ref, p.truth)
     _, r_got = o.mean_rmse(got, p.truth)
     assert r_got == pytest.approx(r_ref, rel=1e-2)
+
+
+def test_batched_staged_epilogue_is_bitwise_the_unstaged_one():
+    """The batched W X of many uneven filters with the TMA-staged epilogue
+    (per-filter staging maps in the device table) against the batched
+    per-thread epilogue: bitwise, for every filter, BF16 and split Gram."""
+    import torch
+    from paper_2407_12168_gb300 import ensf
+    cases = [(91, 33, 36, 1, 1, 0.5, 0.4), (92, 130, 32, 2, 0, 1.0, 0.6), (93, 64, 44, 1, 1, 0.25, 0.3),
+             (94, 200, 20, 2, 1, 0.6, 0.4), (95, 16, 64, 2, 0, 0.5, 1.0)]
+    probs = [inputs.small_case(seed=c[0], n=c[1], grid=c[2], layers=c[3], K=5, obs_op=c[4], obs_frac=c[5],
+                               sigma_obs=c[6]) for c in cases]
+    for gram in ("split", "bf16"):
+        outs = []
+        for unstaged in (False, True):
+            f = ensf.Filter(256, 8192, gram=gram, wx="bf16", wx_unstaged=unstaged)
+            filters = [dict(prior=torch.from_numpy(p.prior).cuda(), y=torch.from_numpy(p.y).cuda(),
+                            mask=torch.from_numpy(p.mask).cuda() if p.mask is not None else None,
+                            sigma_obs=p.sigma_obs, obs_op=p.obs_op, seed=p.seed) for p in probs]
+            outs.append([o.cpu().numpy() for o in f.analysis_batched(filters, 5, 0.05)])
+            assert f.status_sync() == 0
+        for a, b in zip(*outs):
+            assert np.array_equal(a, b)
