@@ -1999,6 +1999,166 @@ k_wx_em_staged_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__re
     }
 }
 
+// ------------------------------------------------ 3x3 convolution (implicit GEMM)
+// out[p][n] = sum over taps (dy, dx) and input channels c of
+//             xpad[b][y + dy][x + dx][c] * wt[n][(dy * 3 + dx) * C + c]
+// for output pixel p = (b, y, x) of an image of h x w pixels, xpad the input
+// with a one-pixel circular halo ((h + 2) x (w + 2) per image, NHWC, BF16).
+// One CTA computes 128 pixels (128 / w whole image rows) x BN output
+// channels: k-block kb = tap * (C / 32) + channel block is one TMA box of
+// 32 channels x w pixels x 128 / w rows read at the tap's offset from xpad,
+// plus 32 columns of the K-major weights, so no im2col matrix exists.  The
+// epilogue adds the bias and applies SiLU (act) or stores the plain sums
+// (the data gradient, with the weights' taps mirrored by the caller).
+struct ConvParams {
+    int P;          // output pixels (a multiple of 128)
+    int N;          // output channels
+    int cblk;       // input channels / 32
+    int h, w, hp;   // image rows and columns, padded rows h + 2
+    int rows;       // image rows per 128-pixel tile (128 / w)
+    const float *bias;  // [N] or NULL
+    int act;            // 1: z = sum + bias, y = SiLU(z); 0: the sum alone
+    float *out32;       // [P][N] FP32 (the pre-activation z, or the data gradient)
+    __nv_bfloat16 *out16;  // [P][N] BF16 SiLU(z), or NULL
+    int *err;
+};
+
+constexpr int kConvKB = 32;     // input channels per k-block (64-byte rows)
+constexpr int kConvStages = 6;
+struct ConvPlan {
+    static constexpr int kA = BM * kConvKB * 2;      // 8 KB: 128 pixels x 32 channels
+    static constexpr int kBmax = 256 * kConvKB * 2;  // 16 KB: up to 256 output channels
+    static constexpr int kStage = kA + kBmax;
+    static constexpr int kBarOff = kStage * kConvStages;
+    static constexpr int kBytes = kBarOff + 256 + 1024;
+    static_assert(kBytes <= 227 * 1024, "shared memory plan too large");
+};
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1)
+k_conv3x3(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUtensorMap b_map, ConvParams p, int BN,
+          uint32_t tmem_cols) {
+    using P = ConvPlan;
+    extern __shared__ uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*reinterpret_cast<volatile int *>(p.err) != 0) return;
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    uint8_t *tiles = smem_raw + pad;
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
+    uint64_t *empty = full + kConvStages;
+    uint64_t *accum = empty + kConvStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kConvStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int p0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int img = p0 / (p.h * p.w), y0 = (p0 / p.w) % p.h;
+    const int nkb = 9 * p.cblk;
+    const uint32_t stage_bytes = P::kA + BN * kConvKB * 2;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % kConvStages;
+                const uint32_t ph = (kb / kConvStages) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) break;
+                const uint32_t st = smem_u32(tiles + s * P::kStage);
+                mbar_expect_tx(&full[s], stage_bytes);
+                const int tap = kb / p.cblk, cb = kb % p.cblk;
+                tma_load_3d(st, &a_map, &full[s], cb * kConvKB, tap % 3, img * p.hp + y0 + tap / 3);
+                tma_load_2d(st + P::kA, &b_map, &full[s], kb * kConvKB, n0);
+                issued = kb + 1;
+            }
+            if (*abort_flag) {
+                const uint64_t t0 = globaltimer();
+                for (int i = issued > kConvStages ? issued - kConvStages : 0; i < issued; ++i) {
+                    const int s = i % kConvStages;
+                    while (!mbar_try_wait(&full[s], (i / kConvStages) & 1) && globaltimer() - t0 < kTimeoutNs) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(BM, BN);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % kConvStages;
+                const uint32_t ph = (kb / kConvStages) & 1;
+                if (!mbar_wait(&full[s], ph, abort_flag, p.err)) break;
+                tc_fence_after();
+                const uint32_t a = smem_u32(tiles + s * P::kStage);
+                const uint32_t b = a + P::kA;
+#pragma unroll
+                for (int kk = 0; kk < kConvKB / 16; ++kk)
+                    mma_bf16(tmem, desc_sw64(a + kk * 32), desc_sw64(b + kk * 32), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&empty[s]);
+            }
+            mma_commit(accum);
+        }
+    } else {
+        const int q = warp & 3;  // TMEM lane quarter
+        const int pix = p0 + q * 32 + lane;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(accum, 0, abort_flag, p.err));
+        tc_fence_after();
+        if (ok) {
+            for (int cc = 0; cc < BN; cc += 32) {
+                float v[32];
+                tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + cc, v);
+                const int nb = n0 + cc;
+                if (nb >= p.N) continue;
+                float *o32 = p.out32 + static_cast<int64_t>(pix) * p.N + nb;
+                if (p.act) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] = __fadd_rn(v[e], p.bias[nb + e]);
+                }
+#pragma unroll
+                for (int e = 0; e < 32; e += 4)
+                    *reinterpret_cast<float4 *>(o32 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                if (p.out16) {
+                    __nv_bfloat16 *o16 = p.out16 + static_cast<int64_t>(pix) * p.N + nb;
+#pragma unroll
+                    for (int e = 0; e < 32; e += 8) {
+                        __align__(16) __nv_bfloat16 t8[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const float z = v[e + k];
+                            t8[k] = __float2bfloat16_rn(z * (1.f / (1.f + __expf(-z))));
+                        }
+                        *reinterpret_cast<uint4 *>(o16 + e) = *reinterpret_cast<const uint4 *>(t8);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, tmem_cols);
+    }
+}
+
 }  // namespace
 
 // =================================================================== host
@@ -2337,6 +2497,63 @@ cudaError_t launch_gram_tc(TcContext *ctx, const TcGramArgs &a, int sms, int *sp
         if (it != ctx->gram_tuned.end()) ch = it->second;
     }
     return gram_launch(ctx, a, sms, ch, splits, part_stride, ldp, s);
+}
+
+bool conv3x3_supported(int C, int N, int h, int w, int P) {
+    return C % kConvKB == 0 && C > 0 && N % 32 == 0 && N > 0 && N <= 512 && w <= BM && BM % w == 0 &&
+           (BM / w) <= h && h % (BM / w) == 0 && P % BM == 0;
+}
+
+cudaError_t launch_conv3x3(TcContext *ctx, const __nv_bfloat16 *xpad, int C, int B, int h, int w,
+                           const __nv_bfloat16 *wt, int N, const float *bias, int act, float *out32,
+                           __nv_bfloat16 *out16, int *err, cudaStream_t s) {
+    const int P = B * h * w;
+    if (!ctx || !conv3x3_supported(C, N, h, w, P)) return cudaErrorInvalidValue;
+    CUtensorMap am, bm;
+    {
+        const int wp = w + 2, hp = h + 2;
+        cuuint64_t dims[3] = {static_cast<cuuint64_t>(C), static_cast<cuuint64_t>(wp),
+                              static_cast<cuuint64_t>(B) * hp};
+        cuuint64_t strides[2] = {static_cast<cuuint64_t>(C) * 2, static_cast<cuuint64_t>(wp) * C * 2};
+        cuuint32_t box[3] = {static_cast<cuuint32_t>(kConvKB), static_cast<cuuint32_t>(w),
+                             static_cast<cuuint32_t>(BM / w)};
+        cuuint32_t estr[3] = {1, 1, 1};
+        if (ctx->encode(&am, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(xpad), dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const int BN = N <= 256 ? N : N / 2;
+    if (BN % 16 != 0) return cudaErrorInvalidValue;
+    {
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(9) * C, static_cast<cuuint64_t>(N)};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(9) * C * 2};
+        cuuint32_t box[2] = {static_cast<cuuint32_t>(kConvKB), static_cast<cuuint32_t>(BN)};
+        cuuint32_t estr[2] = {1, 1};
+        if (ctx->encode(&bm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(wt), dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    ConvParams prm;
+    prm.P = P;
+    prm.N = N;
+    prm.cblk = C / kConvKB;
+    prm.h = h;
+    prm.w = w;
+    prm.hp = h + 2;
+    prm.rows = BM / w;
+    prm.bias = bias;
+    prm.act = act;
+    prm.out32 = out32;
+    prm.out16 = out16;
+    prm.err = err;
+    uint32_t cols = 32;
+    while (static_cast<int>(cols) < BN) cols <<= 1;
+    cudaError_t e = set_smem(k_conv3x3, ConvPlan::kBytes);
+    if (e != cudaSuccess) return e;
+    k_conv3x3<<<dim3(P / BM, (N + BN - 1) / BN), 192, ConvPlan::kBytes, s>>>(am, bm, prm, BN, cols);
+    return cudaGetLastError();
 }
 
 cudaError_t tc_encode_stage_map(TcContext *ctx, void *out128, const void *base, int esize, int64_t cols,

@@ -149,6 +149,17 @@ cudaError_t launch_softmax_batched(const BRow *rows, int n_rows, const BInst *in
 cudaError_t launch_wx_em_tc_batched(const void *maps, const BWxItem *items, int n_items, const BInst *insts,
                                     bool split, const StepCoef &cf, float alpha_next, int *err, int sms,
                                     cudaStream_t s, bool staged = false);
+// 3x3 convolution with circular padding as an implicit GEMM on the tensor
+// cores: out[p][n] = sum_{dy, dx, c} xpad[b][y + dy][x + dx][c] wt[n][(dy * 3 + dx) * C + c]
+// (xpad: the BF16 NHWC input with a one-pixel circular halo, B x (h + 2) x (w + 2) x C;
+// wt: [N][9 C] BF16).  act = 1: out32 = sum + bias (the pre-activation),
+// out16 = SiLU of it; act = 0: out32 = the sum.  conv3x3_supported tells
+// which shapes it takes (C a multiple of 32, N of 32 up to 512, whole image
+// rows per 128-pixel tile).
+bool conv3x3_supported(int C, int N, int h, int w, int P);
+cudaError_t launch_conv3x3(TcContext *ctx, const __nv_bfloat16 *xpad, int C, int B, int h, int w,
+                           const __nv_bfloat16 *wt, int N, const float *bias, int act, float *out32,
+                           __nv_bfloat16 *out16, int *err, cudaStream_t s);
 // Host: the staging tensor map of the staged W X epilogue (rows x cols of
 // esize-byte elements, 128 x 16 boxes, no swizzle) into `out` (NULL base: zeroed).
 cudaError_t tc_encode_stage_map(TcContext *ctx, void *out128, const void *base, int esize, int64_t cols,

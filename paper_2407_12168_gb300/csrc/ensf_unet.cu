@@ -88,6 +88,32 @@ __global__ void k_col2im(const float *__restrict__ dcol, int B, int H, int W, in
     dx[i] = accumulate ? dx[i] + acc : acc;
 }
 
+// xp[b][yy][xx][c] = x[b][(yy - 1) mod h][(xx - 1) mod w][c]: the input of an
+// implicit-GEMM convolution with its one-pixel circular halo; 8 channels per thread.
+__global__ void k_pad_circ(const bf16 *__restrict__ x, int B, int h, int w, int C, bf16 *__restrict__ xp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over B (h + 2) (w + 2) C / 8
+    const int c8 = C / 8;
+    const int64_t total = (int64_t)B * (h + 2) * (w + 2) * c8;
+    if (i >= total) return;
+    const int cv = (int)(i % c8);
+    const int64_t pp = i / c8;
+    const int xx = (int)(pp % (w + 2)), yy = (int)((pp / (w + 2)) % (h + 2));
+    const int64_t b = pp / ((int64_t)(w + 2) * (h + 2));
+    const int sy = (yy - 1 + h) % h, sx = (xx - 1 + w) % w;
+    reinterpret_cast<uint4 *>(xp)[i] = reinterpret_cast<const uint4 *>(x)[((b * h + sy) * w + sx) * c8 + cv];
+}
+
+// Weights of the data gradient: wf[c][tap'][n] = W[n][8 - tap'][c] (the taps
+// mirrored), so that the gradient is the same implicit-GEMM convolution.
+__global__ void k_repack_flip(const float *__restrict__ W, int Co, int Ci, bf16 *__restrict__ wf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over Ci * 9 * Co
+    if (i >= (int64_t)Ci * 9 * Co) return;
+    const int n = (int)(i % Co);
+    const int tap = (int)((i / Co) % 9);
+    const int c = (int)(i / ((int64_t)9 * Co));
+    wf[i] = __float2bfloat16_rn(W[((int64_t)n * 9 + (8 - tap)) * Ci + c]);
+}
+
 __global__ void k_reduce_splits(const float *__restrict__ part, int S, int64_t count, float *__restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -337,6 +363,7 @@ struct ensf_unet {
         int ci, co, kp, res;  // res: resolution level 0..3
         int64_t w_off, b_off; // offsets in the flat parameter vector
         bf16 *wb, *wt;        // BF16 weights [co][kp] and [kp][co]
+        bf16 *wf;             // BF16 weights of the data gradient [ci][9][co], taps mirrored
         float *z;             // pre-activation [P][co]
         bf16 *y;              // activation [P][co]
         const bf16 *in;       // input activation [P][ci]
@@ -353,6 +380,7 @@ struct ensf_unet {
     int *err;                  // device error word of the GEMM launches (ENSF_ETIMEOUT on an expired wait)
     // scratch
     bf16 *col, *colT, *dz16, *dzT;
+    bf16 *xpad;                // a convolution's input with its circular halo (implicit GEMM)
     float *gemm_c, *partial, *dz32, *ga, *gb, *colsum_part;
     float *gskip[kLevels];     // gradients of the encoder outputs (skips), levels 0..2
     int64_t partial_cap = 0;
@@ -417,6 +445,7 @@ size_t unet_layout(ensf_unet *u, const ensf_unet_config *c, char *base) {
         ensf_unet::Conv &cv = u->conv[l];
         cv.wb = a.take<bf16>((int64_t)cv.co * cv.kp);
         cv.wt = a.take<bf16>((int64_t)cv.co * cv.kp);
+        cv.wf = a.take<bf16>((int64_t)cv.co * 9 * cv.ci);
         cv.z = a.take<float>(P(cv.res) * cv.co);
         cv.y = a.take<bf16>(P(cv.res) * cv.co);
     }
@@ -433,6 +462,15 @@ size_t unet_layout(ensf_unet *u, const ensf_unet_config *c, char *base) {
     u->sq = a.take<float>(P0 * 2);
     u->loss = a.take<double>(1);
     u->err = a.take<int>(4);
+    {
+        int64_t mx = 0;
+        for (int l = 0; l < kConvs; ++l) {
+            const ensf_unet::Conv &cv = u->conv[l];
+            const int64_t hp = (c->height >> cv.res) + 2, wp = (c->width >> cv.res) + 2;
+            mx = std::max<int64_t>(mx, (int64_t)c->max_batch * hp * wp * std::max(cv.ci, cv.co));
+        }
+        u->xpad = a.take<bf16>(mx);
+    }
     u->col = a.take<bf16>(max_colk);
     u->colT = a.take<bf16>(max_colk);
     u->dz16 = a.take<bf16>(max_chan);
@@ -525,6 +563,16 @@ ensf_status forward(ensf_unet *u, const float *x_nchw, int B, cudaStream_t s) {
         ensf_unet::Conv &cv = u->conv[l];
         const int h = H >> cv.res, w = W >> cv.res;
         const int64_t P = (int64_t)B * h * w;
+        if (ensf::conv3x3_supported(cv.ci, cv.co, h, w, (int)P)) {
+            // implicit GEMM: the haloed input, then one kernel with bias + SiLU in its epilogue
+            k_pad_circ<<<nb((int64_t)B * (h + 2) * (w + 2) * (cv.ci / 8)), 256, 0, s>>>(cv.in, B, h, w, cv.ci,
+                                                                                         u->xpad);
+            UNET_LAUNCH();
+            if (ensf::launch_conv3x3(u->tc, u->xpad, cv.ci, B, h, w, cv.wb, cv.co, u->params + cv.b_off, 1, cv.z,
+                                     cv.y, u->err, s) != cudaSuccess)
+                return unet_fail(ENSF_ECUDA, "unet implicit convolution launch");
+            return ENSF_OK;
+        }
         k_im2col<<<nb(P * cv.kp), 256, 0, s>>>(cv.in, B, h, w, cv.ci, cv.kp, u->col);
         UNET_LAUNCH();
         ensf_status st = gemm(u, u->col, cv.wb, P, cv.co, cv.kp, u->gemm_c, s);
@@ -586,6 +634,16 @@ ensf_status conv_back(ensf_unet *u, int l, int B, const float *dy, float *dx, in
                                                                u->grads + cv.w_off);
     UNET_LAUNCH();
     if (!dx) return ENSF_OK;
+    if (!accumulate && ensf::conv3x3_supported(cv.co, cv.ci, h, w, (int)P)) {
+        // the data gradient as the same implicit-GEMM convolution of the haloed dZ with mirrored taps
+        k_pad_circ<<<nb((int64_t)B * (h + 2) * (w + 2) * (cv.co / 8)), 256, 0, s>>>(u->dz16, B, h, w, cv.co,
+                                                                                     u->xpad);
+        UNET_LAUNCH();
+        if (ensf::launch_conv3x3(u->tc, u->xpad, cv.co, B, h, w, cv.wf, cv.ci, nullptr, 0, dx, nullptr, u->err, s) !=
+            cudaSuccess)
+            return unet_fail(ENSF_ECUDA, "unet implicit convolution launch (data gradient)");
+        return ENSF_OK;
+    }
     // data gradient: dZ [P][co] x W^T [kp][co] -> dcol [P][kp] -> col2im
     st = gemm(u, u->dz16, cv.wt, P, cv.kp, cv.co, u->gemm_c, s);
     if (st != ENSF_OK) return st;
@@ -662,6 +720,7 @@ ensf_status repack(ensf_unet *u, cudaStream_t s) {
         ensf_unet::Conv &cv = u->conv[l];
         k_repack<<<nb((int64_t)cv.co * cv.kp), 256, 0, s>>>(u->params + cv.w_off, cv.co, 9 * cv.ci, cv.kp, cv.wb,
                                                             cv.wt);
+        k_repack_flip<<<nb((int64_t)cv.co * 9 * cv.ci), 256, 0, s>>>(u->params + cv.w_off, cv.co, cv.ci, cv.wf);
     }
     UNET_LAUNCH();
     return ENSF_OK;
