@@ -94,15 +94,24 @@ def _traffic_record(kernel: str, workload: str, path: str, splits: int = 0, n: i
 
 def _traffic_for(kernel: str, p, args):
     """The recorded traffic, when this run launched the kernel in the shape it
-    was captured in: CTA-pair Gram on BF16 planes writing the next step's
-    noise, and W X in tiles of 256 particles."""
+    was captured in: the CTA-pair Gram on BF16 planes (with or without the
+    next step's noise written by its spare warps), W X in tiles of 256
+    particles (reading the noise slice, or with the TMA-staged epilogue
+    that draws the noise itself)."""
     t = args.tuning or {}
-    if kernel == "gram" and (t.get("gram_cta_pair") != 1 or t.get("gram_fp32_particles") or t.get("noise_inline")
-                             or args.inline_noise):
+    inline = bool(t.get("noise_inline") == 1 or args.inline_noise)
+    if kernel == "gram":
+        if t.get("gram_cta_pair") != 1 or t.get("gram_fp32_particles") or t.get("gram_fused_softmax") or \
+                t.get("noise_inline") == 2:
+            return None
+        tag = "gram_pair" if inline else "gram_pair_noise"
+    elif kernel == "wx_em":
+        if t.get("wx_tile_n") != 256 or t.get("noise_inline") == 2:
+            return None
+        tag = "wx_em_staged" if inline else "wx_em_slice"
+    else:
         return None
-    if kernel == "wx_em" and (t.get("wx_tile_n") != 256 or t.get("noise_inline") or args.inline_noise):
-        return None
-    return _traffic_record(kernel, p.name, args.path, t.get("gram_splits") or 0, p.n)
+    return _traffic_record(tag, p.name, args.path, t.get("gram_splits") or 0, p.n)
 
 
 class ClockSampler:
@@ -238,9 +247,10 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
     gram (Z X^T, 2 N^2 d FLOP algorithmic per launch; split-BF16x3 executes
     three BF16 products) is a dense contraction: tensor (or FP32 ALU) bound.
     wx_em (W X + score + Euler-Maruyama) moves per launch 8 N d bytes of
-    particle state (read + write), 4 N d of noise, 2 N d of X^T (BF16), and
-    4 N d of BF16 Z planes when the Gram runs on tensor cores: at N = 1024 its
-    2 N^2 d FLOP sit below the BF16 ridge, so it is HBM bound."""
+    particle state (read + write), 4 N d of noise when it reads a
+    pre-generated slice (none when it draws the noise itself), 2 N d of X^T
+    (BF16), and 4 N d of BF16 Z planes when the Gram runs on tensor cores: at
+    N = 1024 its 2 N^2 d FLOP sit below the BF16 ridge, so it is HBM bound."""
     launches, timed, tot_ms = rec
     avg_ms = tot_ms / timed
     n, d = p.n, p.d
@@ -248,8 +258,12 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
     prec = gram if kernel == "gram" else wx
     flops = 2.0 * n * nx * d
     if kernel == "wx_em" and prec != "fp32":
-        nbytes = ((8 + 4 + (4 if gram != "fp32" else 0)) * n * d + 2 * (2 if prec == "split" else 1) * nx * d
-                  + 5 * d)
+        # the noise slice is read only when the draws were made before W X;
+        # drawn in its epilogue they cost instructions, not bytes
+        t = args.tuning or {}
+        slice_read = not (t.get("noise_inline") == 1 or args.inline_noise)
+        nbytes = ((8 + (4 if slice_read else 0) + (4 if gram != "fp32" else 0)) * n * d
+                  + 2 * (2 if prec == "split" else 1) * nx * d + 5 * d)
         peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
         achieved = nbytes / (avg_ms / 1e3) / 1e9
         return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -266,6 +266,23 @@ cudaError_t prof_end(ensf_handle *h, cudaStream_t s) {
 // Gram + row softmax for particles z [n][d] against prior [n_x][d] at step
 // coefficients c.  Writes W FP32 into h->w when want_fp32, and the BF16
 // weight planes when the W X contraction runs on tensor cores.
+// The row softmax of Eq. 16 from split-K partials: rows of at least one
+// 256-column tile in the tiled form (one warp per row and tile; the form the
+// pair Gram's fused softmax shares), shorter rows with a block per row whose
+// threads also split the partial sums (a warp alone would sum every split of
+// its columns).
+cudaError_t row_softmax(ensf_handle *h, const float *partial, int splits, int64_t part_stride, int ldp, int n,
+                        int n_x, const double *norms, double alpha, double inv_2beta2, float *w, int ldw,
+                        __nv_bfloat16 *wb_hi, __nv_bfloat16 *wb_lo, int ldwb, cudaStream_t s, bool pdl) {
+    const Layout &L = h->L;
+    if (n_x < 256)
+        return ensf::launch_softmax_rows(partial, splits, part_stride, ldp, n, n_x, norms, alpha, inv_2beta2, w, ldw,
+                                         wb_hi, wb_lo, ldwb, s, pdl);
+    return ensf::launch_softmax_tiled(partial, splits, part_stride, ldp, n, n_x, norms, alpha, inv_2beta2,
+                                      h->ws + L.sm_L, h->at<float4>(L.sm_stats), h->at<int>(L.sm_cnt), w, ldw, wb_hi,
+                                      wb_lo, ldwb, s, pdl);
+}
+
 struct NoiseRequest {
     float *slice = nullptr;  // write xi[k] [n][d] here during the Gram (tensor-core Gram only)
     uint64_t seed = 0;
@@ -341,10 +358,9 @@ ensf_status gram_softmax(ensf_handle *h, const float *z, int n, const float *pri
         ldwb = (int)round_up(n_x, 8);
     }
     ENSF_LAUNCH(h, P_SOFTMAX, s,
-                ensf::launch_softmax_tiled(partial, splits, part_stride, ldp, n, n_x, h->at<double>(L.norms) + x0,
-                                           c.alpha_d, c.inv_2beta2_d, h->ws + L.sm_L, h->at<float4>(L.sm_stats),
-                                           h->at<int>(L.sm_cnt), want_fp32 ? h->at<float>(L.w) : nullptr, n_x,
-                                           wb_hi, wb_lo, ldwb, s, h->use_pdl(n, d)));
+                row_softmax(h, partial, splits, part_stride, ldp, n, n_x, h->at<double>(L.norms) + x0, c.alpha_d,
+                            c.inv_2beta2_d, want_fp32 ? h->at<float>(L.w) : nullptr, n_x, wb_hi, wb_lo, ldwb, s,
+                            h->use_pdl(n, d)));
     return ENSF_OK;
 }
 
@@ -701,13 +717,12 @@ ensf_status autotune_pass(ensf_handle *h, const float *prior, int n, int64_t d, 
     auto after = [](void *vp, int splits, int64_t part_stride, int ldp, cudaStream_t st, bool pdl) -> cudaError_t {
         const SoftmaxCtx &x = *static_cast<const SoftmaxCtx *>(vp);
         const Layout &L = x.h->L;
-        return ensf::launch_softmax_tiled(x.h->at<float>(L.partial), splits, part_stride, ldp, x.n, x.n,
-                                          x.h->at<double>(L.norms), x.c.alpha_d, x.c.inv_2beta2_d,
-                                          x.h->ws + L.sm_L, x.h->at<float4>(L.sm_stats), x.h->at<int>(L.sm_cnt),
-                                          x.tc_wx ? nullptr : x.h->at<float>(L.w), x.n,
-                                          x.tc_wx ? x.h->at<__nv_bfloat16>(L.wb_hi) : nullptr,
-                                          (x.tc_wx && L.wb_lo) ? x.h->at<__nv_bfloat16>(L.wb_lo) : nullptr,
-                                          (int)round_up(x.n, 8), st, pdl);
+        return row_softmax(x.h, x.h->at<float>(L.partial), splits, part_stride, ldp, x.n, x.n,
+                           x.h->at<double>(L.norms), x.c.alpha_d, x.c.inv_2beta2_d,
+                           x.tc_wx ? nullptr : x.h->at<float>(L.w), x.n,
+                           x.tc_wx ? x.h->at<__nv_bfloat16>(L.wb_hi) : nullptr,
+                           (x.tc_wx && L.wb_lo) ? x.h->at<__nv_bfloat16>(L.wb_lo) : nullptr, (int)round_up(x.n, 8),
+                           st, pdl);
     };
     cudaError_t e = ensf::tc_autotune(h->tc, tc_gram ? &ga : nullptr, tc_wx ? &wa : nullptr, h->sms, s, rep,
                                       tc_gram ? +after : nullptr, &sctx);
@@ -1171,10 +1186,9 @@ ensf_status ensf_shard_update(ensf_handle *h, const ensf_shard *sh, int k, const
     __nv_bfloat16 *wb_hi = tc_wx ? h->at<__nv_bfloat16>(L.wb_hi) : nullptr;
     __nv_bfloat16 *wb_lo = (tc_wx && L.wb_lo) ? h->at<__nv_bfloat16>(L.wb_lo) : nullptr;
     ENSF_LAUNCH(h, P_SOFTMAX, s,
-                ensf::launch_softmax_tiled(partials, splits_total, (int64_t)n * n, n, n, n, norms, c.alpha_d,
-                                           c.inv_2beta2_d, h->ws + L.sm_L, h->at<float4>(L.sm_stats),
-                                           h->at<int>(L.sm_cnt), tc_wx ? nullptr : h->at<float>(L.w), n, wb_hi,
-                                           wb_lo, (int)round_up(n, 8), s, h->use_pdl(n, d)));
+                row_softmax(h, partials, splits_total, (int64_t)n * n, n, n, n, norms, c.alpha_d, c.inv_2beta2_d,
+                            tc_wx ? nullptr : h->at<float>(L.w), n, wb_hi, wb_lo, (int)round_up(n, 8), s,
+                            h->use_pdl(n, d)));
     const bool gram_f32 =
         tc_gram && ensf::tc_gram_reads_fp32(h->tc, n, n, d, h->cfg.gram == ENSF_PREC_SPLIT_BF16X3);
     if (!tc_wx) {
