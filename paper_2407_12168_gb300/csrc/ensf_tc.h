@@ -153,13 +153,26 @@ cudaError_t launch_wx_em_tc_batched(const void *maps, const BWxItem *items, int 
 // cores: out[p][n] = sum_{dy, dx, c} xpad[b][y + dy][x + dx][c] wt[n][(dy * 3 + dx) * C + c]
 // (xpad: the BF16 NHWC input with a one-pixel circular halo, B x (h + 2) x (w + 2) x C;
 // wt: [N][9 C] BF16).  act = 1: out32 = sum + bias (the pre-activation),
-// out16 = SiLU of it; act = 0: out32 = the sum.  conv3x3_supported tells
+// out16 = SiLU of it; act = 0: out32 = the sum.  Either output may be NULL
+// (an inference forward keeps no pre-activation), not both.  conv3x3_supported tells
 // which shapes it takes (C a multiple of 32, N of 32 up to 512, whole image
 // rows per 128-pixel tile).
 bool conv3x3_supported(int C, int N, int h, int w, int P);
 cudaError_t launch_conv3x3(TcContext *ctx, const __nv_bfloat16 *xpad, int C, int B, int h, int w,
                            const __nv_bfloat16 *wt, int N, const float *bias, int act, float *out32,
                            __nv_bfloat16 *out16, int *err, cudaStream_t s);
+// The weight gradient of that convolution, dw[n][tap][c] (FP32, the flat
+// parameter layout [N][3][3][C]) = sum_p dZ[p][n] x[p shifted by the tap][c]:
+// dzT = dZ^T [N][P] BF16, xs = the input's three column-shifted, transposed,
+// row-haloed copies written by launch_shift3_transpose ([3][C][B (h + 2)][w]
+// BF16); split-K over the pixels into `partial` (at most partial_cap floats),
+// summed in a fixed order.
+bool conv3x3_wgrad_supported(int C, int N, int h, int w, int P);
+cudaError_t launch_shift3_transpose(const __nv_bfloat16 *x, int B, int h, int w, int C, __nv_bfloat16 *xs,
+                                    cudaStream_t s);
+cudaError_t launch_conv3x3_wgrad(TcContext *ctx, const __nv_bfloat16 *dzT, const __nv_bfloat16 *xs, int B, int h,
+                                 int w, int C, int N, float *partial, int64_t partial_cap, float *dw, int *err,
+                                 cudaStream_t s);
 // Host: the staging tensor map of the staged W X epilogue (rows x cols of
 // esize-byte elements, 128 x 16 boxes, no swizzle) into `out` (NULL base: zeroed).
 cudaError_t tc_encode_stage_map(TcContext *ctx, void *out128, const void *base, int esize, int64_t cols,

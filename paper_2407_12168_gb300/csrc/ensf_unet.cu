@@ -31,6 +31,8 @@ namespace {
 using bf16 = __nv_bfloat16;
 constexpr int kLevels = 3;
 constexpr int kConvs = 14;
+constexpr int kColsumBlocks = 1024;  // row blocks of the column sums (bias and head gradients)
+constexpr int kLossBlocks = 296;     // blocks of the loss reduction (two per SM)
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + __expf(-z)); }
 
@@ -132,35 +134,70 @@ __global__ void k_bias_silu(const float *__restrict__ c, const float *__restrict
 }
 
 // dZ = dY * silu'(z): FP32 (bias sums) and BF16 (GEMM operand) copies.
-__global__ void k_silu_back(const float *__restrict__ dy, const float *__restrict__ z, int64_t count,
-                            float *__restrict__ dz32, bf16 *__restrict__ dz16) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const float s = sigmoidf_(z[i]);
-    const float g = dy[i] * s * (1.f + z[i] * (1.f - s));
-    dz32[i] = g;
-    dz16[i] = __float2bfloat16_rn(g);
-}
-
-// Column sums of in [P][C] in two fixed-order stages: partial[blk][c] over
-// row chunks, then out[c] (+)= sum over blocks.
-__global__ void k_colsum_partial(const float *__restrict__ in, int64_t P, int C, int64_t rows_per_blk,
-                                 float *__restrict__ partial) {
-    const int c = threadIdx.x + blockIdx.y * blockDim.x;
-    if (c >= C) return;
+// dz = dy * SiLU'(z) as BF16 for the GEMMs and, per block of rows, the
+// column sums of dz (the bias gradient) in FP32: block (bx, by) covers rows
+// [bx * rows_per_blk, ...) and the columns [by * 256, by * 256 + Cg); thread t
+// takes column t % Cg of every (256 / Cg)-th row, and partial[bx][c] sums the
+// threads of a column in thread order (fixed order; k_colsum_final ends it).
+__global__ void __launch_bounds__(256) k_silu_back_colsum(const float *__restrict__ dy, const float *__restrict__ z,
+                                                          int64_t P, int C, int64_t rows_per_blk,
+                                                          bf16 *__restrict__ dz16, float *__restrict__ partial) {
+    __shared__ float red[256];
+    const int cb = blockIdx.y * 256;
+    const int Cg = min(256, C - cb);
+    const int R = 256 / Cg;
+    const int t = threadIdx.x, cl = t % Cg, j = t / Cg;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
     const int64_t r1 = r0 + rows_per_blk < P ? r0 + rows_per_blk : P;
     float acc = 0.f;
-    for (int64_t r = r0; r < r1; ++r) acc += in[r * C + c];
-    partial[(int64_t)blockIdx.x * C + c] = acc;
+    if (j < R) {
+        int64_t r = r0 + j;
+        // eight rows' loads in flight before their arithmetic and stores
+        for (; r + 7 * R < r1; r += 8 * R) {
+            float zv[8], dv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int64_t i = (r + k * R) * C + cb + cl;
+                zv[k] = z[i];
+                dv[k] = dy[i];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float sg = sigmoidf_(zv[k]);
+                const float g = dv[k] * sg * (1.f + zv[k] * (1.f - sg));
+                dz16[(r + k * R) * C + cb + cl] = __float2bfloat16_rn(g);
+                acc += g;
+            }
+        }
+        for (; r < r1; r += R) {
+            const int64_t i = r * C + cb + cl;
+            const float zz = z[i];
+            const float sg = sigmoidf_(zz);
+            const float g = dy[i] * sg * (1.f + zz * (1.f - sg));
+            dz16[i] = __float2bfloat16_rn(g);
+            acc += g;
+        }
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < Cg) {
+        float sum = 0.f;
+        for (int k = 0; k < R; ++k) sum += red[k * Cg + t];
+        partial[(int64_t)blockIdx.x * C + cb + t] = sum;
+    }
 }
 
+// out[c] = sum over blocks of partial[blk][c]: one warp per column, lane l
+// summing blocks l, l + 32, ..., then a fixed butterfly across the lanes.
 __global__ void k_colsum_final(const float *__restrict__ partial, int blocks, int C, float *__restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= C) return;  // whole warps
     float acc = 0.f;
-    for (int b = 0; b < blocks; ++b) acc += partial[(int64_t)b * C + c];
-    out[c] = acc;
+    for (int b = lane; b < blocks; b += 32) acc += partial[(int64_t)b * C + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[c] = acc;
 }
 
 __global__ void k_transpose_bf16(const bf16 *__restrict__ in, int64_t R, int C, bf16 *__restrict__ out) {
@@ -207,16 +244,20 @@ __global__ void k_pool_bwd(const float *__restrict__ dy, int B, int H, int W, in
 }
 
 // out[b][y][x] = [low upsampled (Cl channels), skip (Cs channels)]
+// out[p] = [nearest-upsampled low (Cl channels), skip (Cs channels)], eight
+// channels (16 bytes) per thread; Cl and Cs are multiples of 8.
 __global__ void k_up_concat_fwd(const bf16 *__restrict__ low, const bf16 *__restrict__ skip, int B, int H, int W,
                                 int Cl, int Cs, bf16 *__restrict__ out) {
-    const int Ct = Cl + Cs;
+    const int Ct8 = (Cl + Cs) / 8, Cl8 = Cl / 8, Cs8 = Cs / 8;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)B * H * W * Ct) return;
-    const int c = (int)(i % Ct);
-    const int64_t p = i / Ct;
+    if (i >= (int64_t)B * H * W * Ct8) return;
+    const int c8 = (int)(i % Ct8);
+    const int64_t p = i / Ct8;
     const int xx = (int)(p % W), yy = (int)((p / W) % H);
     const int64_t b = p / ((int64_t)W * H);
-    out[i] = c < Cl ? low[((b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * Cl + c] : skip[p * Cs + (c - Cl)];
+    reinterpret_cast<uint4 *>(out)[i] =
+        c8 < Cl8 ? reinterpret_cast<const uint4 *>(low)[((b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * Cl8 + c8]
+                 : reinterpret_cast<const uint4 *>(skip)[p * Cs8 + (c8 - Cl8)];
 }
 
 // Gradient of k_up_concat_fwd: dlow (coarse, sum of 4) and dskip (+=).
@@ -259,16 +300,39 @@ __global__ void k_head_fwd(const bf16 *__restrict__ d1, const float *__restrict_
 }
 
 // Loss gradient at the output (NHWC dout [P][O]) and per-pixel squared error.
-__global__ void k_mse_grad(const float *__restrict__ out, const float *__restrict__ tgt, int B, int O, int H, int W,
-                           float *__restrict__ dout, float *__restrict__ sq) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // NCHW index
+// Loss gradient and the loss's block partials: dout (NHWC) = 2 (out - tgt) /
+// count, and part[blk] = sum of the squared errors of the elements blk,
+// blk + gridDim.x * 256, ... taken by this block (FP32 squares summed in FP64,
+// thread partials then combined in thread order).
+__global__ void __launch_bounds__(256) k_mse_grad(const float *__restrict__ out, const float *__restrict__ tgt, int B,
+                                                  int O, int H, int W, float *__restrict__ dout,
+                                                  double *__restrict__ part) {
+    __shared__ double red[256];
     const int64_t total = (int64_t)B * O * H * W;
-    if (i >= total) return;
-    const int xx = (int)(i % W), yy = (int)((i / W) % H), o = (int)((i / ((int64_t)W * H)) % O);
-    const int64_t b = i / ((int64_t)W * H * O);
-    const float d = out[i] - tgt[i];
-    sq[i] = d * d;
-    dout[((b * H + yy) * W + xx) * O + o] = 2.f * d / (float)total;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int xx = (int)(i % W), yy = (int)((i / W) % H), o = (int)((i / ((int64_t)W * H)) % O);
+        const int64_t b = i / ((int64_t)W * H * O);
+        const float d = out[i] - tgt[i];
+        const float q = d * d;
+        acc += (double)q;
+        dout[((b * H + yy) * W + xx) * O + o] = 2.f * d / (float)total;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int k = 0; k < 256; ++k) sum += red[k];
+        part[blockIdx.x] = sum;
+    }
+}
+
+// loss = (sum of the block partials, in block order) / count
+__global__ void k_loss_final(const double *__restrict__ part, int blocks, int64_t count, double *__restrict__ loss) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double sum = 0.0;
+    for (int b = 0; b < blocks; ++b) sum += part[b];
+    *loss = sum / (double)count;
 }
 
 // dd1[p][c] = sum_o dout[p][o] Wh[o][c]
@@ -300,19 +364,6 @@ __global__ void k_head_dw_partial(const float *__restrict__ dout, const bf16 *__
         for (int64_t r = r0; r < r1; ++r) acc += dout[r * O + o];
     }
     partial[(int64_t)blockIdx.x * nj + j] = acc;
-}
-
-__global__ void k_sum_partial_f64(const float *__restrict__ v, int64_t count, double *__restrict__ out) {
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < count; i += 256) acc += (double)v[i];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = red[0] / (double)count;
 }
 
 // master W [Co][9Ci] -> Wb [Co][Kp] (zero padded) and Wt [Kp][Co]
@@ -375,13 +426,14 @@ struct ensf_unet {
     bf16 *pool[kLevels];       // pooled activations at levels 1..3
     bf16 *cat[kLevels];        // decoder concat buffers (levels 2, 1, 0)
     float *out;                // prediction NCHW
-    float *dout, *sq;          // loss gradient NHWC [P0][2], squared errors NCHW
+    float *dout;               // loss gradient NHWC [P0][2]
     double *loss;              // device scalar
     int *err;                  // device error word of the GEMM launches (ENSF_ETIMEOUT on an expired wait)
     // scratch
     bf16 *col, *colT, *dz16, *dzT;
     bf16 *xpad;                // a convolution's input with its circular halo (implicit GEMM)
-    float *gemm_c, *partial, *dz32, *ga, *gb, *colsum_part;
+    float *gemm_c, *partial, *ga, *gb, *colsum_part;
+    double *loss_part;         // block partials of the loss
     float *gskip[kLevels];     // gradients of the encoder outputs (skips), levels 0..2
     int64_t partial_cap = 0;
 };
@@ -459,8 +511,8 @@ size_t unet_layout(ensf_unet *u, const ensf_unet_config *c, char *base) {
     u->cat[2] = a.take<bf16>(P(0) * (w2 + w1));
     u->out = a.take<float>(P0 * 2);
     u->dout = a.take<float>(P0 * 2);
-    u->sq = a.take<float>(P0 * 2);
     u->loss = a.take<double>(1);
+    u->loss_part = a.take<double>(kLossBlocks);
     u->err = a.take<int>(4);
     {
         int64_t mx = 0;
@@ -476,7 +528,6 @@ size_t unet_layout(ensf_unet *u, const ensf_unet_config *c, char *base) {
     u->dz16 = a.take<bf16>(max_chan);
     u->dzT = a.take<bf16>(max_chan);
     u->gemm_c = a.take<float>(max_c);
-    u->dz32 = a.take<float>(max_chan);
     u->ga = a.take<float>(max_chan);
     u->gb = a.take<float>(max_chan);
     u->gskip[0] = a.take<float>(P(0) * w1);
@@ -543,17 +594,9 @@ ensf_status gemm(ensf_unet *u, const bf16 *A, const bf16 *B, int64_t M, int64_t 
     return ENSF_OK;
 }
 
-ensf_status colsum(ensf_unet *u, const float *in, int64_t P, int C, float *out, cudaStream_t s) {
-    const int blocks = (int)std::min<int64_t>(1024, (P + 255) / 256);
-    const int64_t rows = (P + blocks - 1) / blocks;
-    dim3 grid(blocks, (C + 127) / 128);
-    k_colsum_partial<<<grid, 128, 0, s>>>(in, P, C, rows, u->colsum_part);
-    k_colsum_final<<<nb(C, 128), 128, 0, s>>>(u->colsum_part, blocks, C, out);
-    UNET_LAUNCH();
-    return ENSF_OK;
-}
-
-ensf_status forward(ensf_unet *u, const float *x_nchw, int B, cudaStream_t s) {
+// keep_z: store the FP32 pre-activations the backward pass reads (an
+// inference forward of the implicit-GEMM convolutions skips them).
+ensf_status forward(ensf_unet *u, const float *x_nchw, int B, bool keep_z, cudaStream_t s) {
     const int H = u->cfg.height, W = u->cfg.width;
     const int w1 = u->cfg.widths[0], w2 = u->cfg.widths[1], w3 = u->cfg.widths[2], w4 = u->cfg.widths[3];
     const int64_t P0 = (int64_t)B * H * W;
@@ -568,8 +611,8 @@ ensf_status forward(ensf_unet *u, const float *x_nchw, int B, cudaStream_t s) {
             k_pad_circ<<<nb((int64_t)B * (h + 2) * (w + 2) * (cv.ci / 8)), 256, 0, s>>>(cv.in, B, h, w, cv.ci,
                                                                                          u->xpad);
             UNET_LAUNCH();
-            if (ensf::launch_conv3x3(u->tc, u->xpad, cv.ci, B, h, w, cv.wb, cv.co, u->params + cv.b_off, 1, cv.z,
-                                     cv.y, u->err, s) != cudaSuccess)
+            if (ensf::launch_conv3x3(u->tc, u->xpad, cv.ci, B, h, w, cv.wb, cv.co, u->params + cv.b_off, 1,
+                                     keep_z ? cv.z : nullptr, cv.y, u->err, s) != cudaSuccess)
                 return unet_fail(ENSF_ECUDA, "unet implicit convolution launch");
             return ENSF_OK;
         }
@@ -588,7 +631,7 @@ ensf_status forward(ensf_unet *u, const float *x_nchw, int B, cudaStream_t s) {
         return ENSF_OK;
     };
     auto upcat = [&](const bf16 *low, const bf16 *skip, int res, int Cl, int Cs, bf16 *out) -> ensf_status {
-        k_up_concat_fwd<<<nb((int64_t)B * (H >> res) * (W >> res) * (Cl + Cs)), 256, 0, s>>>(
+        k_up_concat_fwd<<<nb((int64_t)B * (H >> res) * (W >> res) * ((Cl + Cs) / 8)), 256, 0, s>>>(
             low, skip, B, H >> res, W >> res, Cl, Cs, out);
         UNET_LAUNCH();
         return ENSF_OK;
@@ -616,23 +659,40 @@ ensf_status conv_back(ensf_unet *u, int l, int B, const float *dy, float *dx, in
     ensf_unet::Conv &cv = u->conv[l];
     const int h = u->cfg.height >> cv.res, w = u->cfg.width >> cv.res;
     const int64_t P = (int64_t)B * h * w;
-    k_silu_back<<<nb(P * cv.co), 256, 0, s>>>(dy, cv.z, P * cv.co, u->dz32, u->dz16);
-    UNET_LAUNCH();
-    ensf_status st = colsum(u, u->dz32, P, cv.co, u->grads + cv.b_off, s);
-    if (st != ENSF_OK) return st;
-    // weight gradient: dZ^T [co][P] x col^T [kp][P]
-    k_im2col<<<nb(P * cv.kp), 256, 0, s>>>(cv.in, B, h, w, cv.ci, cv.kp, u->col);
-    UNET_LAUNCH();
-    k_transpose_bf16<<<dim3((cv.kp + 31) / 32, (unsigned)((P + 31) / 32)), dim3(32, 8), 0, s>>>(u->col, P, cv.kp,
-                                                                                              u->colT);
+    {
+        // dZ and the bias gradient (column sums of dZ) in one pass
+        const int blocks = (int)std::min<int64_t>(kColsumBlocks, (P + 255) / 256);
+        const int64_t rows = (P + blocks - 1) / blocks;
+        k_silu_back_colsum<<<dim3(blocks, (cv.co + 255) / 256), 256, 0, s>>>(dy, cv.z, P, cv.co, rows, u->dz16,
+                                                                             u->colsum_part);
+        k_colsum_final<<<(cv.co + 3) / 4, 128, 0, s>>>(u->colsum_part, blocks, cv.co, u->grads + cv.b_off);
+        UNET_LAUNCH();
+    }
+    ensf_status st;
     k_transpose_bf16<<<dim3((cv.co + 31) / 32, (unsigned)((P + 31) / 32)), dim3(32, 8), 0, s>>>(u->dz16, P, cv.co,
                                                                                               u->dzT);
     UNET_LAUNCH();
-    st = gemm(u, u->dzT, u->colT, cv.co, cv.kp, P, u->gemm_c, s);
-    if (st != ENSF_OK) return st;
-    k_unpad_grad<<<nb((int64_t)cv.co * 9 * cv.ci), 256, 0, s>>>(u->gemm_c, cv.co, 9 * cv.ci, cv.kp,
-                                                               u->grads + cv.w_off);
-    UNET_LAUNCH();
+    if (ensf::conv3x3_wgrad_supported(cv.ci, cv.co, h, w, (int)P)) {
+        // weight gradient as nine implicit GEMMs over the pixels: dZ^T against
+        // the input's column-shifted, transposed copies (held in the im2col
+        // scratch, which is 9 * P * ci >= 3 * B * (h + 2) * w * ci long)
+        if (ensf::launch_shift3_transpose(cv.in, B, h, w, cv.ci, u->col, s) != cudaSuccess ||
+            ensf::launch_conv3x3_wgrad(u->tc, u->dzT, u->col, B, h, w, cv.ci, cv.co, u->partial, u->partial_cap,
+                                       u->grads + cv.w_off, u->err, s) != cudaSuccess)
+            return unet_fail(ENSF_ECUDA, "unet implicit weight-gradient launch");
+    } else {
+        // weight gradient: dZ^T [co][P] x col^T [kp][P]
+        k_im2col<<<nb(P * cv.kp), 256, 0, s>>>(cv.in, B, h, w, cv.ci, cv.kp, u->col);
+        UNET_LAUNCH();
+        k_transpose_bf16<<<dim3((cv.kp + 31) / 32, (unsigned)((P + 31) / 32)), dim3(32, 8), 0, s>>>(u->col, P, cv.kp,
+                                                                                                  u->colT);
+        UNET_LAUNCH();
+        st = gemm(u, u->dzT, u->colT, cv.co, cv.kp, P, u->gemm_c, s);
+        if (st != ENSF_OK) return st;
+        k_unpad_grad<<<nb((int64_t)cv.co * 9 * cv.ci), 256, 0, s>>>(u->gemm_c, cv.co, 9 * cv.ci, cv.kp,
+                                                                   u->grads + cv.w_off);
+        UNET_LAUNCH();
+    }
     if (!dx) return ENSF_OK;
     if (!accumulate && ensf::conv3x3_supported(cv.co, cv.ci, h, w, (int)P)) {
         // the data gradient as the same implicit-GEMM convolution of the haloed dZ with mirrored taps
@@ -657,8 +717,8 @@ ensf_status backward(ensf_unet *u, const float *target, int B, cudaStream_t s) {
     const int w1 = u->cfg.widths[0], w2 = u->cfg.widths[1], w3 = u->cfg.widths[2], w4 = u->cfg.widths[3];
     const int64_t P0 = (int64_t)B * H * W;
     auto P = [&](int r) { return P0 >> (2 * r); };
-    k_mse_grad<<<nb(P0 * 2), 256, 0, s>>>(u->out, target, B, 2, H, W, u->dout, u->sq);
-    k_sum_partial_f64<<<1, 256, 0, s>>>(u->sq, P0 * 2, u->loss);
+    k_mse_grad<<<kLossBlocks, 256, 0, s>>>(u->out, target, B, 2, H, W, u->dout, u->loss_part);
+    k_loss_final<<<1, 32, 0, s>>>(u->loss_part, kLossBlocks, P0 * 2, u->loss);
     UNET_LAUNCH();
     // head
     {
@@ -667,7 +727,7 @@ ensf_status backward(ensf_unet *u, const float *target, int B, cudaStream_t s) {
         const int64_t rows = (P0 + blocks - 1) / blocks;
         k_head_dw_partial<<<dim3(blocks, (nj + 127) / 128), 128, 0, s>>>(u->dout, u->conv[13].y, P0, w1, 2, rows,
                                                                          u->colsum_part);
-        k_colsum_final<<<nb(nj, 128), 128, 0, s>>>(u->colsum_part, blocks, nj, u->grads + u->head_w_off);
+        k_colsum_final<<<(nj + 3) / 4, 128, 0, s>>>(u->colsum_part, blocks, nj, u->grads + u->head_w_off);
         k_head_dx<<<nb(P0 * w1), 256, 0, s>>>(u->dout, u->params + u->head_w_off, P0, w1, 2, u->ga);
         UNET_LAUNCH();
     }
@@ -815,7 +875,7 @@ ensf_status ensf_unet_forward(ensf_unet *u, const float *x, int batch, float *y,
     if (!u || !x || !y || batch < 1 || batch > u->cfg.max_batch)
         return unet_fail(ENSF_EINVAL, "ensf_unet_forward: bad arguments");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    ensf_status st = forward(u, x, batch, s);
+    ensf_status st = forward(u, x, batch, false, s);
     if (st != ENSF_OK) return st;
     UNET_CUDA(cudaMemcpyAsync(y, u->out, sizeof(float) * (size_t)batch * 2 * u->cfg.height * u->cfg.width,
                               cudaMemcpyDeviceToDevice, s));
@@ -827,7 +887,7 @@ ensf_status ensf_unet_gradients(ensf_unet *u, const float *x, const float *targe
     if (!u || !x || !target || batch < 1 || batch > u->cfg.max_batch)
         return unet_fail(ENSF_EINVAL, "ensf_unet_gradients: bad arguments");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    ensf_status st = forward(u, x, batch, s);
+    ensf_status st = forward(u, x, batch, true, s);
     if (st == ENSF_OK) st = backward(u, target, batch, s);
     if (st != ENSF_OK) return st;
     if (grads)

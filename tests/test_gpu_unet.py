@@ -123,14 +123,19 @@ def test_adamw_step_matches_oracle():
         w_prev, m_prev, v_prev = w_gpu, m_gpu, v_gpu
 
 
-@pytest.mark.parametrize("widths,grid", [((32, 32, 64, 64), 32), ((32, 64, 64, 96), 64)])
+@pytest.mark.parametrize("widths,grid", [((32, 32, 64, 64), 32), ((32, 64, 64, 96), 64),
+                                         ((32, 64, 128, 192), 128)])
 def test_implicit_convolutions_match_oracle(widths, grid):
     """Channel widths that are multiples of 32 run the 3x3 convolutions as
     implicit GEMMs (haloed input read tap by tap by TMA, bias and SiLU in the
     epilogue; the data gradients the same kernel with mirrored taps) wherever
-    a 128-pixel tile holds whole image rows; the smallest levels and the
-    2-channel input convolution keep the im2col form.  Output, loss and every
-    parameter gradient against the FP64 oracle at the BF16 bar."""
+    a 128-pixel tile holds whole image rows, and their weight gradients as
+    nine GEMMs over the pixels of column-shifted input copies wherever image
+    rows are at least 32 wide (32- and 64-pixel k-blocks; the 320-channel
+    decoder input of the third case in two channel tiles); the smallest
+    levels and the 2-channel input convolution keep the im2col form.  Output,
+    loss and every parameter gradient against the FP64 oracle at the BF16
+    bar."""
     import torch
     from paper_2407_12168_gb300 import ensf
     g = np.random.default_rng(9)
