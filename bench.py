@@ -305,27 +305,49 @@ def _roofline(kernel, rec, p, gram, wx, args, peaks):
             "executed_frac": executed / (avg_ms / 1e3) / 1e12 / peak}
 
 
-def _host_buffers(ensf, p, small_pages=False):
+def _cpu_nodes():
+    """NUMA nodes whose CPUs this process may run on (from sysfs)."""
+    import glob
+    try:
+        allowed = os.sched_getaffinity(0)
+    except AttributeError:
+        return None
+    nodes = []
+    for path in sorted(glob.glob("/sys/devices/system/node/node[0-9]*/cpulist")):
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            if part:
+                lo, _, hi = part.partition("-")
+                cpus.update(range(int(lo), int(hi or lo) + 1))
+        if cpus & allowed:
+            nodes.append(int(path.split("/node")[-1].split("/")[0]))
+    return nodes
+
+
+def _host_buffers(ensf, p, small_pages=False, any_node=False):
     """Page-locked host copies of the inputs and a host buffer for the result
-    (ensf_host_alloc: huge pages unless small_pages), and a record of how much
-    of them the kernel backs with huge pages."""
+    (ensf_host_alloc: huge pages unless small_pages, on the device's nearest
+    host NUMA node unless any_node), and a record of how much of them the
+    kernel backs with huge pages and where their pages sit."""
     import torch
-    huge = not small_pages
-    h_prior = ensf.host_empty(p.prior.shape, torch.float32, huge)
+    huge, near = not small_pages, not any_node
+    h_prior = ensf.host_empty(p.prior.shape, torch.float32, huge, near)
     h_prior.copy_(torch.from_numpy(p.prior))
-    h_y = ensf.host_empty(p.y.shape, torch.float32, huge)
+    h_y = ensf.host_empty(p.y.shape, torch.float32, huge, near)
     h_y.copy_(torch.from_numpy(p.y))
     h_mask = None
     if p.mask is not None:
-        h_mask = ensf.host_empty(p.mask.shape, torch.uint8, huge)
+        h_mask = ensf.host_empty(p.mask.shape, torch.uint8, huge, near)
         h_mask.copy_(torch.from_numpy(p.mask))
-    h_out = ensf.host_empty(p.prior.shape, torch.float32, huge)
-    rec = {"alloc": "ensf_host_alloc" + ("" if huge else " (small pages)")}
+    h_out = ensf.host_empty(p.prior.shape, torch.float32, huge, near)
+    rec = {"alloc": "ensf_host_alloc" + ("" if huge else " (small pages)") + ("" if near else " (any node)")}
     try:
         rec["huge_page_fraction"] = {"prior": round(ensf.host_huge_fraction(h_prior), 3),
                                      "out": round(ensf.host_huge_fraction(h_out), 3)}
     except Exception as e:  # no smaps: the buffers are still page-locked
         rec["huge_page_fraction"] = str(e)
+    (n_prior, dev_node), (n_out, _) = ensf.host_numa(h_prior), ensf.host_numa(h_out)
+    rec["numa"] = {"prior": n_prior, "out": n_out, "device_nearest": dev_node, "process_cpus_on": _cpu_nodes()}
     return h_prior, h_y, h_mask, h_out, rec
 
 
@@ -497,7 +519,7 @@ def run_ours(args):
     # result, backed by huge pages (ensf_host_alloc; buffers pinned page by
     # page copied 3-6x slower right after an analysis on a host that had been
     # busy) ----
-    h_prior, h_y, h_mask, h_out, host_huge = _host_buffers(ensf, p, args.small_pages)
+    h_prior, h_y, h_mask, h_out, host_huge = _host_buffers(ensf, p, args.small_pages, args.any_node)
     d_prior, d_y = torch.empty_like(prior), torch.empty_like(y)
     d_mask = torch.empty_like(mask) if mask is not None else None
     # sequential end-to-end steps (copy in, analyse, copy out, the host takes
@@ -774,7 +796,7 @@ def run_sharded(args):
     sl = types.SimpleNamespace(prior=np.ascontiguousarray(p.prior[:, c0:c0 + dl]),
                                y=np.ascontiguousarray(p.y[c0:c0 + dl]),
                                mask=None if p.mask is None else np.ascontiguousarray(p.mask[c0:c0 + dl]))
-    h_prior, h_y, h_mask, h_out, host_huge = _host_buffers(ensf, sl, args.small_pages)
+    h_prior, h_y, h_mask, h_out, host_huge = _host_buffers(ensf, sl, args.small_pages, args.any_node)
     d_prior, d_y = torch.empty_like(prior), torch.empty_like(y)
     d_mask = torch.empty_like(mask) if mask is not None else None
     e2e_steps = max(1, min(args.steps, 3))
@@ -905,6 +927,8 @@ def main(argv=None):
                          "filter split along d over the GPUs")
     ap.add_argument("--sharded", action="store_true",
                     help="the d-sharded mode also on one GPU (under torchrun: exercises the NCCL exchange)")
+    ap.add_argument("--any-node", action="store_true",
+                    help="host buffers without the preference for the device's nearest NUMA node (comparison)")
     ap.add_argument("--small-pages", action="store_true",
                     help="end-to-end host buffers pinned without huge pages (for comparison)")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)

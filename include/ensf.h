@@ -504,11 +504,16 @@ ensf_status ensf_unet_destroy(ensf_unet *u);
  * anonymous mapping aligned to the transparent-huge-page size and advised and
  * collapsed into huge pages before registration with the CUDA driver (each
  * best effort: where the kernel offers no huge pages the buffer is still
- * page-locked).  flags: 0, or ENSF_HOST_SMALL_PAGES to skip the huge-page
- * advice (for comparisons).  The memory is zeroed.  Release with
- * ensf_host_free.  ENSF_EINVAL (bytes 0, out NULL), ENSF_ENOMEM (mmap),
- * ENSF_ECUDA (registration). */
+ * page-locked).  Its pages are placed, before the first touch, with a
+ * preference for the host NUMA node closest to the current device
+ * (cudaDevAttrHostNumaId; on a two-socket host the far socket's memory is
+ * reached over the inter-socket link too); a full node falls back to others.
+ * flags: 0, or ENSF_HOST_SMALL_PAGES to skip the huge-page advice and
+ * ENSF_HOST_ANY_NODE to skip the node preference (for comparisons).  The
+ * memory is zeroed.  Release with ensf_host_free.  ENSF_EINVAL (bytes 0, out
+ * NULL), ENSF_ENOMEM (mmap), ENSF_ECUDA (registration). */
 #define ENSF_HOST_SMALL_PAGES 1u
+#define ENSF_HOST_ANY_NODE 2u
 ensf_status ensf_host_alloc(size_t bytes, unsigned flags, void **out);
 /* Unregister and unmap a buffer of ensf_host_alloc (NULL: no-op). */
 ensf_status ensf_host_free(void *ptr);
@@ -523,6 +528,10 @@ ensf_status ensf_host_registered(const void *ptr, int *registered);
 /* Share of [ptr, ptr + bytes) that the kernel backs with huge pages right
  * now (from /proc/self/smaps; ENSF_EUNSUPPORTED where that is unreadable). */
 ensf_status ensf_host_huge_fraction(const void *ptr, size_t bytes, double *fraction);
+/* *node = the NUMA node holding the page at ptr (-1 when unknown or not yet
+ * touched); *device_node = the host NUMA node closest to the current device
+ * (-1 when the system reports none). */
+ensf_status ensf_host_numa(const void *ptr, int *node, int *device_node);
 
 /* Wait for `stream` and return the handle's recorded device error, clearing it. */
 ensf_status ensf_status_sync(ensf_handle *h, void *stream);

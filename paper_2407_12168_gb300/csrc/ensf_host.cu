@@ -10,6 +10,13 @@
 // these buffers are anonymous mappings aligned to the huge-page size, advised
 // as huge pages (and collapsed into them where the kernel supports it) before
 // they are registered with the CUDA driver as page-locked memory.
+//
+// On a host with several NUMA nodes (two Grace sockets, each with its own
+// memory and GPUs) a buffer whose pages sit on the far socket is reached over
+// the inter-socket link as well: the pages are placed, before the first
+// touch, with a preference (MPOL_PREFERRED, so a full node falls back to the
+// others instead of failing) for the host node the CUDA driver reports as the
+// device's closest.
 #include <cerrno>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +24,7 @@
 #include <unordered_map>
 
 #include <sys/mman.h>
+#include <sys/syscall.h>
 #include <unistd.h>
 
 #include <cuda_runtime.h>
@@ -52,6 +60,31 @@ size_t huge_page_bytes() {
         fclose(f);
     }
     return hp ? hp : (size_t(2) << 20);
+}
+
+// Memory-policy constants of the Linux system calls (linux/mempolicy.h).
+constexpr int kMpolPreferred = 1;
+constexpr unsigned long kMpolFNode = 1, kMpolFAddr = 2;
+constexpr int kMaxNodes = 1024;
+constexpr int kMaskWords = kMaxNodes / (8 * static_cast<int>(sizeof(unsigned long)));
+
+// Host NUMA node closest to the current device, or -1 (no NUMA, or unknown).
+int device_host_node() {
+    int dev = 0, id = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&id, cudaDevAttrHostNumaId, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return id;
+}
+
+// Prefer `node` for the not yet touched pages of [addr, addr + len).
+bool prefer_node(void *addr, size_t len, int node) {
+    if (node < 0 || node >= kMaxNodes) return false;
+    unsigned long mask[kMaskWords] = {0};
+    const int bits = 8 * static_cast<int>(sizeof(unsigned long));
+    mask[node / bits] |= 1UL << (node % bits);
+    return syscall(SYS_mbind, addr, len, kMpolPreferred, mask, static_cast<unsigned long>(kMaxNodes) + 1, 0UL) == 0;
 }
 
 ensf_status host_fail(ensf_status s, const char *msg) {
@@ -92,6 +125,7 @@ ensf_status ensf_host_alloc(size_t bytes, unsigned flags, void **out) {
     if (!(flags & ENSF_HOST_SMALL_PAGES)) {
         madvise(base, len, MADV_HUGEPAGE);  // best effort: the kernel may not offer huge pages
     }
+    if (!(flags & ENSF_HOST_ANY_NODE)) prefer_node(base, len, device_host_node());  // best effort
     // touch every page now (with huge pages advised, each first touch of a
     // huge-page range faults in a whole huge page)
     const long pg = sysconf(_SC_PAGESIZE) > 0 ? sysconf(_SC_PAGESIZE) : 4096;
@@ -161,6 +195,15 @@ ensf_status ensf_host_registered(const void *ptr, int *registered) {
         return ENSF_OK;
     }
     *registered = attr.type == cudaMemoryTypeHost ? 1 : 0;
+    return ENSF_OK;
+}
+
+ensf_status ensf_host_numa(const void *ptr, int *node, int *device_node) {
+    if (!ptr || !node || !device_node) return host_fail(ENSF_EINVAL, "ensf_host_numa: NULL argument");
+    *device_node = device_host_node();
+    int nd = -1;
+    if (syscall(SYS_get_mempolicy, &nd, nullptr, 0UL, const_cast<void *>(ptr), kMpolFNode | kMpolFAddr) != 0) nd = -1;
+    *node = nd;
     return ENSF_OK;
 }
 

@@ -2051,7 +2051,8 @@ k_conv3x3(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUt
     if (*reinterpret_cast<volatile int *>(p.err) != 0) return;
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     uint8_t *tiles = smem_raw + pad;
-    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
+    const int sstride = P::kA + BN * kConvKB * 2;  // stage bytes for this BN (a multiple of 1024)
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + sstride * kConvStages);
     uint64_t *empty = full + kConvStages;
     uint64_t *accum = empty + kConvStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
@@ -2083,7 +2084,7 @@ k_conv3x3(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUt
                 const int s = kb % kConvStages;
                 const uint32_t ph = (kb / kConvStages) & 1;
                 if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) break;
-                const uint32_t st = smem_u32(tiles + s * P::kStage);
+                const uint32_t st = smem_u32(tiles + s * sstride);
                 mbar_expect_tx(&full[s], stage_bytes);
                 const int tap = kb / p.cblk, cb = kb % p.cblk;
                 tma_load_3d(st, &a_map, &full[s], cb * kConvKB, tap % 3, img * p.hp + y0 + tap / 3);
@@ -2107,7 +2108,7 @@ k_conv3x3(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUt
                 const uint32_t ph = (kb / kConvStages) & 1;
                 if (!mbar_wait(&full[s], ph, abort_flag, p.err)) break;
                 tc_fence_after();
-                const uint32_t a = smem_u32(tiles + s * P::kStage);
+                const uint32_t a = smem_u32(tiles + s * sstride);
                 const uint32_t b = a + P::kA;
 #pragma unroll
                 for (int kk = 0; kk < kConvKB / 16; ++kk)
@@ -2212,7 +2213,8 @@ k_conv3x3_wgrad(const __grid_constant__ CUtensorMap a_map, const __grid_constant
     if (*reinterpret_cast<volatile int *>(p.err) != 0) return;
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     uint8_t *tiles = smem_raw + pad;
-    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + P::kBarOff);
+    const int sstride = P::kA + p.BNc * KB * 2;  // stage bytes for this channel tile (a multiple of 1024)
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + sstride * NST);
     uint64_t *empty = full + NST;
     uint64_t *accum = empty + NST;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
@@ -2249,7 +2251,7 @@ k_conv3x3_wgrad(const __grid_constant__ CUtensorMap a_map, const __grid_constant
                 const int s = i % NST;
                 const uint32_t ph = (i / NST) & 1;
                 if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) break;
-                const uint32_t st = smem_u32(tiles + s * P::kStage);
+                const uint32_t st = smem_u32(tiles + s * sstride);
                 mbar_expect_tx(&full[s], stage_bytes);
                 const int pix = (kb0 + i) * KB;
                 const int img = pix / (p.h * p.w), y = (pix / p.w) % p.h, x0 = pix % p.w;
@@ -2274,7 +2276,7 @@ k_conv3x3_wgrad(const __grid_constant__ CUtensorMap a_map, const __grid_constant
                 const uint32_t ph = (i / NST) & 1;
                 if (!mbar_wait(&full[s], ph, abort_flag, p.err)) break;
                 tc_fence_after();
-                const uint32_t a = smem_u32(tiles + s * P::kStage);
+                const uint32_t a = smem_u32(tiles + s * sstride);
                 const uint32_t b = a + P::kA;
 #pragma unroll
                 for (int kk = 0; kk < KB / 16; ++kk)
@@ -2754,9 +2756,12 @@ cudaError_t launch_conv3x3(TcContext *ctx, const __nv_bfloat16 *xpad, int C, int
     prm.err = err;
     uint32_t cols = 32;
     while (static_cast<int>(cols) < BN) cols <<= 1;
+    // shared memory sized for this BN: narrow layers fit two or three CTAs per
+    // SM, so one CTA's epilogue overlaps another's loads and MMAs
+    const int smem = (ConvPlan::kA + BN * kConvKB * 2) * kConvStages + 256 + 1024;
     cudaError_t e = set_smem(k_conv3x3, ConvPlan::kBytes);
     if (e != cudaSuccess) return e;
-    k_conv3x3<<<dim3(P / BM, (N + BN - 1) / BN), 192, ConvPlan::kBytes, s>>>(am, bm, prm, BN, cols);
+    k_conv3x3<<<dim3(P / BM, (N + BN - 1) / BN), 192, smem, s>>>(am, bm, prm, BN, cols);
     return cudaGetLastError();
 }
 
@@ -2847,12 +2852,15 @@ cudaError_t launch_conv3x3_wgrad(TcContext *ctx, const __nv_bfloat16 *dzT, const
     while (static_cast<int>(cols) < BNc) cols <<= 1;
     cudaError_t e;
     dim3 grid(base, S);
+    // shared memory sized for this channel tile (several CTAs per SM when narrow)
+    const int smem = (BM * KB * 2 + BNc * KB * 2) * (KB == 64 ? WgradPlan<64>::kStages : WgradPlan<32>::kStages) +
+                     256 + 1024;
     if (KB == 64) {
         if ((e = set_smem(k_conv3x3_wgrad<64>, WgradPlan<64>::kBytes)) != cudaSuccess) return e;
-        k_conv3x3_wgrad<64><<<grid, 192, WgradPlan<64>::kBytes, s>>>(am, bm, prm, cols);
+        k_conv3x3_wgrad<64><<<grid, 192, smem, s>>>(am, bm, prm, cols);
     } else {
         if ((e = set_smem(k_conv3x3_wgrad<32>, WgradPlan<32>::kBytes)) != cudaSuccess) return e;
-        k_conv3x3_wgrad<32><<<grid, 192, WgradPlan<32>::kBytes, s>>>(am, bm, prm, cols);
+        k_conv3x3_wgrad<32><<<grid, 192, smem, s>>>(am, bm, prm, cols);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t total = static_cast<int64_t>(N) * 9 * C;

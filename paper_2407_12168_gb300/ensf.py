@@ -165,6 +165,7 @@ _SIGNATURES = [
                                     ctypes.c_void_p]),
     ("ensf_host_registered", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("ensf_host_huge_fraction", ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
+    ("ensf_host_numa", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("ensf_status_sync", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ensf_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("ensf_last_error", ctypes.c_char_p, []),
@@ -607,12 +608,14 @@ def _same_device(ref, **others):
 
 
 HOST_SMALL_PAGES = 1
+HOST_ANY_NODE = 2
 
 
-def host_empty(shape, dtype=None, huge_pages: bool = True):
+def host_empty(shape, dtype=None, huge_pages: bool = True, near_device: bool = True):
     """A page-locked host tensor from ensf_host_alloc: backed by huge pages
     (where the kernel offers them) so that copies to and from the device keep
-    their speed right after large kernels.  Zeroed; freed when the tensor is
+    their speed right after large kernels, and placed on the host NUMA node
+    closest to the current device.  Zeroed; freed when the tensor is
     garbage-collected."""
     import weakref
 
@@ -627,7 +630,8 @@ def host_empty(shape, dtype=None, huge_pages: bool = True):
     nbytes = max(count * itemsize, 1)
     lib = load()
     ptr = ctypes.c_void_p()
-    _check(lib.ensf_host_alloc(nbytes, 0 if huge_pages else HOST_SMALL_PAGES, ctypes.byref(ptr)), "ensf_host_alloc")
+    flags = (0 if huge_pages else HOST_SMALL_PAGES) | (0 if near_device else HOST_ANY_NODE)
+    _check(lib.ensf_host_alloc(nbytes, flags, ctypes.byref(ptr)), "ensf_host_alloc")
     raw = (ctypes.c_uint8 * nbytes).from_address(ptr.value)
     t = torch.from_numpy(np.ctypeslib.as_array(raw)).view(dtype)[:count].view(shape)
     weakref.finalize(t, lib.ensf_host_free, ctypes.c_void_p(ptr.value))
@@ -658,6 +662,14 @@ def host_huge_fraction(t) -> float:
     _check(load().ensf_host_huge_fraction(t.data_ptr(), t.numel() * t.element_size(), ctypes.byref(frac)),
            "ensf_host_huge_fraction")
     return float(frac.value)
+
+
+def host_numa(t):
+    """(NUMA node of the page holding the tensor's first byte, host node
+    closest to the current device); -1 where unknown."""
+    node, dev_node = ctypes.c_int(-1), ctypes.c_int(-1)
+    _check(load().ensf_host_numa(t.data_ptr(), ctypes.byref(node), ctypes.byref(dev_node)), "ensf_host_numa")
+    return int(node.value), int(dev_node.value)
 
 
 def weights_static(z, prior, t: float, eps: float, out=None, stream=None):

@@ -104,3 +104,20 @@ def test_sm_copy_kernel_moves_host_and_device_bytes():
         ensf.copy_sm(d[:5], src[:6])
     st = ensf.load().ensf_copy_sm(d.data_ptr() + 4, src.data_ptr(), 16, 1, None)
     assert st == ensf.EINVAL
+
+
+def test_host_buffer_sits_on_the_devices_nearest_node():
+    """ensf_host_alloc places a buffer's pages on the host NUMA node the
+    driver reports as closest to the device (where it reports one), and the
+    query answers for buffers placed either way."""
+    import torch
+    from paper_2407_12168_gb300 import ensf
+    torch.cuda.init()
+    near = ensf.host_empty((1 << 20,), torch.float32)
+    anyn = ensf.host_empty((1 << 20,), torch.float32, near_device=False)
+    node, dev_node = ensf.host_numa(near)
+    node_any, dev_node2 = ensf.host_numa(anyn)
+    assert dev_node == dev_node2
+    assert node >= -1 and node_any >= -1
+    if dev_node >= 0 and node >= 0:
+        assert node == dev_node, (node, dev_node)
