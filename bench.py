@@ -73,13 +73,17 @@ def _peaks():
 
 def _traffic_record(kernel: str, workload: str, path: str, splits: int = 0, n: int = 0):
     """DRAM traffic per launch from a committed ncu summary, valid only while
-    the kernel source is unchanged (sha256 recorded beside the number)."""
+    the kernel source is unchanged (sha256 of the kernel file and its PTX
+    wrappers, recorded beside the number)."""
     fn = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(fn):
         return None
-    src = os.path.join(ROOT, "paper_2407_12168_gb300", "csrc",
-                       "ensf_simt.cu" if path == "fp32" else "ensf_tc.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2407_12168_gb300", "csrc")
+    srcs = ["ensf_simt.cu"] if path == "fp32" else ["ensf_tc.cu", "ensf_ptx.cuh"]
+    h = hashlib.sha256()
+    for f in srcs:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    sha = h.hexdigest()[:16]
     for line in open(fn):
         m = re.match(r"^traffic\s+(\S+)\s+(\S+)\s+(\S+)\s+(\S+)\s+bytes_per_launch=(\d+)(?:\s+splits=(\d+))?",
                      line)

@@ -17,9 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libensf.so")
-SOURCES = ["ensf_api.cu", "ensf_simt.cu", "ensf_tc.cu", "ensf_static.cu", "ensf_sqg.cu", "ensf_unet.cu",
-           "ensf_small.cu", "ensf_host.cu"]
-HEADERS = ["ensf_device.cuh", "ensf_internal.h", "ensf_tc.h"]
+SOURCES = ["ensf_api.cu", "ensf_simt.cu", "ensf_tc.cu", "ensf_conv.cu", "ensf_static.cu", "ensf_sqg.cu",
+           "ensf_unet.cu", "ensf_small.cu", "ensf_host.cu"]
+HEADERS = ["ensf_device.cuh", "ensf_internal.h", "ensf_tc.h", "ensf_ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
