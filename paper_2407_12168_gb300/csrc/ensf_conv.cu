@@ -386,8 +386,10 @@ __global__ void __launch_bounds__(256) k_shift3_transpose(const __nv_bfloat16 *_
 }  // namespace
 
 bool conv3x3_supported(int C, int N, int h, int w, int P) {
-    return C % kConvKB == 0 && C > 0 && N % 32 == 0 && N > 0 && N <= 512 && w <= BM && BM % w == 0 &&
-           (BM / w) <= h && h % (BM / w) == 0 && P % BM == 0;
+    // output tiles of N (<= 256) or N / 2 channels, a multiple of 32 either way:
+    // the epilogue drains the accumulator 32 columns at a time
+    return C % kConvKB == 0 && C > 0 && N % 32 == 0 && N > 0 && N <= 512 && (N <= 256 || N % 64 == 0) &&
+           w <= BM && BM % w == 0 && (BM / w) <= h && h % (BM / w) == 0 && P % BM == 0;
 }
 
 cudaError_t launch_conv3x3(TcContext *ctx, const __nv_bfloat16 *xpad, int C, int B, int h, int w,

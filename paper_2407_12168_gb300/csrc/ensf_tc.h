@@ -155,8 +155,8 @@ cudaError_t launch_wx_em_tc_batched(const void *maps, const BWxItem *items, int 
 // wt: [N][9 C] BF16).  act = 1: out32 = sum + bias (the pre-activation),
 // out16 = SiLU of it; act = 0: out32 = the sum.  Either output may be NULL
 // (an inference forward keeps no pre-activation), not both.  conv3x3_supported tells
-// which shapes it takes (C a multiple of 32, N of 32 up to 512, whole image
-// rows per 128-pixel tile).
+// which shapes it takes (C a multiple of 32; N a multiple of 32 up to 256, or
+// of 64 up to 512; whole image rows per 128-pixel tile).
 bool conv3x3_supported(int C, int N, int h, int w, int P);
 cudaError_t launch_conv3x3(TcContext *ctx, const __nv_bfloat16 *xpad, int C, int B, int h, int w,
                            const __nv_bfloat16 *wt, int N, const float *bias, int act, float *out32,

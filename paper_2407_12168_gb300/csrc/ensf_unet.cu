@@ -92,17 +92,30 @@ __global__ void k_col2im(const float *__restrict__ dcol, int B, int H, int W, in
 
 // xp[b][yy][xx][c] = x[b][(yy - 1) mod h][(xx - 1) mod w][c]: the input of an
 // implicit-GEMM convolution with its one-pixel circular halo; 8 channels per thread.
+// I: the index type (32-bit where the element count allows: its divisions
+// are several times cheaper than 64-bit ones).
+template <class I>
 __global__ void k_pad_circ(const bf16 *__restrict__ x, int B, int h, int w, int C, bf16 *__restrict__ xp) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over B (h + 2) (w + 2) C / 8
-    const int c8 = C / 8;
-    const int64_t total = (int64_t)B * (h + 2) * (w + 2) * c8;
+    const I i = (I)blockIdx.x * blockDim.x + threadIdx.x;  // over B (h + 2) (w + 2) C / 8
+    const I c8 = C / 8;
+    const I total = (I)B * (h + 2) * (w + 2) * c8;
     if (i >= total) return;
-    const int cv = (int)(i % c8);
-    const int64_t pp = i / c8;
-    const int xx = (int)(pp % (w + 2)), yy = (int)((pp / (w + 2)) % (h + 2));
-    const int64_t b = pp / ((int64_t)(w + 2) * (h + 2));
-    const int sy = (yy - 1 + h) % h, sx = (xx - 1 + w) % w;
+    const I cv = i % c8;
+    const I pp = i / c8;
+    const I xx = pp % (I)(w + 2), yy = (pp / (I)(w + 2)) % (I)(h + 2);
+    const I b = pp / ((I)(w + 2) * (h + 2));
+    const I sy = yy == 0 ? h - 1 : (yy == (I)h + 1 ? 0 : yy - 1);
+    const I sx = xx == 0 ? w - 1 : (xx == (I)w + 1 ? 0 : xx - 1);
     reinterpret_cast<uint4 *>(xp)[i] = reinterpret_cast<const uint4 *>(x)[((b * h + sy) * w + sx) * c8 + cv];
+}
+
+// The haloed copy of x for the implicit convolutions.
+void pad_circ(const bf16 *x, int B, int h, int w, int C, bf16 *xp, cudaStream_t s) {
+    const int64_t total = (int64_t)B * (h + 2) * (w + 2) * (C / 8);
+    if (total < ((int64_t)1 << 31))
+        k_pad_circ<uint32_t><<<nb(total), 256, 0, s>>>(x, B, h, w, C, xp);
+    else
+        k_pad_circ<int64_t><<<nb(total), 256, 0, s>>>(x, B, h, w, C, xp);
 }
 
 // Weights of the data gradient: wf[c][tap'][n] = W[n][8 - tap'][c] (the taps
@@ -133,7 +146,6 @@ __global__ void k_bias_silu(const float *__restrict__ c, const float *__restrict
     y[i] = __float2bfloat16_rn(zz * sigmoidf_(zz));
 }
 
-// dZ = dY * silu'(z): FP32 (bias sums) and BF16 (GEMM operand) copies.
 // dz = dy * SiLU'(z) as BF16 for the GEMMs and, per block of rows, the
 // column sums of dz (the bias gradient) in FP32: block (bx, by) covers rows
 // [bx * rows_per_blk, ...) and the columns [by * 256, by * 256 + Cg); thread t
@@ -243,7 +255,6 @@ __global__ void k_pool_bwd(const float *__restrict__ dy, int B, int H, int W, in
     dx[i] = accumulate ? dx[i] + g : g;
 }
 
-// out[b][y][x] = [low upsampled (Cl channels), skip (Cs channels)]
 // out[p] = [nearest-upsampled low (Cl channels), skip (Cs channels)], eight
 // channels (16 bytes) per thread; Cl and Cs are multiples of 8.
 __global__ void k_up_concat_fwd(const bf16 *__restrict__ low, const bf16 *__restrict__ skip, int B, int H, int W,
@@ -299,7 +310,6 @@ __global__ void k_head_fwd(const bf16 *__restrict__ d1, const float *__restrict_
     }
 }
 
-// Loss gradient at the output (NHWC dout [P][O]) and per-pixel squared error.
 // Loss gradient and the loss's block partials: dout (NHWC) = 2 (out - tgt) /
 // count, and part[blk] = sum of the squared errors of the elements blk,
 // blk + gridDim.x * 256, ... taken by this block (FP32 squares summed in FP64,
@@ -327,12 +337,110 @@ __global__ void __launch_bounds__(256) k_mse_grad(const float *__restrict__ out,
     }
 }
 
-// loss = (sum of the block partials, in block order) / count
+// loss = (sum of the block partials) / count: one warp, lane l summing
+// blocks l, l + 32, ..., then a fixed butterfly across the lanes.
 __global__ void k_loss_final(const double *__restrict__ part, int blocks, int64_t count, double *__restrict__ loss) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     double sum = 0.0;
-    for (int b = 0; b < blocks; ++b) sum += part[b];
-    *loss = sum / (double)count;
+    for (int b = threadIdx.x; b < blocks; b += 32) sum += part[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (threadIdx.x == 0) *loss = sum / (double)count;
+}
+
+// The 2-channel input convolution, direct: a warp per pixel, lane = output
+// channel n0 + lane (coalesced stores); the 18 inputs of the pixel are read
+// once per warp (broadcast), the BF16 weights [k][n] sit in shared memory as
+// floats; 18 products accumulated in FP32 in (tap, c) order, then the bias,
+// z (FP32, if kept) and y = SiLU(z) (BF16).  Grid: x over 8-pixel blocks of
+// an image row, y over image rows (b, y) with a stride loop, z over groups
+// of 32 output channels.
+constexpr int kInCh = 2;
+constexpr int kInK = 9 * kInCh;
+__global__ void __launch_bounds__(256) k_conv_in_fwd(const bf16 *__restrict__ x, int B, int H, int W,
+                                                     const bf16 *__restrict__ wb, int Co, int Kp,
+                                                     const float *__restrict__ bias, float *__restrict__ z,
+                                                     bf16 *__restrict__ y) {
+    __shared__ float wsm[kInK][32];
+    const int n0 = blockIdx.z * 32, lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < kInK * 32; t += blockDim.x) {
+        const int k = t / 32, n = n0 + t % 32;
+        wsm[k][t % 32] = n < Co ? __bfloat162float(wb[(int64_t)n * Kp + k]) : 0.f;
+    }
+    __syncthreads();
+    const int xx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (xx >= W) return;
+    const int n = n0 + lane;
+    for (int row = blockIdx.y; row < B * H; row += gridDim.y) {
+        const int b = row / H, yy = row - b * H;
+        float acc = 0.f;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+            sy = sy < 0 ? sy + H : (sy >= H ? sy - H : sy);
+            sx = sx < 0 ? sx + W : (sx >= W ? sx - W : sx);
+            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(
+                x + (((int64_t)b * H + sy) * W + sx) * kInCh);
+            acc = __fmaf_rn(__low2float(v), wsm[tap * kInCh][lane], acc);
+            acc = __fmaf_rn(__high2float(v), wsm[tap * kInCh + 1][lane], acc);
+        }
+        if (n < Co) {
+            const int64_t p = (int64_t)row * W + xx;
+            const float zz = acc + bias[n];
+            if (z) z[p * Co + n] = zz;
+            y[p * Co + n] = __float2bfloat16_rn(zz * sigmoidf_(zz));
+        }
+    }
+}
+
+// Weight gradient of the input convolution, block partials:
+// partial[blk][n * 18 + k] = sum over the block's image rows and their pixels
+// of dz[p][n] x[p shifted by tap k / 2][k % 2].  Per image row the block
+// stages the three source rows with their circular halo (FP32) and the row's
+// dz for its 32 output channels (FP32) in shared memory; thread t takes
+// channel n0 + t % 32 and k = t / 32, t / 32 + 8, t / 32 + 16 (< 18) and runs
+// over the row's pixels in order.  k_colsum_final sums the blocks.
+__global__ void __launch_bounds__(256) k_conv_in_wgrad(const bf16 *__restrict__ dz, const bf16 *__restrict__ x, int B,
+                                                       int H, int W, int Co, int rows_per_blk,
+                                                       float *__restrict__ partial) {
+    extern __shared__ float sm_in[];
+    float *xs = sm_in;                          // [3][W + 2][2]
+    float *dzs = sm_in + 3 * (W + 2) * kInCh;   // [W][32]
+    const int nl = threadIdx.x & 31, kg = threadIdx.x >> 5;
+    const int n0 = blockIdx.y * 32, n = n0 + nl;
+    float acc[3] = {0.f, 0.f, 0.f};
+    int off[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int k = kg + 8 * j < kInK ? kg + 8 * j : 0;
+        const int tap = k / kInCh;
+        off[j] = ((tap / 3) * (W + 2) + tap % 3) * kInCh + k % kInCh;  // + px * kInCh
+    }
+    const int r0 = blockIdx.x * rows_per_blk;
+    const int r1 = min(B * H, r0 + rows_per_blk);
+    for (int r = r0; r < r1; ++r) {
+        const int b = r / H, yy = r % H;
+        __syncthreads();  // the previous row's reads are done
+        for (int i = threadIdx.x; i < 3 * (W + 2) * kInCh; i += blockDim.x) {
+            const int c = i % kInCh, col = (i / kInCh) % (W + 2), dy = i / (kInCh * (W + 2));
+            const int sy = (yy + dy - 1 + H) % H, sx = (col - 1 + W) % W;
+            xs[i] = __bfloat162float(x[(((int64_t)b * H + sy) * W + sx) * kInCh + c]);
+        }
+        for (int i = threadIdx.x; i < W * 32; i += blockDim.x) {
+            const int px = i / 32, c = n0 + i % 32;
+            dzs[i] = c < Co ? __bfloat162float(dz[(((int64_t)b * H + yy) * W + px) * Co + c]) : 0.f;
+        }
+        __syncthreads();
+        for (int px = 0; px < W; ++px) {
+            const float d = dzs[px * 32 + nl];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc[j] = __fmaf_rn(d, xs[off[j] + px * kInCh], acc[j]);
+        }
+    }
+    if (n >= Co) return;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        if (kg + 8 * j < kInK) partial[(int64_t)blockIdx.x * Co * kInK + n * kInK + kg + 8 * j] = acc[j];
 }
 
 // dd1[p][c] = sum_o dout[p][o] Wh[o][c]
@@ -533,7 +641,9 @@ size_t unet_layout(ensf_unet *u, const ensf_unet_config *c, char *base) {
     u->gskip[0] = a.take<float>(P(0) * w1);
     u->gskip[1] = a.take<float>(P(1) * w2);
     u->gskip[2] = a.take<float>(P(2) * w3);
-    u->colsum_part = a.take<float>((int64_t)1024 * std::max(1024, 2 * w1 + 2));
+    // block partials: bias sums (<= 1024 channels), head weights (2 w1 + 2),
+    // the input convolution's weights (18 w1)
+    u->colsum_part = a.take<float>((int64_t)kColsumBlocks * std::max(std::max(1024, 2 * w1 + 2), kInK * w1));
     u->partial_cap = std::max<int64_t>(max_c, (int64_t)64 << 20);
     u->partial = a.take<float>(u->partial_cap);
     // inputs of the convolutions
@@ -608,12 +718,18 @@ ensf_status forward(ensf_unet *u, const float *x_nchw, int B, bool keep_z, cudaS
         const int64_t P = (int64_t)B * h * w;
         if (ensf::conv3x3_supported(cv.ci, cv.co, h, w, (int)P)) {
             // implicit GEMM: the haloed input, then one kernel with bias + SiLU in its epilogue
-            k_pad_circ<<<nb((int64_t)B * (h + 2) * (w + 2) * (cv.ci / 8)), 256, 0, s>>>(cv.in, B, h, w, cv.ci,
-                                                                                         u->xpad);
+            pad_circ(cv.in, B, h, w, cv.ci, u->xpad, s);
             UNET_LAUNCH();
             if (ensf::launch_conv3x3(u->tc, u->xpad, cv.ci, B, h, w, cv.wb, cv.co, u->params + cv.b_off, 1,
                                      keep_z ? cv.z : nullptr, cv.y, u->err, s) != cudaSuccess)
                 return unet_fail(ENSF_ECUDA, "unet implicit convolution launch");
+            return ENSF_OK;
+        }
+        if (cv.ci == kInCh) {
+            // the 2-channel input convolution: 18 products per output, direct
+            k_conv_in_fwd<<<dim3(nb(w, 8), (unsigned)std::min(B * h, 65535), (cv.co + 31) / 32), 256, 0, s>>>(
+                cv.in, B, h, w, cv.wb, cv.co, cv.kp, u->params + cv.b_off, keep_z ? cv.z : nullptr, cv.y);
+            UNET_LAUNCH();
             return ENSF_OK;
         }
         k_im2col<<<nb(P * cv.kp), 256, 0, s>>>(cv.in, B, h, w, cv.ci, cv.kp, u->col);
@@ -661,7 +777,7 @@ ensf_status conv_back(ensf_unet *u, int l, int B, const float *dy, float *dx, in
     const int64_t P = (int64_t)B * h * w;
     {
         // dZ and the bias gradient (column sums of dZ) in one pass
-        const int blocks = (int)std::min<int64_t>(kColsumBlocks, (P + 255) / 256);
+        const int blocks = (int)std::min<int64_t>(kColsumBlocks, P);  // enough blocks at every level
         const int64_t rows = (P + blocks - 1) / blocks;
         k_silu_back_colsum<<<dim3(blocks, (cv.co + 255) / 256), 256, 0, s>>>(dy, cv.z, P, cv.co, rows, u->dz16,
                                                                              u->colsum_part);
@@ -672,7 +788,21 @@ ensf_status conv_back(ensf_unet *u, int l, int B, const float *dy, float *dx, in
     k_transpose_bf16<<<dim3((cv.co + 31) / 32, (unsigned)((P + 31) / 32)), dim3(32, 8), 0, s>>>(u->dz16, P, cv.co,
                                                                                               u->dzT);
     UNET_LAUNCH();
-    if (ensf::conv3x3_wgrad_supported(cv.ci, cv.co, h, w, (int)P)) {
+    if (cv.ci == kInCh) {
+        // the input convolution's 18 x co weight gradient: block partials of the
+        // pixel sums, then a fixed-order sum over the blocks
+        const int rows = (B * h + kColsumBlocks - 1) / kColsumBlocks;  // image rows per block
+        const int blocks = (B * h + rows - 1) / rows;
+        const int smem = (3 * (w + 2) * kInCh + w * 32) * (int)sizeof(float);
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(k_conv_in_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return unet_fail(ENSF_ECUDA, "unet input-convolution weight gradient: shared memory");
+        k_conv_in_wgrad<<<dim3(blocks, (cv.co + 31) / 32), 256, smem, s>>>(u->dz16, cv.in, B, h, w, cv.co, rows,
+                                                                           u->colsum_part);
+        k_colsum_final<<<(cv.co * kInK + 3) / 4, 128, 0, s>>>(u->colsum_part, blocks, cv.co * kInK,
+                                                              u->grads + cv.w_off);
+        UNET_LAUNCH();
+    } else if (ensf::conv3x3_wgrad_supported(cv.ci, cv.co, h, w, (int)P)) {
         // weight gradient as nine implicit GEMMs over the pixels: dZ^T against
         // the input's column-shifted, transposed copies (held in the im2col
         // scratch, which is 9 * P * ci >= 3 * B * (h + 2) * w * ci long)
@@ -696,8 +826,7 @@ ensf_status conv_back(ensf_unet *u, int l, int B, const float *dy, float *dx, in
     if (!dx) return ENSF_OK;
     if (!accumulate && ensf::conv3x3_supported(cv.co, cv.ci, h, w, (int)P)) {
         // the data gradient as the same implicit-GEMM convolution of the haloed dZ with mirrored taps
-        k_pad_circ<<<nb((int64_t)B * (h + 2) * (w + 2) * (cv.co / 8)), 256, 0, s>>>(u->dz16, B, h, w, cv.co,
-                                                                                     u->xpad);
+        pad_circ(u->dz16, B, h, w, cv.co, u->xpad, s);
         UNET_LAUNCH();
         if (ensf::launch_conv3x3(u->tc, u->xpad, cv.co, B, h, w, cv.wf, cv.ci, nullptr, 0, dx, nullptr, u->err, s) !=
             cudaSuccess)
