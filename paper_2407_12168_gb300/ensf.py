@@ -312,7 +312,9 @@ class Filter:
         the SMs (``copy_sm``) when the host buffer is page-locked and 16-byte
         sized: measured on GB300, copy-engine transfers of 2 GiB slowed to
         100-150 ms on a busy host while the SMs moved the same bytes in
-        25-45 ms (10 ms on a quiet host)."""
+        25-45 ms (10 ms on a quiet host).  Right after other processes on the
+        host free much memory, both kinds of copy run far slower for their
+        first gigabytes (a 2 GiB copy-out measured 927, 76, then 11 ms)."""
         torch = _torch()
         if not jobs:
             return []
