@@ -33,6 +33,7 @@ constexpr int kLevels = 3;
 constexpr int kConvs = 14;
 constexpr int kColsumBlocks = 1024;  // row blocks of the column sums (bias and head gradients)
 constexpr int kLossBlocks = 296;     // blocks of the loss reduction (two per SM)
+constexpr int64_t kSiluTransposeSmem = 32 * 1024;  // dz rows a SiLU-backward block transposes in shared memory
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + __expf(-z)); }
 
@@ -153,8 +154,11 @@ __global__ void k_bias_silu(const float *__restrict__ c, const float *__restrict
 // threads of a column in thread order (fixed order; k_colsum_final ends it).
 __global__ void __launch_bounds__(256) k_silu_back_colsum(const float *__restrict__ dy, const float *__restrict__ z,
                                                           int64_t P, int C, int64_t rows_per_blk,
-                                                          bf16 *__restrict__ dz16, float *__restrict__ partial) {
+                                                          bf16 *__restrict__ dz16, float *__restrict__ partial,
+                                                          bf16 *__restrict__ dzT) {
     __shared__ float red[256];
+    extern __shared__ bf16 tsm[];  // with dzT: the block's dz rows [rows_per_blk][Cg + 2] (padded: no bank conflicts)
+    const int tld = min(256, C - (int)blockIdx.y * 256) + 2;
     const int cb = blockIdx.y * 256;
     const int Cg = min(256, C - cb);
     const int R = 256 / Cg;
@@ -177,7 +181,9 @@ __global__ void __launch_bounds__(256) k_silu_back_colsum(const float *__restric
             for (int k = 0; k < 8; ++k) {
                 const float sg = sigmoidf_(zv[k]);
                 const float g = dv[k] * sg * (1.f + zv[k] * (1.f - sg));
-                dz16[(r + k * R) * C + cb + cl] = __float2bfloat16_rn(g);
+                const bf16 gb = __float2bfloat16_rn(g);
+                dz16[(r + k * R) * C + cb + cl] = gb;
+                if (dzT) tsm[(r + k * R - r0) * tld + cl] = gb;
                 acc += g;
             }
         }
@@ -186,7 +192,9 @@ __global__ void __launch_bounds__(256) k_silu_back_colsum(const float *__restric
             const float zz = z[i];
             const float sg = sigmoidf_(zz);
             const float g = dy[i] * sg * (1.f + zz * (1.f - sg));
-            dz16[i] = __float2bfloat16_rn(g);
+            const bf16 gb = __float2bfloat16_rn(g);
+            dz16[i] = gb;
+            if (dzT) tsm[(r - r0) * tld + cl] = gb;
             acc += g;
         }
     }
@@ -196,6 +204,14 @@ __global__ void __launch_bounds__(256) k_silu_back_colsum(const float *__restric
         float sum = 0.f;
         for (int k = 0; k < R; ++k) sum += red[k * Cg + t];
         partial[(int64_t)blockIdx.x * C + cb + t] = sum;
+    }
+    if (dzT) {
+        // dzT[c][r] for the block's rows: runs of consecutive rows per channel
+        const int nrows = (int)(r1 - r0);
+        for (int idx = t; idx < Cg * nrows; idx += blockDim.x) {
+            const int c = idx / nrows, rr = idx - c * nrows;
+            dzT[(int64_t)(cb + c) * P + r0 + rr] = tsm[rr * tld + c];
+        }
     }
 }
 
@@ -777,17 +793,23 @@ ensf_status conv_back(ensf_unet *u, int l, int B, const float *dy, float *dx, in
     const int64_t P = (int64_t)B * h * w;
     {
         // dZ and the bias gradient (column sums of dZ) in one pass
+        // dZ, its transpose for the weight-gradient GEMMs (when a block's rows
+        // fit in shared memory) and the bias gradient (column sums) in one pass
         const int blocks = (int)std::min<int64_t>(kColsumBlocks, P);  // enough blocks at every level
         const int64_t rows = (P + blocks - 1) / blocks;
-        k_silu_back_colsum<<<dim3(blocks, (cv.co + 255) / 256), 256, 0, s>>>(dy, cv.z, P, cv.co, rows, u->dz16,
-                                                                             u->colsum_part);
+        const int64_t tbytes = rows * (std::min(cv.co, 256) + 2) * (int64_t)sizeof(bf16);
+        const bool fused_t = tbytes <= kSiluTransposeSmem;
+        k_silu_back_colsum<<<dim3(blocks, (cv.co + 255) / 256), 256, fused_t ? (size_t)tbytes : 0, s>>>(
+            dy, cv.z, P, cv.co, rows, u->dz16, u->colsum_part, fused_t ? u->dzT : nullptr);
         k_colsum_final<<<(cv.co + 3) / 4, 128, 0, s>>>(u->colsum_part, blocks, cv.co, u->grads + cv.b_off);
         UNET_LAUNCH();
+        if (!fused_t) {
+            k_transpose_bf16<<<dim3((cv.co + 31) / 32, (unsigned)((P + 31) / 32)), dim3(32, 8), 0, s>>>(
+                u->dz16, P, cv.co, u->dzT);
+            UNET_LAUNCH();
+        }
     }
     ensf_status st;
-    k_transpose_bf16<<<dim3((cv.co + 31) / 32, (unsigned)((P + 31) / 32)), dim3(32, 8), 0, s>>>(u->dz16, P, cv.co,
-                                                                                              u->dzT);
-    UNET_LAUNCH();
     if (cv.ci == kInCh) {
         // the input convolution's 18 x co weight gradient: block partials of the
         // pixel sums, then a fixed-order sum over the blocks
