@@ -939,7 +939,7 @@ def run_sharded(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="large-512", choices=sorted(inputs.WORKLOADS) + ["batched-uneven"])
     ap.add_argument("--path", default="split-bf16", choices=sorted(PATHS))

@@ -1593,6 +1593,26 @@ k_wx_em_tc_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__restri
     }
 }
 
+// One staged chunk's update (16 particles of this thread's state column):
+// score, Euler-Maruyama step and the next Gram's BF16 planes, the
+// observation operator (OBS) and the lo plane (LO) fixed at compile time.
+template <int OBS, bool LO>
+__device__ __forceinline__ void staged_chunk_update(float *zs, __nv_bfloat16 *hs, __nv_bfloat16 *ls, int cl,
+                                                    const float (&u)[16], const float (&xi)[16], bool obs, float yc,
+                                                    float inv_r, const StepCoef &cf, float shift) {
+#pragma unroll
+    for (int e = 0; e < kStgRows; ++e) {
+        const float zv = zs[e * kStgCols + cl];
+        const float gl = obs ? lik_score(OBS, zv, yc, inv_r) : 0.f;
+        const float zn = em_update(cf, zv, u[e], gl, xi[e]);
+        zs[e * kStgCols + cl] = zn;
+        const float zc = __fsub_rn(zn, shift);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
+        hs[e * kStgCols + cl] = hi;
+        if (LO) ls[e * kStgCols + cl] = __float2bfloat16_rn(zc - __bfloat162float(hi));
+    }
+}
+
 // Batched W X + EM with the TMA-staged epilogue of k_wx_em_staged, over the
 // tile list of all filters (BN = kBatchTileN particles per item).  The
 // filter's maps sit at maps[8 inst + ...]: 0, 2 the W X operands (X^T, W),
@@ -1706,12 +1726,15 @@ k_wx_em_staged_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__re
         uint64_t *zf = zfull + part * 2;
         uint64_t *zd = zdone + part * 2;
         // An item's chunks that hold particles go round-robin to the four
-        // groups of epilogue warps (chunk j to group j % 4), so that items of
-        // small filters keep every group busy.
+        // groups of epilogue warps, starting at a group that rotates with the
+        // item (chunk j of item t to group (j - t) mod 4), so that items of
+        // small filters keep every group busy over consecutive items.
+        auto group_slot = [&](int t) -> int { return (part + t) & 3; };  // this group's first chunk of item t
         auto chunks_of = [&](int t) -> int {
             const BWxItem w = items[t];
             const int live = min(kMaxChunks, (insts[w.inst].n - w.n0 + kStgRows - 1) / kStgRows);
-            return live > part ? (live - part - 1) / 4 + 1 : 0;
+            const int g0 = group_slot(t);
+            return live > g0 ? (live - g0 - 1) / 4 + 1 : 0;
         };
         // the cursor of this group's next chunk to load: item nt, local chunk nc
         int nt = blockIdx.x, nc = 0;
@@ -1726,7 +1749,7 @@ k_wx_em_staged_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__re
             skip_empty();
             if (nt >= n_items) return;
             const BWxItem w = items[nt];
-            const int y = w.n0 + (part + 4 * nc) * kStgRows;
+            const int y = w.n0 + (group_slot(nt) + 4 * nc) * kStgRows;
             uint64_t *bar = &zf[loads & 1];
             mbar_expect_tx(bar, P::kStgZ);
             tma_load_2d(smem_u32(stg + (loads & 1) * P::kStgBuf), maps + 8 * w.inst + 4, bar, w.m0, y);
@@ -1758,7 +1781,7 @@ k_wx_em_staged_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__re
                     bulk_wait_read_all();  // the store of this group's previous chunk has left that buffer
                     issue_next();
                 }
-                const int cc = (part + 4 * ch) * kStgRows;  // accumulator column = particle within the item
+                const int cc = (group_slot(t) + 4 * ch) * kStgRows;  // accumulator column = particle within the item
                 float u[16];
                 tmem_ld16(tmem + slot * 256 + (static_cast<uint32_t>(q * 32) << 16) + cc, u);
                 if (!__all_sync(0xffffffffu, mbar_wait(&zf[buf], (g >> 1) & 1u, abort_flag, err))) {
@@ -1778,16 +1801,17 @@ k_wx_em_staged_batched(const CUtensorMap *__restrict__ maps, const BWxItem *__re
                     xi[e4 * 4 + 2] = v.z;
                     xi[e4 * 4 + 3] = v.w;
                 }
-#pragma unroll
-                for (int e = 0; e < kStgRows; ++e) {
-                    const float zv = zs[e * kStgCols + cl];
-                    const float gl = obs ? lik_score(I.obs_op, zv, yc, I.inv_r) : 0.f;
-                    const float zn = em_update(cf, zv, u[e], gl, xi[e]);
-                    zs[e * kStgCols + cl] = zn;
-                    const float zc = __fsub_rn(zn, shift);
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(zc);
-                    hs[e * kStgCols + cl] = hi;
-                    if (lo_plane) ls[e * kStgCols + cl] = __float2bfloat16_rn(zc - __bfloat162float(hi));
+                // the element loop specialised on the item's operator and planes
+                if (I.obs_op == 1) {
+                    if (lo_plane)
+                        staged_chunk_update<1, true>(zs, hs, ls, cl, u, xi, obs, yc, I.inv_r, cf, shift);
+                    else
+                        staged_chunk_update<1, false>(zs, hs, ls, cl, u, xi, obs, yc, I.inv_r, cf, shift);
+                } else {
+                    if (lo_plane)
+                        staged_chunk_update<0, true>(zs, hs, ls, cl, u, xi, obs, yc, I.inv_r, cf, shift);
+                    else
+                        staged_chunk_update<0, false>(zs, hs, ls, cl, u, xi, obs, yc, I.inv_r, cf, shift);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(&zd[buf]);
