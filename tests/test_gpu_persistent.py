@@ -32,6 +32,7 @@ def _run(p, noise_buf=None, graph=False, filt=None):
 @pytest.mark.parametrize("case", [
     dict(seed=71, n=1, grid=8, K=5, obs_op=0, sigma_obs=0.6),
     dict(seed=72, n=33, grid=36, K=8, obs_op=1, obs_frac=0.5, sigma_obs=0.4),
+    dict(seed=77, n=64, grid=32, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.4),
     dict(seed=73, n=70, grid=44, K=6, obs_op=0, obs_frac=0.25, sigma_obs=0.5),
     dict(seed=74, n=128, grid=24, layers=2, K=6, obs_op=1, obs_frac=0.5, sigma_obs=0.5),
 ])
