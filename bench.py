@@ -636,8 +636,9 @@ def run_ours(args):
     if pipelined:
         t0, t1, evs = pipe
         e2e_ms = t0.elapsed_time(t1) / pipe_steps
-        e2e_parts = {"mode": f"{pipe_steps} analyses through host buffers, each one's copy-in and the previous "
-                             f"one's copy-out overlapping the analysis before and after (Filter.analyses_from_host)",
+        e2e_parts = {"mode": f"{pipe_steps} analyses through host buffers, the copy-ins of the next ones and the "
+                             f"copy-outs of the previous ones (two copy streams, three device sets) overlapping "
+                             f"each analysis (Filter.analyses_from_host)",
                      "ms_per_step": round(e2e_ms, 2),
                      "copy_in_to_analysed_ms": [round(a.elapsed_time(b), 2) for a, b, _ in evs],
                      "analysed_to_copied_out_ms": [round(b.elapsed_time(c), 2) for _, b, c in evs],

@@ -291,14 +291,17 @@ class Filter:
         return out
 
     def analyses_from_host(self, jobs, sigma_obs: float, K: int, eps: float, obs_op: int = OBS_IDENTITY,
-                           stream=None, copy_stream=None, copy_blocks: int = 152):
+                           stream=None, copy_stream=None, copy_blocks: int = 152, sets: int = 3,
+                           out_stream=None):
         """A sequence of analyses whose inputs and results live in page-locked
         host memory (e.g. ``host_empty``), with the copies overlapped: while
-        analysis s runs, the inputs of analysis s + 1 are copied in and the
-        result of analysis s - 1 is copied out, on ``copy_stream``.  Two device
-        sets of inputs and results alternate; events order every reuse (an
-        input set is refilled only after the analysis that read it, a result
-        buffer is rewritten only after its copy-out).
+        analysis s runs, the inputs of the next analyses are copied in on
+        ``copy_stream`` and the results of the previous ones copied out on
+        ``out_stream`` (the two directions run side by side).  ``sets``
+        device sets of inputs and results rotate; events order every reuse
+        (an input set is refilled only after the analysis that read it, a
+        result buffer is rewritten only after its copy-out), so copies of up
+        to about (sets - 1) analysis times stay hidden.
 
         jobs: list of dicts with host tensors ``prior`` [n][d], ``y`` [d],
         ``mask`` [d] or None, ``out`` [n][d], and ``seed`` (and ``offset``).
@@ -318,8 +321,11 @@ class Filter:
         torch = _torch()
         if not jobs:
             return []
+        if sets < 2:
+            raise ValueError("analyses_from_host needs at least two device sets")
         s = stream if stream is not None else torch.cuda.current_stream()
         cs = copy_stream if copy_stream is not None else torch.cuda.Stream()
+        co = out_stream if out_stream is not None else torch.cuda.Stream()
         p0 = jobs[0]["prior"]
         n, d = p0.shape
         for j in jobs:
@@ -329,53 +335,59 @@ class Filter:
                 raise ValueError("jobs hold host tensors")
         dev = torch.device("cuda", torch.cuda.current_device())
         has_mask = jobs[0].get("mask") is not None
-        sets = [dict(prior=torch.empty((n, d), dtype=torch.float32, device=dev),
-                     y=torch.empty((d,), dtype=torch.float32, device=dev),
-                     mask=torch.empty((d,), dtype=torch.uint8, device=dev) if has_mask else None,
-                     out=torch.empty((n, d), dtype=torch.float32, device=dev)) for _ in range(2)]
+        nsets = min(int(sets), len(jobs))
+        devsets = [dict(prior=torch.empty((n, d), dtype=torch.float32, device=dev),
+                        y=torch.empty((d,), dtype=torch.float32, device=dev),
+                        mask=torch.empty((d,), dtype=torch.uint8, device=dev) if has_mask else None,
+                        out=torch.empty((n, d), dtype=torch.float32, device=dev)) for _ in range(nsets)]
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in jobs]
         start = torch.cuda.Event()
         start.record(s)
         cs.wait_event(start)
+        co.wait_event(start)
 
-        def move(dst, src, sm):
+        def move(dst, src, sm, stream_):
             host = src if not src.is_cuda else dst
             nbytes = src.numel() * src.element_size()
             if (sm and copy_blocks > 0 and nbytes % 16 == 0 and dst.data_ptr() % 16 == 0
                     and src.data_ptr() % 16 == 0 and host_registered(host)):
-                copy_sm(dst, src, copy_blocks, stream=cs)
+                copy_sm(dst, src, copy_blocks, stream=stream_)
             else:
                 dst.copy_(src, non_blocking=True)
 
+        issued = [0]  # copy-ins enqueued so far
+
         def copy_in(i):
-            b, j = sets[i % 2], jobs[i]
+            b, j = devsets[i % nsets], jobs[i]
             with torch.cuda.stream(cs):
-                if i >= 2:
-                    cs.wait_event(ev[i - 2][1])   # the analysis that read this set is done
-                move(b["prior"], j["prior"], i == 0)
-                move(b["y"], j["y"], i == 0)
+                if i >= nsets:
+                    cs.wait_event(ev[i - nsets][1])   # the analysis that read this set is done
+                move(b["prior"], j["prior"], i == 0, cs)
+                move(b["y"], j["y"], i == 0, cs)
                 if has_mask:
-                    move(b["mask"], j["mask"], i == 0)
+                    move(b["mask"], j["mask"], i == 0, cs)
                 ev[i][0].record(cs)
+            issued[0] = i + 1
 
         copy_in(0)
         for i, j in enumerate(jobs):
-            b = sets[i % 2]
-            if i + 1 < len(jobs):
-                copy_in(i + 1)
+            b = devsets[i % nsets]
+            # the copy-ins the free sets allow, ahead of this analysis
+            while issued[0] < len(jobs) and issued[0] <= i + nsets - 1:
+                copy_in(issued[0])
             s.wait_event(ev[i][0])
-            if i >= 2:
-                s.wait_event(ev[i - 2][2])        # this result buffer has been copied out
+            if i >= nsets:
+                s.wait_event(ev[i - nsets][2])    # this result buffer has been copied out
             self.analysis(b["prior"], b["y"], b["mask"], sigma_obs, K, eps, obs_op, seed=j.get("seed", 0),
                           offset=j.get("offset", 0), out=b["out"], stream=s)
             ev[i][1].record(s)
-            with torch.cuda.stream(cs):
-                cs.wait_event(ev[i][1])
-                move(j["out"], b["out"], i == len(jobs) - 1)
-                ev[i][2].record(cs)
+            with torch.cuda.stream(co):
+                co.wait_event(ev[i][1])
+                move(j["out"], b["out"], i == len(jobs) - 1, co)
+                ev[i][2].record(co)
         s.wait_event(ev[-1][2])
-        self._pipeline_keep = (sets, cs)          # device buffers live until the streams are done
+        self._pipeline_keep = (devsets, cs, co)   # device buffers live until the streams are done
         return ev
 
     def analysis_minibatch(self, prior, y, mask, sigma_obs: float, K: int, eps: float, perm, J: int,

@@ -81,11 +81,14 @@ def test_pipelined_host_analyses_equal_one_by_one():
         jobs.append(dict(prior=h_prior, y=h_y, mask=h_mask, out=ensf.host_empty(p.prior.shape), seed=p.seed + i))
         refs.append(f.analysis(d_prior * scale, d_y, d_mask, p.sigma_obs, p.K, p.eps, p.obs_op,
                                seed=p.seed + i).cpu())
-    evs = f.analyses_from_host(jobs, p.sigma_obs, p.K, p.eps, p.obs_op)
-    torch.cuda.synchronize()
-    assert len(evs) == 5
-    for j, ref in zip(jobs, refs):
-        assert torch.equal(j["out"], ref)
+    for sets in (2, 3):  # device sets rotating under the five jobs
+        for j in jobs:
+            j["out"].zero_()
+        evs = f.analyses_from_host(jobs, p.sigma_obs, p.K, p.eps, p.obs_op, sets=sets)
+        torch.cuda.synchronize()
+        assert len(evs) == 5
+        for j, ref in zip(jobs, refs):
+            assert torch.equal(j["out"], ref), sets
 
 
 def test_sm_copy_kernel_moves_host_and_device_bytes():
