@@ -119,16 +119,6 @@ void pad_circ(const bf16 *x, int B, int h, int w, int C, bf16 *xp, cudaStream_t 
         k_pad_circ<int64_t><<<nb(total), 256, 0, s>>>(x, B, h, w, C, xp);
 }
 
-// Weights of the data gradient: wf[c][tap'][n] = W[n][8 - tap'][c] (the taps
-// mirrored), so that the gradient is the same implicit-GEMM convolution.
-__global__ void k_repack_flip(const float *__restrict__ W, int Co, int Ci, bf16 *__restrict__ wf) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over Ci * 9 * Co
-    if (i >= (int64_t)Ci * 9 * Co) return;
-    const int n = (int)(i % Co);
-    const int tap = (int)((i / Co) % 9);
-    const int c = (int)(i / ((int64_t)9 * Co));
-    wf[i] = __float2bfloat16_rn(W[((int64_t)n * 9 + (8 - tap)) * Ci + c]);
-}
 
 __global__ void k_reduce_splits(const float *__restrict__ part, int S, int64_t count, float *__restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,15 +354,17 @@ __global__ void k_loss_final(const double *__restrict__ part, int blocks, int64_
     if (threadIdx.x == 0) *loss = sum / (double)count;
 }
 
-// The 2-channel input convolution, direct: a warp per pixel, lane = output
-// channel n0 + lane (coalesced stores); the 18 inputs of the pixel are read
-// once per warp (broadcast), the BF16 weights [k][n] sit in shared memory as
-// floats; 18 products accumulated in FP32 in (tap, c) order, then the bias,
-// z (FP32, if kept) and y = SiLU(z) (BF16).  Grid: x over 8-pixel blocks of
-// an image row, y over image rows (b, y) with a stride loop, z over groups
-// of 32 output channels.
+// The 2-channel input convolution, direct: a warp takes 8 consecutive
+// pixels of an image row, lane = output channel n0 + lane (coalesced
+// stores); the 3 x 10 input neighbourhood of the 8 pixels is read once per
+// warp (broadcast loads), the BF16 weights [k][n] sit in shared memory as
+// floats; per pixel 18 products accumulated in FP32 in (tap, c) order, then
+// the bias, z (FP32, if kept) and y = SiLU(z) (BF16).  Grid: x over 64-pixel
+// blocks of an image row, y over image rows (b, y) with a stride loop, z over
+// groups of 32 output channels.
 constexpr int kInCh = 2;
 constexpr int kInK = 9 * kInCh;
+constexpr int kInPx = 8;  // pixels per warp
 __global__ void __launch_bounds__(256) k_conv_in_fwd(const bf16 *__restrict__ x, int B, int H, int W,
                                                      const bf16 *__restrict__ wb, int Co, int Kp,
                                                      const float *__restrict__ bias, float *__restrict__ z,
@@ -384,27 +376,45 @@ __global__ void __launch_bounds__(256) k_conv_in_fwd(const bf16 *__restrict__ x,
         wsm[k][t % 32] = n < Co ? __bfloat162float(wb[(int64_t)n * Kp + k]) : 0.f;
     }
     __syncthreads();
-    const int xx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (xx >= W) return;
+    const int x0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kInPx;
+    if (x0 >= W) return;
     const int n = n0 + lane;
+    float wr[kInK];
+#pragma unroll
+    for (int k = 0; k < kInK; ++k) wr[k] = wsm[k][lane];
+    const float bn = n < Co ? bias[n] : 0.f;
     for (int row = blockIdx.y; row < B * H; row += gridDim.y) {
         const int b = row / H, yy = row - b * H;
-        float acc = 0.f;
+        float nb[3][kInPx + 2][kInCh];  // the neighbourhood, columns x0 - 1 .. x0 + 8
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
+        for (int dy = 0; dy < 3; ++dy) {
+            int sy = yy + dy - 1;
             sy = sy < 0 ? sy + H : (sy >= H ? sy - H : sy);
-            sx = sx < 0 ? sx + W : (sx >= W ? sx - W : sx);
-            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(
-                x + (((int64_t)b * H + sy) * W + sx) * kInCh);
-            acc = __fmaf_rn(__low2float(v), wsm[tap * kInCh][lane], acc);
-            acc = __fmaf_rn(__high2float(v), wsm[tap * kInCh + 1][lane], acc);
+            const bf16 *rowp = x + ((int64_t)b * H + sy) * W * kInCh;
+#pragma unroll
+            for (int q = 0; q < kInPx + 2; ++q) {
+                int sx = x0 + q - 1;
+                sx = sx < 0 ? sx + W : (sx >= W ? sx - W : sx);
+                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(rowp + sx * kInCh);
+                nb[dy][q][0] = __low2float(v);
+                nb[dy][q][1] = __high2float(v);
+            }
         }
-        if (n < Co) {
-            const int64_t p = (int64_t)row * W + xx;
-            const float zz = acc + bias[n];
-            if (z) z[p * Co + n] = zz;
-            y[p * Co + n] = __float2bfloat16_rn(zz * sigmoidf_(zz));
+#pragma unroll
+        for (int px = 0; px < kInPx; ++px) {
+            if (x0 + px >= W) break;
+            float acc = 0.f;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                acc = __fmaf_rn(nb[tap / 3][px + tap % 3][0], wr[tap * kInCh], acc);
+                acc = __fmaf_rn(nb[tap / 3][px + tap % 3][1], wr[tap * kInCh + 1], acc);
+            }
+            if (n < Co) {
+                const int64_t p = (int64_t)row * W + x0 + px;
+                const float zz = acc + bn;
+                if (z) z[p * Co + n] = zz;
+                y[p * Co + n] = __float2bfloat16_rn(zz * sigmoidf_(zz));
+            }
         }
     }
 }
@@ -490,16 +500,6 @@ __global__ void k_head_dw_partial(const float *__restrict__ dout, const bf16 *__
     partial[(int64_t)blockIdx.x * nj + j] = acc;
 }
 
-// master W [Co][9Ci] -> Wb [Co][Kp] (zero padded) and Wt [Kp][Co]
-__global__ void k_repack(const float *__restrict__ w, int Co, int K9, int Kp, bf16 *__restrict__ wb,
-                         bf16 *__restrict__ wt) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)Co * Kp) return;
-    const int o = (int)(i / Kp), k = (int)(i % Kp);
-    const bf16 v = __float2bfloat16_rn(k < K9 ? w[(int64_t)o * K9 + k] : 0.f);
-    wb[i] = v;
-    wt[(int64_t)k * Co + o] = v;
-}
 
 __global__ void k_unpad_grad(const float *__restrict__ c, int Co, int K9, int Kp, float *__restrict__ g) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -743,7 +743,8 @@ ensf_status forward(ensf_unet *u, const float *x_nchw, int B, bool keep_z, cudaS
         }
         if (cv.ci == kInCh) {
             // the 2-channel input convolution: 18 products per output, direct
-            k_conv_in_fwd<<<dim3(nb(w, 8), (unsigned)std::min(B * h, 65535), (cv.co + 31) / 32), 256, 0, s>>>(
+            k_conv_in_fwd<<<dim3(nb(w, 8 * kInPx), (unsigned)std::min(B * h, 65535), (cv.co + 31) / 32), 256, 0,
+                            s>>>(
                 cv.in, B, h, w, cv.wb, cv.co, cv.kp, u->params + cv.b_off, keep_z ? cv.z : nullptr, cv.y);
             UNET_LAUNCH();
             return ENSF_OK;
@@ -926,13 +927,62 @@ ensf_status backward(ensf_unet *u, const float *target, int B, cudaStream_t s) {
     return ENSF_OK;
 }
 
-ensf_status repack(ensf_unet *u, cudaStream_t s) {
-    for (int l = 0; l < kConvs; ++l) {
-        ensf_unet::Conv &cv = u->conv[l];
-        k_repack<<<nb((int64_t)cv.co * cv.kp), 256, 0, s>>>(u->params + cv.w_off, cv.co, 9 * cv.ci, cv.kp, cv.wb,
-                                                            cv.wt);
-        k_repack_flip<<<nb((int64_t)cv.co * 9 * cv.ci), 256, 0, s>>>(u->params + cv.w_off, cv.co, cv.ci, cv.wf);
+// Every convolution's BF16 weight copies from the FP32 master weights
+// W [co][9 ci] in one launch (a layer table passed by value): the elements
+// [0, total_b) are Wb [co][kp] (zero padded past 9 ci) and its transpose
+// Wt [kp][co], layer after layer; [total_b, total) the weights of the data
+// gradient, wf[c][tap'][n] = W[n][8 - tap'][c] (taps mirrored, so that the
+// gradient is the same implicit-GEMM convolution).
+struct RepackTable {
+    const float *w[kConvs];
+    bf16 *wb[kConvs], *wt[kConvs], *wf[kConvs];
+    int co[kConvs], ci[kConvs], kp[kConvs];
+    int64_t end_b[kConvs], end_f[kConvs];  // running element ends of the two parts
+};
+
+__global__ void __launch_bounds__(256) k_repack_all(RepackTable t) {
+    const int64_t total_b = t.end_b[kConvs - 1], total = total_b + t.end_f[kConvs - 1];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < total_b) {
+            int l = 0;
+            while (i >= t.end_b[l]) ++l;
+            const int64_t e = i - (l ? t.end_b[l - 1] : 0);
+            const int Kp = t.kp[l], K9 = 9 * t.ci[l], Co = t.co[l];
+            const int o = (int)(e / Kp), k = (int)(e % Kp);
+            const bf16 v = __float2bfloat16_rn(k < K9 ? t.w[l][(int64_t)o * K9 + k] : 0.f);
+            t.wb[l][e] = v;
+            t.wt[l][(int64_t)k * Co + o] = v;
+        } else {
+            const int64_t j = i - total_b;
+            int l = 0;
+            while (j >= t.end_f[l]) ++l;
+            const int64_t e = j - (l ? t.end_f[l - 1] : 0);
+            const int Co = t.co[l], Ci = t.ci[l];
+            const int n = (int)(e % Co), tap = (int)((e / Co) % 9), c = (int)(e / ((int64_t)9 * Co));
+            t.wf[l][e] = __float2bfloat16_rn(t.w[l][((int64_t)n * 9 + (8 - tap)) * Ci + c]);
+        }
     }
+}
+
+ensf_status repack(ensf_unet *u, cudaStream_t s) {
+    RepackTable t;
+    int64_t eb = 0, ef = 0;
+    for (int l = 0; l < kConvs; ++l) {
+        const ensf_unet::Conv &cv = u->conv[l];
+        t.w[l] = u->params + cv.w_off;
+        t.wb[l] = cv.wb;
+        t.wt[l] = cv.wt;
+        t.wf[l] = cv.wf;
+        t.co[l] = cv.co;
+        t.ci[l] = cv.ci;
+        t.kp[l] = cv.kp;
+        eb += (int64_t)cv.co * cv.kp;
+        ef += (int64_t)cv.co * 9 * cv.ci;
+        t.end_b[l] = eb;
+        t.end_f[l] = ef;
+    }
+    k_repack_all<<<(unsigned)std::min<int64_t>(nb(eb + ef), 152 * 8), 256, 0, s>>>(t);
     UNET_LAUNCH();
     return ENSF_OK;
 }
