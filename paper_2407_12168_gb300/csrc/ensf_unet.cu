@@ -249,16 +249,30 @@ __global__ void k_pool_fwd(const bf16 *__restrict__ x, int B, int H, int W, int 
     y[i] = __float2bfloat16_rn(0.25f * s);
 }
 
+// dx (+)= dy / 4 spread back over each 2 x 2 window, four channels
+// (16 bytes) per thread; C a multiple of 4; I: the index type.
+template <class I>
 __global__ void k_pool_bwd(const float *__restrict__ dy, int B, int H, int W, int C, float *__restrict__ dx,
                            int accumulate) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over the fine grid
-    if (i >= (int64_t)B * H * W * C) return;
-    const int c = (int)(i % C);
-    const int64_t p = i / C;
-    const int xx = (int)(p % W), yy = (int)((p / W) % H);
-    const int64_t b = p / ((int64_t)W * H);
-    const float g = 0.25f * dy[((b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c];
-    dx[i] = accumulate ? dx[i] + g : g;
+    const I i = (I)blockIdx.x * blockDim.x + threadIdx.x;  // over the fine grid, C / 4 per pixel
+    const I c4 = C / 4;
+    if (i >= (I)B * H * W * c4) return;
+    const I cv = i % c4, p = i / c4;
+    const I xx = p % (I)W, yy = (p / (I)W) % (I)H, b = p / ((I)W * H);
+    float4 g = reinterpret_cast<const float4 *>(dy)[((b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * c4 + cv];
+    g.x *= 0.25f;
+    g.y *= 0.25f;
+    g.z *= 0.25f;
+    g.w *= 0.25f;
+    float4 *d4 = reinterpret_cast<float4 *>(dx) + i;
+    if (accumulate) {
+        const float4 o = *d4;
+        g.x += o.x;
+        g.y += o.y;
+        g.z += o.z;
+        g.w += o.w;
+    }
+    *d4 = g;
 }
 
 // out[p] = [nearest-upsampled low (Cl channels), skip (Cs channels)], eight
@@ -277,29 +291,45 @@ __global__ void k_up_concat_fwd(const bf16 *__restrict__ low, const bf16 *__rest
                  : reinterpret_cast<const uint4 *>(skip)[p * Cs8 + (c8 - Cl8)];
 }
 
-// Gradient of k_up_concat_fwd: dlow (coarse, sum of 4) and dskip (+=).
+// Gradient of k_up_concat_fwd: dlow (coarse, the sum of its 4 fine pixels'
+// first Cl channels), four channels per thread; I: the index type.
+template <class I>
 __global__ void k_up_bwd(const float *__restrict__ dout, int B, int H, int W, int Cl, int Cs,
                          float *__restrict__ dlow) {
-    const int Ct = Cl + Cs;
-    const int h = H / 2, w = W / 2;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)B * h * w * Cl) return;
-    const int c = (int)(i % Cl);
-    const int64_t p = i / Cl;
-    const int xx = (int)(p % w), yy = (int)((p / w) % h);
-    const int64_t b = p / ((int64_t)w * h);
-    float s = 0.f;
+    const I Ct4 = (Cl + Cs) / 4, Cl4 = Cl / 4;
+    const I h = H / 2, w = W / 2;
+    const I i = (I)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (I)B * h * w * Cl4) return;
+    const I c = i % Cl4, p = i / Cl4;
+    const I xx = p % w, yy = (p / w) % h, b = p / (w * h);
+    const float4 *d4 = reinterpret_cast<const float4 *>(dout);
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int a = 0; a < 2; ++a)
-        for (int e = 0; e < 2; ++e) s += dout[((b * H + 2 * yy + a) * W + 2 * xx + e) * Ct + c];
-    dlow[i] = s;
+        for (int e = 0; e < 2; ++e) {
+            const float4 v = d4[((b * H + 2 * yy + a) * W + 2 * xx + e) * Ct4 + c];
+            sum.x += v.x;
+            sum.y += v.y;
+            sum.z += v.z;
+            sum.w += v.w;
+        }
+    reinterpret_cast<float4 *>(dlow)[i] = sum;
 }
 
+// dskip (+)= the skip channels of dout [P][Cl + Cs], four per thread.
+template <class I>
 __global__ void k_skip_bwd(const float *__restrict__ dout, int64_t P, int Cl, int Cs, float *__restrict__ dskip) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P * Cs) return;
-    const int64_t p = i / Cs;
-    const int c = (int)(i % Cs);
-    dskip[i] += dout[p * (Cl + Cs) + Cl + c];
+    const I i = (I)blockIdx.x * blockDim.x + threadIdx.x;
+    const I Cs4 = Cs / 4, Ct4 = (Cl + Cs) / 4, Cl4 = Cl / 4;
+    if (i >= (I)P * Cs4) return;
+    const I p = i / Cs4, c = i % Cs4;
+    const float4 v = reinterpret_cast<const float4 *>(dout)[p * Ct4 + Cl4 + c];
+    float4 *o = reinterpret_cast<float4 *>(dskip) + i;
+    float4 r = *o;
+    r.x += v.x;
+    r.y += v.y;
+    r.z += v.z;
+    r.w += v.w;
+    *o = r;
 }
 
 // Head: out_nchw[b][o][y][x] = x_in + sum_c d1[p][c] Wh[o][c] + bh[o].
@@ -864,6 +894,16 @@ ensf_status conv_back(ensf_unet *u, int l, int B, const float *dy, float *dx, in
     return ENSF_OK;
 }
 
+// Launches one of a kernel's two index-type forms over `count` elements:
+// 32-bit indices where they suffice (their divisions are cheaper).
+template <class K32, class K64, class... A>
+void launch_vec(int64_t count, cudaStream_t s, K32 k32, K64 k64, A... args) {
+    if (count < ((int64_t)1 << 31))
+        k32<<<nb(count), 256, 0, s>>>(args...);
+    else
+        k64<<<nb(count), 256, 0, s>>>(args...);
+}
+
 ensf_status backward(ensf_unet *u, const float *target, int B, cudaStream_t s) {
     const int H = u->cfg.height, W = u->cfg.width;
     const int w1 = u->cfg.widths[0], w2 = u->cfg.widths[1], w3 = u->cfg.widths[2], w4 = u->cfg.widths[3];
@@ -891,35 +931,35 @@ ensf_status backward(ensf_unet *u, const float *target, int B, cudaStream_t s) {
     STEP(conv_back(u, 13, B, u->ga, u->gb, 0, s))
     STEP(conv_back(u, 12, B, u->gb, u->ga, 0, s))   // ga = d cat[2] [P0][w2+w1]
     UNET_CUDA(cudaMemsetAsync(u->gskip[0], 0, sizeof(float) * P(0) * w1, s));
-    k_skip_bwd<<<nb(P(0) * w1), 256, 0, s>>>(u->ga, P(0), w2, w1, u->gskip[0]);
-    k_up_bwd<<<nb(P(1) * w2), 256, 0, s>>>(u->ga, B, H, W, w2, w1, u->gb);  // gb = d d2 [P1][w2]
+    launch_vec(P(0) * w1 / 4, s, k_skip_bwd<uint32_t>, k_skip_bwd<int64_t>, u->ga, P(0), w2, w1, u->gskip[0]);
+    launch_vec(P(1) * w2 / 4, s, k_up_bwd<uint32_t>, k_up_bwd<int64_t>, u->ga, B, H, W, w2, w1, u->gb);  // gb = d d2 [P1][w2]
     UNET_LAUNCH();
     // decoder level 1: convs 11, 10 (input = cat[1] = [up(d3) w3, e2 w2])
     STEP(conv_back(u, 11, B, u->gb, u->ga, 0, s))
     STEP(conv_back(u, 10, B, u->ga, u->gb, 0, s))   // gb = d cat[1] [P1][w3+w2]
     UNET_CUDA(cudaMemsetAsync(u->gskip[1], 0, sizeof(float) * P(1) * w2, s));
-    k_skip_bwd<<<nb(P(1) * w2), 256, 0, s>>>(u->gb, P(1), w3, w2, u->gskip[1]);
-    k_up_bwd<<<nb(P(2) * w3), 256, 0, s>>>(u->gb, B, H >> 1, W >> 1, w3, w2, u->ga);  // ga = d d3 [P2][w3]
+    launch_vec(P(1) * w2 / 4, s, k_skip_bwd<uint32_t>, k_skip_bwd<int64_t>, u->gb, P(1), w3, w2, u->gskip[1]);
+    launch_vec(P(2) * w3 / 4, s, k_up_bwd<uint32_t>, k_up_bwd<int64_t>, u->gb, B, H >> 1, W >> 1, w3, w2, u->ga);  // ga = d d3 [P2][w3]
     UNET_LAUNCH();
     // decoder level 2: convs 9, 8 (input = cat[0] = [up(m) w4, e3 w3])
     STEP(conv_back(u, 9, B, u->ga, u->gb, 0, s))
     STEP(conv_back(u, 8, B, u->gb, u->ga, 0, s))    // ga = d cat[0] [P2][w4+w3]
     UNET_CUDA(cudaMemsetAsync(u->gskip[2], 0, sizeof(float) * P(2) * w3, s));
-    k_skip_bwd<<<nb(P(2) * w3), 256, 0, s>>>(u->ga, P(2), w4, w3, u->gskip[2]);
-    k_up_bwd<<<nb(P(3) * w4), 256, 0, s>>>(u->ga, B, H >> 2, W >> 2, w4, w3, u->gb);  // gb = d m [P3][w4]
+    launch_vec(P(2) * w3 / 4, s, k_skip_bwd<uint32_t>, k_skip_bwd<int64_t>, u->ga, P(2), w4, w3, u->gskip[2]);
+    launch_vec(P(3) * w4 / 4, s, k_up_bwd<uint32_t>, k_up_bwd<int64_t>, u->ga, B, H >> 2, W >> 2, w4, w3, u->gb);  // gb = d m [P3][w4]
     UNET_LAUNCH();
     // middle: convs 7, 6; then back through the pool into e3
     STEP(conv_back(u, 7, B, u->gb, u->ga, 0, s))
     STEP(conv_back(u, 6, B, u->ga, u->gb, 0, s))    // gb = d pool[2] [P3][w3]
-    k_pool_bwd<<<nb(P(2) * w3), 256, 0, s>>>(u->gb, B, H >> 2, W >> 2, w3, u->gskip[2], 1);
+    launch_vec(P(2) * w3 / 4, s, k_pool_bwd<uint32_t>, k_pool_bwd<int64_t>, u->gb, B, H >> 2, W >> 2, w3, u->gskip[2], 1);
     UNET_LAUNCH();
     STEP(conv_back(u, 5, B, u->gskip[2], u->ga, 0, s))
     STEP(conv_back(u, 4, B, u->ga, u->gb, 0, s))    // gb = d pool[1] [P2][w2]
-    k_pool_bwd<<<nb(P(1) * w2), 256, 0, s>>>(u->gb, B, H >> 1, W >> 1, w2, u->gskip[1], 1);
+    launch_vec(P(1) * w2 / 4, s, k_pool_bwd<uint32_t>, k_pool_bwd<int64_t>, u->gb, B, H >> 1, W >> 1, w2, u->gskip[1], 1);
     UNET_LAUNCH();
     STEP(conv_back(u, 3, B, u->gskip[1], u->ga, 0, s))
     STEP(conv_back(u, 2, B, u->ga, u->gb, 0, s))    // gb = d pool[0] [P1][w1]
-    k_pool_bwd<<<nb(P(0) * w1), 256, 0, s>>>(u->gb, B, H, W, w1, u->gskip[0], 1);
+    launch_vec(P(0) * w1 / 4, s, k_pool_bwd<uint32_t>, k_pool_bwd<int64_t>, u->gb, B, H, W, w1, u->gskip[0], 1);
     UNET_LAUNCH();
     STEP(conv_back(u, 1, B, u->gskip[0], u->ga, 0, s))
     STEP(conv_back(u, 0, B, u->ga, nullptr, 0, s))
