@@ -156,6 +156,24 @@ def _run(world, leave_at=None):
     return res
 
 
+def test_sharded_analysis_equals_unsharded_oracle_on_three_uneven_gloo_ranks():
+    """Three ranks over 128 columns in 32-column blocks: slices of 32, 32 and 64."""
+    from oracle import oracle as o
+    p = _problem()
+    res = _run(3)
+    z = np.zeros((p.n, p.d))
+    widths = []
+    for r in range(3):
+        (kind, (c0, dl, zr, _)), = res[r]
+        assert kind == "done"
+        z[:, c0:c0 + dl] = zr
+        widths.append(dl)
+    assert widths == [32, 32, 64]
+    ref = o.analysis(p.prior, p.y, p.mask, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed)
+    rel = np.linalg.norm(z - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() <= 1e-12, rel
+
+
 def test_sharded_analysis_equals_unsharded_oracle_on_two_gloo_ranks():
     from oracle import oracle as o
     p = _problem()
