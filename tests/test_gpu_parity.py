@@ -717,3 +717,37 @@ def test_pair_gram_in_a_cuda_graph(f32):
         stream.synchronize()
         assert graph.status_sync() == 0
         np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_analysis_rejects_degenerate_arguments():
+    """Empty and oversized problems, a non-positive or non-finite sigma_obs,
+    eps outside (0, 1), K < 1, an unknown operator, misaligned or aliased
+    buffers: the entry point answers ENSF_EINVAL before any launch, and the
+    handle still runs a valid analysis afterwards (against the oracle)."""
+    import ctypes
+    import torch
+    from paper_2407_12168_gb300 import ensf
+    p = inputs.small_case(seed=91, n=8, grid=8, K=4, obs_op=0, obs_frac=1.0, sigma_obs=0.5)
+    f = ensf.Filter(p.n, p.d, gram="fp32", wx="fp32", check_finite=True)
+    lib = ensf.load()
+    prior = torch.from_numpy(p.prior).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    out = torch.empty_like(prior)
+    nz = ensf.EnsfNoise(None, p.seed, 0)
+
+    def call(n=p.n, d=p.d, sigma=0.5, K=4, eps=p.eps, op=0, prior_ptr=None, out_ptr=None, noise=True):
+        return lib.ensf_analysis(f._h, prior.data_ptr() if prior_ptr is None else prior_ptr, n, d, y.data_ptr(),
+                                 None, op, sigma, K, eps, ctypes.byref(nz) if noise else None,
+                                 out.data_ptr() if out_ptr is None else out_ptr, None)
+
+    bad = [dict(n=0), dict(n=p.n + 1), dict(d=0), dict(d=p.d + 8), dict(d=12), dict(K=0), dict(sigma=0.0),
+           dict(sigma=-1.0), dict(sigma=float("inf")), dict(sigma=float("nan")), dict(eps=0.0), dict(eps=1.0),
+           dict(op=2), dict(prior_ptr=prior.data_ptr() + 4), dict(out_ptr=prior.data_ptr()), dict(noise=False)]
+    for kw in bad:
+        assert call(**kw) == ensf.EINVAL, kw
+    torch.cuda.synchronize()
+    assert f.status_sync() == 0
+    got = f.analysis(prior, y, None, p.sigma_obs, p.K, p.eps, p.obs_op, seed=p.seed).cpu().numpy()
+    ref = run_oracle(p)
+    rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() <= 1e-4, rel
