@@ -10,7 +10,17 @@
 // bias + SiLU.  Loss: mean squared error.  Optimiser: AdamW on FP32 master
 // weights; BF16 copies feed the tensor cores.
 //
-// Every 3x3 convolution is a BF16 GEMM on the tcgen05 kernel of ensf_tc.cu
+// The 3x3 convolutions run on the tensor cores (ensf_conv.cu) wherever the
+// shapes allow (channel counts multiples of 32, whole image rows per
+// 128-pixel tile):
+//   forward        implicit GEMM over TMA boxes of the haloed input, bias and
+//                  SiLU in the epilogue                        -> z, y [P][Cout]
+//   data gradient  the same kernel on the haloed dZ with tap-mirrored weights
+//   weight grad.   nine GEMMs over the pixels: dZ^T [Cout][P] against the
+//                  input's column-shifted transposed copies   -> dW [Cout][9][Cin]
+// The 2-channel input convolution runs as direct SIMT kernels; other shapes
+// (the 16 x 16 level's weight gradients, channel counts that are not
+// multiples of 32) as im2col + the tcgen05 GEMM of ensf_tc.cu
 // (C[M][N] = A[M][K] B[N][K]^T, FP32 accumulation, split-K partials):
 //   forward        col [P][Kp]  x  W  [Cout][Kp]   -> [P][Cout]
 //   data gradient  dZ  [P][Cout] x W^T [Kp][Cout]  -> dcol [P][Kp] -> col2im
